@@ -1,0 +1,94 @@
+"""Pins of the seeded input generators (set-up arithmetic, not the step).
+
+* Linear-mode eigen-speeds: Alfven speed v_A cos(theta_kB), and for k
+  perpendicular to B the fast speed is c_ms; for k along B the sound speed
+  c_s and v_A (relativistic closed forms).
+* Fishbone-Moncrief torus: log-enthalpy zero at the inner edge, maximum at
+  r_max on the equator, unit 4-velocity, max rho = 1 after normalisation.
+* Counter-based random numbers depend only on (seed, zone index).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2110_10191_gb300 import problems as pb
+
+
+def _speeds(P0, gam, khat):
+    lam, _ = pb.mode_eigensystem(np.array(P0, float), gam, np.array(khat, float))
+    return np.sort(lam[lam > 1e-10])
+
+
+def _cs_va(rho, u, bsq, gam):
+    ef = rho + gam * u
+    cs2 = gam * (gam - 1) * u / ef
+    va2 = bsq / (bsq + ef)
+    return cs2, va2
+
+
+def test_alfven_speed_oblique():
+    gam = 4 / 3
+    s = _speeds([1, 1, 0, 0, 0, 1, 0, 0], gam, [1 / math.sqrt(2), 1 / math.sqrt(2)])
+    cs2, va2 = _cs_va(1, 1, 1, gam)
+    assert s[1] == pytest.approx(math.sqrt(va2) / math.sqrt(2), rel=1e-10)
+
+
+def test_fast_speed_perpendicular():
+    gam = 4 / 3
+    s = _speeds([1, 1, 0, 0, 0, 0, 1.0, 0], gam, [1, 0])
+    cs2, va2 = _cs_va(1, 1, 1, gam)
+    assert s[-1] == pytest.approx(math.sqrt(cs2 + va2 - cs2 * va2), rel=1e-10)
+
+
+def test_parallel_speeds():
+    gam = 5 / 3
+    s = _speeds([1, 0.5, 0, 0, 0, 0.8, 0, 0], gam, [1, 0])
+    cs2, va2 = _cs_va(1, 0.5, 0.64, gam)
+    got = sorted(set(np.round(s, 12)))
+    assert any(abs(x - math.sqrt(cs2)) < 1e-10 for x in got)
+    assert any(abs(x - math.sqrt(va2)) < 1e-10 for x in got)
+
+
+def test_mode_is_real_and_divergence_free():
+    pr = pb.linear_mode(16, kind="fast")
+    dP = pr.info["dP"]
+    k = np.array(pr.info["k"])
+    assert abs(dP[5] * k[0] + dP[6] * k[1]) < 1e-12
+    assert pr.info["period"] == pytest.approx(1 / (pr.info["speed"] * math.sqrt(2)), rel=1e-14)
+
+
+def test_fm_torus_enthalpy():
+    a, rin, rmax = 0.9375, 6.0, 12.0
+    ell = pb.fm_ell(a, rmax)
+    assert float(pb.fm_lnh(np.array(rin), np.array(math.pi / 2), a, ell, rin)) == 0.0
+    r = np.linspace(8, 20, 24001)
+    lnh = pb.fm_lnh(r, np.full_like(r, math.pi / 2), a, ell, rin)
+    assert r[np.argmax(lnh)] == pytest.approx(rmax, abs=1e-3)
+
+
+def test_fm_torus_four_velocity():
+    pr = pb.fm_torus(16, 16, 2, field=True)
+    P = pr.P
+    assert P[0].max() == pytest.approx(1.0, rel=1e-3)
+    dx1 = (pr.xmax[0] - pr.xmin[0]) / 16
+    X1 = pr.xmin[0] + (np.arange(16) + 0.5) * dx1
+    X2 = (np.arange(16) + 0.5) / 16
+    X1g, X2g = np.meshgrid(X1, X2, indexing="xy")
+    g = pb.mks_gcov(np.exp(X1g), X2g, pr.a, pr.hslope)
+    ut = np.stack([P[2, 0], P[3, 0], P[4, 0]], -1)
+    gam = np.sqrt(1 + np.einsum("...i,...ij,...j->...", ut, g[..., 1:, 1:], ut))
+    assert np.all(gam >= 1.0) and np.all(np.isfinite(gam))
+    inside = P[0, 0] > 1e-3
+    # in the torus the orbital speed is sub-relativistic but not zero
+    assert np.all(gam[inside] < 1.5) and np.any(gam[inside] > 1.01)
+
+
+def test_splitmix_reproducible():
+    idx = np.arange(1000, dtype=np.uint64)
+    a = pb.splitmix_uniform(7, idx)
+    b = pb.splitmix_uniform(7, idx[::-1])[::-1]
+    assert np.array_equal(a, b)
+    assert 0.0 <= a.min() and a.max() < 1.0
+    assert abs(a.mean() - 0.5) < 0.05
+    assert not np.array_equal(a, pb.splitmix_uniform(8, idx))
