@@ -269,7 +269,12 @@ def recon(kind, x):
     return float(out[0]), float(out[1])
 
 
+PHASES = ["flux", "ct", "update", "fixup", "other"]
+
+
 def op_counts(reset: bool = False):
-    out = np.zeros(4)
+    """Counting build: {phase: {add, mul, div, sqrt}} since the last reset."""
+    out = np.zeros(20)
     lib(True).oracle_op_counts(_dp(out), int(reset))
-    return {"add": out[0], "mul": out[1], "div": out[2], "sqrt": out[3]}
+    return {ph: {"add": out[4 * q], "mul": out[4 * q + 1], "div": out[4 * q + 2],
+                 "sqrt": out[4 * q + 3]} for q, ph in enumerate(PHASES)}

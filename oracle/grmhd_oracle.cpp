@@ -46,7 +46,11 @@
 struct OpCounts {
   double add, mul, div, sqrt;
 };
-static OpCounts g_ops;
+/* phases: 0 face fluxes, 1 boundary fixes + flux-CT, 2 update + inversion +
+ * floors, 3 fixup, 4 anything else */
+static OpCounts g_phase_ops[5];
+static int g_phase = 4;
+#define g_ops g_phase_ops[g_phase]
 struct real {
   double v;
   real() : v(0.0) {}
@@ -352,7 +356,7 @@ static void vchar(const real P[NPRIM], const FluidState &s, const GeomPt &g, rea
 /* ------------------------------------------------------------------------ */
 /* Monotonized-central limited slope: minmod(2 dm, (dm+dp)/2, 2 dp), zero
  * where the one-sided differences change sign.  Face values y -/+ slope/2. */
-static void recon_mc(real x0, real x1, real x2, real *lout, real *rout) {
+static real mc_slope(real x0, real x1, real x2) {
   real dm = x1 - x0, dp = x2 - x1;
   real slope = 0.0;
   if (dm * dp > 0.0) {
@@ -360,6 +364,11 @@ static void recon_mc(real x0, real x1, real x2, real *lout, real *rout) {
     real m = rmin(rmin(rabs(2.0 * dm), rabs(dc)), rabs(2.0 * dp));
     slope = (dc > 0.0) ? m : -m;
   }
+  return slope;
+}
+
+static void recon_mc(real x0, real x1, real x2, real *lout, real *rout) {
+  real slope = mc_slope(x0, x1, x2);
   *lout = x1 - 0.5 * slope;
   *rout = x1 + 0.5 * slope;
 }
@@ -470,6 +479,13 @@ static void build_geometry(Sim *S) {
 /* polar reflection copies the mirror zone with utilde^2 and B^2 negated.     */
 /* Order X1 (interior j,k), X2 (all i), X3 (all i,j) fills edges/corners.     */
 /* ------------------------------------------------------------------------ */
+/* periodic image of ghost index g along a direction of n zones */
+static int wrap_index(int g, int n) {
+  int q = (g - NG) % n;
+  if (q < 0) q += n;
+  return NG + q;
+}
+
 static void copy_zone(Sim *S, std::vector<real> &P, long dst, long src) {
   for (int v = 0; v < NPRIM; v++) P[v * S->ntot + dst] = P[v * S->ntot + src];
 }
@@ -484,7 +500,7 @@ static void bounds(Sim *S, std::vector<real> &P) {
         /* lower */
         int ig = g, ia;
         if (S->bc[0][0] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, ig, j, k), IDX(S, ig + n1, j, k));
+          copy_zone(S, P, IDX(S, ig, j, k), IDX(S, wrap_index(ig, n1), j, k));
         } else if (S->bc[0][0] == BC_OUTFLOW) {
           ia = NG;
           long d = IDX(S, ig, j, k), s = IDX(S, ia, j, k);
@@ -496,7 +512,7 @@ static void bounds(Sim *S, std::vector<real> &P) {
         /* upper */
         ig = n1 + NG + g;
         if (S->bc[0][1] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, ig, j, k), IDX(S, NG + g, j, k));
+          copy_zone(S, P, IDX(S, ig, j, k), IDX(S, wrap_index(ig, n1), j, k));
         } else if (S->bc[0][1] == BC_OUTFLOW) {
           ia = n1 + NG - 1;
           long d = IDX(S, ig, j, k), s = IDX(S, ia, j, k);
@@ -512,7 +528,7 @@ static void bounds(Sim *S, std::vector<real> &P) {
       for (int g = 0; g < NG; g++) {
         int jg = NG - 1 - g;
         if (S->bc[1][0] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, jg + n2, k));
+          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, wrap_index(jg, n2), k));
         } else if (S->bc[1][0] == BC_POLAR) {
           long d = IDX(S, i, jg, k);
           copy_zone(S, P, d, IDX(S, i, NG + g, k));
@@ -523,7 +539,7 @@ static void bounds(Sim *S, std::vector<real> &P) {
         }
         jg = n2 + NG + g;
         if (S->bc[1][1] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, NG + g, k));
+          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, wrap_index(jg, n2), k));
         } else if (S->bc[1][1] == BC_POLAR) {
           long d = IDX(S, i, jg, k);
           copy_zone(S, P, d, IDX(S, i, n2 + NG - 1 - g, k));
@@ -539,12 +555,12 @@ static void bounds(Sim *S, std::vector<real> &P) {
       for (int g = 0; g < NG; g++) {
         int kg = NG - 1 - g;
         if (S->bc[2][0] == BC_PERIODIC)
-          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, kg + n3));
+          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));
         else if (S->bc[2][0] == BC_OUTFLOW)
           copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, NG));
         kg = n3 + NG + g;
         if (S->bc[2][1] == BC_PERIODIC)
-          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, NG + g));
+          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));
         else if (S->bc[2][1] == BC_OUTFLOW)
           copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, n3 + NG - 1));
       }
@@ -568,17 +584,12 @@ static void face_states(const Sim *S, const std::vector<real> &P, int d, int i, 
       int s = q - 3;
       x[q] = P[v * S->ntot + IDX(S, i + s * off[0], j + s * off[1], k + s * off[2])];
     }
-    real l, r;
     if (S->recon == RECON_WENO5) {
-      recon_weno5(&x[0], &l, &r); /* zone c-1 */
-      PL[v] = r;
-      recon_weno5(&x[1], &l, &r); /* zone c */
-      PR[v] = l;
+      PL[v] = weno5_right(x[0], x[1], x[2], x[3], x[4]); /* high face of zone c-1 */
+      PR[v] = weno5_right(x[5], x[4], x[3], x[2], x[1]); /* low face of zone c */
     } else {
-      recon_mc(x[1], x[2], x[3], &l, &r);
-      PL[v] = r;
-      recon_mc(x[2], x[3], x[4], &l, &r);
-      PR[v] = l;
+      PL[v] = x[2] + 0.5 * mc_slope(x[1], x[2], x[3]);
+      PR[v] = x[3] - 0.5 * mc_slope(x[2], x[3], x[4]);
     }
   }
 }
@@ -929,6 +940,10 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
       }
   /* fixup of failed zones: mean of the non-failed interior zones of the
    * 3x3x3 neighbourhood (rho, u, utilde); B is kept.  READING. */
+#ifdef ORACLE_COUNT
+  int saved_phase = g_phase;
+  g_phase = 3;
+#endif
   int unrecoverable = 0;
   for (int k = NG; k < n3 + NG; k++)
     for (int j = NG; j < n2 + NG; j++)
@@ -967,6 +982,9 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
       for (int i = NG; i < n1 + NG; i++)
         if (S->fflag[IDX(S, i, j, k)]) S->floor_hits_total++;
   S->unrecoverable_total += unrecoverable;
+#ifdef ORACLE_COUNT
+  g_phase = saved_phase;
+#endif
   bounds(S, Pout);
   return unrecoverable;
 }
@@ -992,20 +1010,34 @@ static double compute_dt(Sim *S) {
   return dt;
 }
 
+#ifdef ORACLE_COUNT
+#define PHASE(p) (g_phase = (p))
+#else
+#define PHASE(p) ((void)0)
+#endif
+
 static int step_once(Sim *S) {
   /* predictor: Ps = Pi = P^n, dt' = dt/2 -> Ph */
+  PHASE(0);
   get_fluxes(S, S->P);
+  PHASE(4);
   double dt = compute_dt(S);
   if (!std::isfinite(dt)) return -3;
   if (dt <= 0.0) return 0; /* at t_final: the step is a no-op */
+  PHASE(1);
   fix_flux(S);
   flux_ct(S);
+  PHASE(2);
   int bad = advance_stage(S, S->P, S->P, S->Ph, 0.5 * dt);
   /* corrector: Ps = P^{n+1/2}, Pi = P^n, dt' = dt -> P^{n+1} */
+  PHASE(0);
   get_fluxes(S, S->Ph);
+  PHASE(1);
   fix_flux(S);
   flux_ct(S);
+  PHASE(2);
   bad += advance_stage(S, S->P, S->Ph, S->P, dt);
+  PHASE(4);
   S->t += dt;
   S->dt = dt;
   S->dt_prev = dt;
@@ -1322,14 +1354,21 @@ int oracle_is_counting(void) {
 #endif
 }
 
-/* add/sub, mul, div, sqrt counts since the last reset (counting build). */
-void oracle_op_counts(double out[4], int reset) {
+/* add/sub, mul, div, sqrt counts per phase since the last reset, out[5][4]
+ * (phases: fluxes, flux fixes + flux-CT, update + inversion + floors,
+ * fixup, other); zeros in the plain build. */
+void oracle_op_counts(double out[20], int reset) {
 #ifdef ORACLE_COUNT
-  out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt;
-  if (reset) g_ops = OpCounts{0, 0, 0, 0};
+  for (int p = 0; p < 5; p++) {
+    out[4 * p + 0] = g_phase_ops[p].add;
+    out[4 * p + 1] = g_phase_ops[p].mul;
+    out[4 * p + 2] = g_phase_ops[p].div;
+    out[4 * p + 3] = g_phase_ops[p].sqrt;
+    if (reset) g_phase_ops[p] = OpCounts{0, 0, 0, 0};
+  }
 #else
   (void)reset;
-  out[0] = out[1] = out[2] = out[3] = 0.0;
+  for (int q = 0; q < 20; q++) out[q] = 0.0;
 #endif
 }
 
