@@ -1,0 +1,202 @@
+/*
+ * grmhd.h -- C ABI of the GB300 (sm_103a) GRMHD step library.
+ *
+ * The library advances the equations of ideal general-relativistic MHD on a
+ * fixed, stationary metric with the HARM conservative finite-volume scheme
+ * that iharm3D implements (arXiv:2110.10191, "Functionality and Purpose"):
+ * a logically Cartesian mesh in arbitrary coordinates, primitives in,
+ * primitives after N predictor-corrector steps out.  Each step is
+ *   predictor: fluxes of P^n -> CFL time step -> U(P^n) + dt/2 (-div F + S)
+ *              -> 1D_W inversion (paper, "Implementation Notes", third
+ *              paragraph) -> bounds (same section, list of bounds) -> fixup;
+ *   corrector: fluxes of P^{n+1/2} -> U(P^n) + dt (-div F + S) -> ... -> P^{n+1},
+ * with flux-CT constrained transport (same section, first paragraph) and a
+ * metric evaluated numerically from its analytic line element (second
+ * paragraph).  Units GM = c = 1 (fourth paragraph).
+ *
+ * Conventions shared by every call:
+ *   - Primitives P: 8 variables in the order rho, u (internal energy
+ *     density), utilde^1..3 (4-velocity relative to the normal observer),
+ *     B^1..3 (= *F^{it}).  Arrays are structure-of-arrays, float64,
+ *     P[v][k][j][i] with i fastest.  "Interior" arrays are [8][n3][n2][n1];
+ *     "ghost" arrays include 3 ghost layers per side:
+ *     [8][n3+6][n2+6][n1+6].
+ *   - on_device = 1: the pointer is a CUDA device pointer valid on the
+ *     simulation's stream (e.g. a torch tensor's data_ptr()); 0: host memory
+ *     (pageable or pinned).  Host copies are synchronous with respect to the
+ *     caller; device copies are ordered on the stream.
+ *   - Ownership: the library owns every device buffer of a simulation; the
+ *     caller owns the buffers it passes.  Nothing is retained after a call.
+ *   - Errors: every call returns GRMHD_OK (0) or a negative code; no call
+ *     aborts, exits or throws.  grmhd_strerror() names a code.
+ *   - All entry points are thread-compatible, not thread-safe: one
+ *     simulation must not be used from two threads at once.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRMHD_OK 0
+#define GRMHD_ERR_INVALID (-1)   /* bad argument, size or enum */
+#define GRMHD_ERR_NOMEM (-2)     /* device allocation failed */
+#define GRMHD_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define GRMHD_ERR_INVERSION (-4) /* a failed zone had no valid neighbour */
+#define GRMHD_ERR_DT (-5)        /* no finite time step (all signal speeds zero) */
+
+#define GRMHD_METRIC_MINKOWSKI 0 /* Cartesian flat space */
+#define GRMHD_METRIC_MKS_KERR 1  /* Kerr in modified Kerr-Schild coordinates */
+
+#define GRMHD_BC_PERIODIC 0
+#define GRMHD_BC_OUTFLOW 1 /* X1 only: copy, sqrt(-g) B constant, no inflow */
+#define GRMHD_BC_POLAR 2   /* X2 only: reflect, utilde^2 and B^2 negated */
+#define GRMHD_BC_FIXED 3   /* ghosts keep the values last set */
+
+#define GRMHD_RECON_MC 0
+#define GRMHD_RECON_WENO5 1
+
+typedef struct grmhd_sim grmhd_sim; /* opaque, library-owned */
+
+/* Logically Cartesian mesh of n1 x n2 x n3 zones on [xmin, xmax] per
+ * direction (code coordinates X^1..3).  n3 = 1 (and n2 = 1) give 2D (1D)
+ * problems; every direction still carries 3 ghost layers. */
+typedef struct {
+  int n1, n2, n3;
+  double x1min, x1max, x2min, x2max, x3min, x3max;
+} grmhd_grid;
+
+/* Stationary metric.  MKS: r = exp(X1), theta = pi X2 + (1-hslope)/2
+ * sin(2 pi X2), phi = X3, Kerr of mass 1 and spin a in Kerr-Schild form. */
+typedef struct {
+  int kind;
+  double a, hslope;
+} grmhd_metric;
+
+/* gamma: adiabatic index; cfl: Courant number; t_final > 0 clamps the last
+ * step to land on it (steps after it do nothing); recon: GRMHD_RECON_*;
+ * floors_on: apply the paper's bounds (needs the MKS radius); bc[d][side]:
+ * GRMHD_BC_* for direction d, side 0 = low, 1 = high. */
+typedef struct {
+  double gamma, cfl, t_final;
+  int recon, floors_on;
+  int bc[3][2];
+} grmhd_params;
+
+/* Running statistics of a simulation (totals over all stages so far). */
+typedef struct {
+  double t, dt;                  /* current time, last step's dt */
+  long long steps;               /* full steps taken */
+  long long inv_failures;        /* zones whose 1D_W inversion failed */
+  long long floor_hits;          /* zones in which any bound acted */
+  long long unrecoverable;       /* failed zones with no valid neighbour */
+} grmhd_stats;
+
+/* Allocate a simulation on the current CUDA device and build its geometry
+ * (metric, inverse, sqrt(-g), lapse at zone centres and faces, numerical
+ * connection at centres).  stream: a cudaStream_t (NULL = legacy default
+ * stream) on which every later call of this simulation is ordered.
+ * n1, n2, n3 >= 1 and (n1+6)(n2+6)(n3+6) < 2^31.  *out is set on success. */
+int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
+                 const grmhd_params *params, void *stream, grmhd_sim **out);
+
+/* Free every device buffer.  NULL is accepted. */
+int grmhd_destroy(grmhd_sim *sim);
+
+/* Set the interior primitives ([8][n3][n2][n1]) and fill the ghosts by the
+ * boundary conditions. */
+int grmhd_set_prims(grmhd_sim *sim, const double *P, int on_device);
+
+/* Set primitives including ghosts ([8][n3+6][n2+6][n1+6]); the boundary
+ * conditions then refill every non-FIXED ghost region. */
+int grmhd_set_prims_ghost(grmhd_sim *sim, const double *P, int on_device);
+
+/* Read the primitives, interior ([8][n3][n2][n1]) or with ghosts. */
+int grmhd_get_prims(grmhd_sim *sim, double *P, int with_ghosts, int on_device);
+
+/* Advance nsteps full predictor-corrector steps, enqueued on the stream.
+ * stats == NULL: returns after enqueueing (errors of this call surface at
+ * the next synchronising call).  stats != NULL: synchronises, fills *stats
+ * and returns GRMHD_ERR_INVERSION if any failed zone had no valid neighbour
+ * since the previous synchronising call. */
+int grmhd_step(grmhd_sim *sim, int nsteps, grmhd_stats *stats);
+
+/* Synchronise and read the running statistics. */
+int grmhd_get_stats(grmhd_sim *sim, grmhd_stats *stats);
+
+/* Restore the clock of a checkpoint: time t, the previous step's dt (the
+ * next step's growth limit depends on it) and the step count. */
+int grmhd_set_time(grmhd_sim *sim, double t, double dt_prev, long long steps);
+
+/* ---- Stage-level access, for verification of the individual steps ---- */
+
+/* Predictor stage only: P <- P^{n+1/2} (time and step count unchanged). */
+int grmhd_predictor(grmhd_sim *sim);
+
+/* Face fluxes of the current state after the boundary flux fixes and
+ * flux-CT, into host memory F[3][8][n3+6][n2+6][n1+6] (face i-1/2 of zone
+ * i stored at zone i; entries outside the computed face ranges are zero),
+ * and the maximum signal speed over interior faces per direction ctop[3]. */
+int grmhd_get_fluxes(grmhd_sim *sim, double *F, double *ctop);
+
+/* The time step the next step would take (host value). */
+int grmhd_next_dt(grmhd_sim *sim, double *dt);
+
+/* Inversion failure code and bound flags of the last stage, interior
+ * [n3][n2][n1] int32, into host memory. */
+int grmhd_get_flags(grmhd_sim *sim, int *pflag, int *fflag);
+
+/* Geometry at location loc (0 zone centre, 1 X1 face, 2 X2 face) as host
+ * out[34][n2+6][n1+6]: g_{mu nu} (16, row-major), g^{mu nu} (16), sqrt(-g),
+ * lapse; loc 3 gives the connection Gamma^l_{m n} out[64][n2+6][n1+6]
+ * (index (l*4+m)*4+n) at zone centres. */
+int grmhd_get_geometry(grmhd_sim *sim, int loc, double *out);
+
+/* Replace the geometry at location loc with caller-supplied values, in the
+ * layout grmhd_get_geometry() returns (host memory; loc 0..2: g_{mu nu},
+ * g^{mu nu}, sqrt(-g), lapse; loc 3: the connection).  Only the upper
+ * triangle (m <= n) of each symmetric index pair is read.  This runs the
+ * step on a tabulated metric (any stationary, X3-independent spacetime
+ * whose line element the library does not build in) and lets a test hold
+ * the geometry fixed while it checks the step.  The bound thresholds keep
+ * following the built-in radius r = exp(X1). */
+int grmhd_set_geometry(grmhd_sim *sim, int loc, const double *in);
+
+/* Kernel classes of the step, for grmhd_get_profile(). */
+#define GRMHD_K_FLUX 0    /* reconstruction + LLF face fluxes (3 launches a stage) */
+#define GRMHD_K_DT 1      /* CFL time step */
+#define GRMHD_K_CT 2      /* boundary flux fixes + flux-CT */
+#define GRMHD_K_UPDATE 3  /* conserved update + 1D_W inversion + bounds */
+#define GRMHD_K_FIXUP 4   /* fixup of failed zones */
+#define GRMHD_K_BOUNDS 5  /* ghost fill */
+#define GRMHD_K_OTHER 6   /* clock advance, signal-speed reset */
+#define GRMHD_NKCLASS 7
+
+typedef struct {
+  double ms[GRMHD_NKCLASS];            /* summed device time per class */
+  long long launches[GRMHD_NKCLASS];   /* kernels launched per class */
+} grmhd_profile_data;
+
+/* enable != 0: record CUDA events on the simulation's stream around each
+ * kernel class of the following steps (timing); launches are always
+ * counted.  The events add no synchronisation. */
+int grmhd_profile(grmhd_sim *sim, int enable);
+
+/* Synchronise and read the per-class device times and launch counts since
+ * the last reset; reset != 0 clears them afterwards. */
+int grmhd_get_profile(grmhd_sim *sim, grmhd_profile_data *out, int reset);
+
+/* Measured double-precision FMA throughput of the current device: runs a
+ * dependency-free DFMA kernel for about `iters` FMAs per thread on every SM
+ * and returns FLOP/s (2 per FMA) in *flops.  Used as the roofline peak of
+ * the FP64-bound kernels. */
+int grmhd_fp64_peak(long long iters, double *flops);
+
+/* Name of an error code. */
+const char *grmhd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRMHD_H */

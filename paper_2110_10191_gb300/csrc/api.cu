@@ -1,0 +1,537 @@
+// api.cu -- the C ABI (include/grmhd.h): simulation lifetime, state I/O and
+// the host-side driver that enqueues the kernels of each step on the
+// simulation's stream.  The step needs no host round trip: the CFL time
+// step, the clock and the statistics live in device memory.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/grmhd.h"
+#include "grmhd_dev.cuh"
+#include "grmhd_impl.h"
+
+using namespace grmhd;
+
+struct grmhd_sim {
+  Dims D;
+  grmhd_grid grid;
+  grmhd_metric metric;
+  grmhd_params params;
+  cudaStream_t st;
+  double *P, *Ph, *F[3], *emf;
+  double *geom, *conn, *floors;
+  int *pflag, *fflag;
+  Clock *clk;
+  unsigned long long unrec_seen, dterr_seen;
+  StepArgs A;
+  // profiling: event pairs per class, launches per class
+  int prof_on;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *prof_ev;
+  std::vector<cudaEvent_t> *ev_pool;
+  long long launches[GRMHD_NKCLASS];
+  double prof_ms[GRMHD_NKCLASS];
+};
+
+// Brackets the launches of one kernel class: counts them and, when
+// profiling, records an event pair on the stream around them.
+struct ClassScope {
+  grmhd_sim *s;
+  int cls;
+  cudaEvent_t e0, e1;
+  ClassScope(grmhd_sim *s_, int cls_, int nlaunch) : s(s_), cls(cls_), e0(nullptr), e1(nullptr) {
+    s->launches[cls] += nlaunch;
+    if (s->prof_on) {
+      e0 = take_event(s);
+      e1 = take_event(s);
+      cudaEventRecord(e0, s->st);
+    }
+  }
+  ~ClassScope() {
+    if (s->prof_on) {
+      cudaEventRecord(e1, s->st);
+      s->prof_ev->push_back({cls, {e0, e1}});
+    }
+  }
+  static cudaEvent_t take_event(grmhd_sim *s) {
+    if (!s->ev_pool->empty()) {
+      cudaEvent_t e = s->ev_pool->back();
+      s->ev_pool->pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return GRMHD_ERR_CUDA; \
+  } while (0)
+
+static int launched(void) { return (cudaGetLastError() == cudaSuccess) ? GRMHD_OK : GRMHD_ERR_CUDA; }
+
+static void collect_profile(grmhd_sim *s) {
+  if (!s->prof_ev) return;
+  for (auto &p : *s->prof_ev) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
+      s->prof_ms[p.first] += ms;
+    s->ev_pool->push_back(p.second.first);
+    s->ev_pool->push_back(p.second.second);
+  }
+  s->prof_ev->clear();
+}
+
+static void free_all(grmhd_sim *s) {
+  if (s->prof_ev) {
+    cudaStreamSynchronize(s->st);
+    collect_profile(s);
+    for (cudaEvent_t e : *s->ev_pool) cudaEventDestroy(e);
+    delete s->prof_ev;
+    delete s->ev_pool;
+    s->prof_ev = nullptr;
+    s->ev_pool = nullptr;
+  }
+  double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->geom, s->conn, s->floors};
+  for (double *p : d)
+    if (p) cudaFree(p);
+  if (s->pflag) cudaFree(s->pflag);
+  if (s->fflag) cudaFree(s->fflag);
+  if (s->clk) cudaFree(s->clk);
+}
+
+extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
+                            const grmhd_params *params, void *stream, grmhd_sim **out) {
+  if (!grid || !metric || !params || !out) return GRMHD_ERR_INVALID;
+  *out = nullptr;
+  const int n[3] = {grid->n1, grid->n2, grid->n3};
+  const double xmin[3] = {grid->x1min, grid->x2min, grid->x3min};
+  const double xmax[3] = {grid->x1max, grid->x2max, grid->x3max};
+  long long tot = 1;
+  for (int d = 0; d < 3; d++) {
+    if (n[d] < 1 || n[d] > (1 << 20)) return GRMHD_ERR_INVALID;
+    if (!(xmax[d] > xmin[d])) return GRMHD_ERR_INVALID;
+    tot *= (long long)(n[d] + 2 * NG);
+  }
+  if (tot >= (1ll << 31)) return GRMHD_ERR_INVALID;
+  if (metric->kind != GRMHD_METRIC_MINKOWSKI && metric->kind != GRMHD_METRIC_MKS_KERR)
+    return GRMHD_ERR_INVALID;
+  if (metric->kind == GRMHD_METRIC_MKS_KERR && !(fabs(metric->a) < 1.0)) return GRMHD_ERR_INVALID;
+  if (!(params->gamma > 1.0) || !(params->cfl > 0.0)) return GRMHD_ERR_INVALID;
+  if (params->recon != GRMHD_RECON_MC && params->recon != GRMHD_RECON_WENO5) return GRMHD_ERR_INVALID;
+  if (params->floors_on && metric->kind != GRMHD_METRIC_MKS_KERR) return GRMHD_ERR_INVALID;
+  for (int d = 0; d < 3; d++)
+    for (int sd = 0; sd < 2; sd++) {
+      const int b = params->bc[d][sd];
+      if (b < 0 || b > 3) return GRMHD_ERR_INVALID;
+      if (b == GRMHD_BC_OUTFLOW && d != 0) return GRMHD_ERR_INVALID;
+      if (b == GRMHD_BC_POLAR && (d != 1 || n[1] < NG)) return GRMHD_ERR_INVALID;
+      if ((b == GRMHD_BC_PERIODIC) != (params->bc[d][1 - sd] == GRMHD_BC_PERIODIC))
+        return GRMHD_ERR_INVALID;
+    }
+
+  grmhd_sim *s = new (std::nothrow) grmhd_sim();
+  if (!s) return GRMHD_ERR_NOMEM;
+  memset((void *)s, 0, sizeof(*s));
+  s->prof_ev = new (std::nothrow) std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
+  s->ev_pool = new (std::nothrow) std::vector<cudaEvent_t>();
+  if (!s->prof_ev || !s->ev_pool) {
+    delete s->prof_ev;
+    delete s->ev_pool;
+    delete s;
+    return GRMHD_ERR_NOMEM;
+  }
+  s->grid = *grid;
+  s->metric = *metric;
+  s->params = *params;
+  s->st = (cudaStream_t)stream;
+  Dims &D = s->D;
+  for (int d = 0; d < 3; d++) {
+    D.n[d] = n[d];
+    D.s[d] = n[d] + 2 * NG;
+  }
+  D.ntot = tot;
+  D.n2d = (long long)D.s[0] * D.s[1];
+  const size_t fb = sizeof(double) * NV * (size_t)tot;
+  bool ok = cudaMalloc(&s->P, fb) == cudaSuccess && cudaMalloc(&s->Ph, fb) == cudaSuccess &&
+            cudaMalloc(&s->F[0], fb) == cudaSuccess && cudaMalloc(&s->F[1], fb) == cudaSuccess &&
+            cudaMalloc(&s->F[2], fb) == cudaSuccess &&
+            cudaMalloc(&s->emf, sizeof(double) * 3 * (size_t)tot) == cudaSuccess &&
+            cudaMalloc(&s->geom, sizeof(double) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
+            cudaMalloc(&s->conn, sizeof(double) * C_NCOMP * (size_t)D.n2d) == cudaSuccess &&
+            cudaMalloc(&s->floors, sizeof(double) * 2 * (size_t)D.n2d) == cudaSuccess &&
+            cudaMalloc(&s->pflag, sizeof(int) * (size_t)tot) == cudaSuccess &&
+            cudaMalloc(&s->fflag, sizeof(int) * (size_t)tot) == cudaSuccess &&
+            cudaMalloc(&s->clk, sizeof(Clock)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(s);
+    delete s;
+    return GRMHD_ERR_NOMEM;
+  }
+  int rc = GRMHD_OK;
+  cudaStream_t st = s->st;
+  // zero every field so that entries outside the computed ranges read as 0
+  if (cudaMemsetAsync(s->P, 0, fb, st) != cudaSuccess || cudaMemsetAsync(s->Ph, 0, fb, st) != cudaSuccess ||
+      cudaMemsetAsync(s->F[0], 0, fb, st) != cudaSuccess || cudaMemsetAsync(s->F[1], 0, fb, st) != cudaSuccess ||
+      cudaMemsetAsync(s->F[2], 0, fb, st) != cudaSuccess ||
+      cudaMemsetAsync(s->emf, 0, sizeof(double) * 3 * (size_t)tot, st) != cudaSuccess ||
+      cudaMemsetAsync(s->pflag, 0, sizeof(int) * (size_t)tot, st) != cudaSuccess ||
+      cudaMemsetAsync(s->fflag, 0, sizeof(int) * (size_t)tot, st) != cudaSuccess)
+    rc = GRMHD_ERR_CUDA;
+  Clock c0;
+  memset(&c0, 0, sizeof(c0));
+  c0.t_final = params->t_final;
+  if (rc == GRMHD_OK && cudaMemcpyAsync(s->clk, &c0, sizeof(c0), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = GRMHD_ERR_CUDA;
+  GeomArgs G;
+  G.D = D;
+  G.kind = metric->kind;
+  G.a = metric->a;
+  G.h = metric->hslope;
+  G.gam = params->gamma;
+  for (int d = 0; d < 3; d++) {
+    G.xmin[d] = xmin[d];
+    G.dx[d] = (xmax[d] - xmin[d]) / n[d];
+  }
+  G.geom = s->geom;
+  G.conn = s->conn;
+  G.floors = s->floors;
+  if (rc == GRMHD_OK) {
+    launch_geometry(G, st);
+    rc = launched();
+  }
+  if (rc == GRMHD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
+  if (rc != GRMHD_OK) {
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  StepArgs &A = s->A;
+  A.D = D;
+  A.gam = params->gamma;
+  A.cfl = params->cfl;
+  for (int d = 0; d < 3; d++) A.dx[d] = G.dx[d];
+  A.recon = params->recon;
+  A.floors_on = params->floors_on;
+  for (int d = 0; d < 3; d++)
+    for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
+  A.geom = s->geom;
+  A.conn = s->conn;
+  A.floors = s->floors;
+  A.clk = s->clk;
+  *out = s;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_destroy(grmhd_sim *s) {
+  if (!s) return GRMHD_OK;
+  cudaStreamSynchronize(s->st);
+  free_all(s);
+  delete s;
+  return GRMHD_OK;
+}
+
+static void enqueue_fluxes(grmhd_sim *s, const double *P) {
+  {
+    ClassScope c(s, GRMHD_K_OTHER, 1);
+    launch_ctop_reset(s->A, s->st);
+  }
+  ClassScope c(s, GRMHD_K_FLUX, 3);
+  launch_fluxes(s->A, P, s->F, s->st);
+}
+
+static void enqueue_bounds(grmhd_sim *s, double *P) {
+  ClassScope c(s, GRMHD_K_BOUNDS, 3);
+  launch_bounds(s->A, P, s->st);
+}
+
+static void enqueue_stage(grmhd_sim *s, const double *Pi, const double *Ps, double *Pout,
+                          double dtfac, bool first) {
+  cudaStream_t st = s->st;
+  enqueue_fluxes(s, Ps);
+  if (first) {
+    ClassScope c(s, GRMHD_K_DT, 1);
+    launch_dt(s->A, st);
+  }
+  {
+    ClassScope c(s, GRMHD_K_CT, 3);
+    launch_fix_ct(s->A, s->F, s->emf, st);
+  }
+  {
+    ClassScope c(s, GRMHD_K_UPDATE, 1);
+    launch_update(s->A, Pi, Ps, Pout, s->F, s->pflag, s->fflag, dtfac, st);
+  }
+  {
+    ClassScope c(s, GRMHD_K_FIXUP, 1);
+    launch_fixup(s->A, Pout, s->pflag, s->fflag, st);
+  }
+  enqueue_bounds(s, Pout);
+}
+
+static int set_common(grmhd_sim *s, const double *P, int on_device, int ghost) {
+  if (!s || !P) return GRMHD_ERR_INVALID;
+  const Dims &D = s->D;
+  const long long nz = (long long)D.n[0] * D.n[1] * D.n[2];
+  const size_t bytes = sizeof(double) * NV * (size_t)(ghost ? D.ntot : nz);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (ghost) {
+    CK(cudaMemcpyAsync(s->P, P, bytes, kind, s->st));
+  } else {
+    CK(cudaMemcpyAsync(s->Ph, P, bytes, kind, s->st));  // Ph is scratch between steps
+    launch_pack(D, s->Ph, s->P, 1, s->st);
+  }
+  enqueue_bounds(s, s->P);
+  int rc = launched();
+  if (rc != GRMHD_OK) return rc;
+  if (!on_device) CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_set_prims(grmhd_sim *s, const double *P, int on_device) {
+  return set_common(s, P, on_device, 0);
+}
+
+extern "C" int grmhd_set_prims_ghost(grmhd_sim *s, const double *P, int on_device) {
+  return set_common(s, P, on_device, 1);
+}
+
+extern "C" int grmhd_get_prims(grmhd_sim *s, double *P, int with_ghosts, int on_device) {
+  if (!s || !P) return GRMHD_ERR_INVALID;
+  const Dims &D = s->D;
+  const long long nz = (long long)D.n[0] * D.n[1] * D.n[2];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (with_ghosts) {
+    CK(cudaMemcpyAsync(P, s->P, sizeof(double) * NV * (size_t)D.ntot, kind, s->st));
+  } else {
+    launch_pack(D, s->P, s->Ph, 0, s->st);
+    int rc = launched();
+    if (rc != GRMHD_OK) return rc;
+    CK(cudaMemcpyAsync(P, s->Ph, sizeof(double) * NV * (size_t)nz, kind, s->st));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+static int read_stats(grmhd_sim *s, grmhd_stats *out, bool check) {
+  Clock c;
+  CK(cudaMemcpyAsync(&c, s->clk, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (out) {
+    out->t = c.t;
+    out->dt = c.dt;
+    out->steps = c.steps;
+    out->inv_failures = (long long)c.counters[0];
+    out->floor_hits = (long long)c.counters[1];
+    out->unrecoverable = (long long)c.counters[2];
+  }
+  int rc = GRMHD_OK;
+  if (check && c.counters[2] > s->unrec_seen) rc = GRMHD_ERR_INVERSION;
+  if (check && c.counters[3] > s->dterr_seen) rc = GRMHD_ERR_DT;
+  s->unrec_seen = c.counters[2];
+  s->dterr_seen = c.counters[3];
+  return rc;
+}
+
+extern "C" int grmhd_step(grmhd_sim *s, int nsteps, grmhd_stats *stats) {
+  if (!s || nsteps < 0) return GRMHD_ERR_INVALID;
+  for (int n = 0; n < nsteps; n++) {
+    enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true);   // predictor
+    enqueue_stage(s, s->P, s->Ph, s->P, 1.0, false);  // corrector
+    ClassScope c(s, GRMHD_K_OTHER, 1);
+    launch_advance(s->A, s->st);
+  }
+  int rc = launched();
+  if (rc != GRMHD_OK) return rc;
+  if (stats) return read_stats(s, stats, true);
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_get_stats(grmhd_sim *s, grmhd_stats *stats) {
+  if (!s || !stats) return GRMHD_ERR_INVALID;
+  return read_stats(s, stats, false);
+}
+
+extern "C" int grmhd_set_time(grmhd_sim *s, double t, double dt_prev, long long steps) {
+  if (!s) return GRMHD_ERR_INVALID;
+  Clock c;
+  CK(cudaMemcpyAsync(&c, s->clk, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  c.t = t;
+  c.dt = dt_prev;
+  c.dt_prev = dt_prev;
+  c.steps = steps;
+  CK(cudaMemcpyAsync(s->clk, &c, sizeof(c), cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_predictor(grmhd_sim *s) {
+  if (!s) return GRMHD_ERR_INVALID;
+  enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true);
+  int rc = launched();
+  if (rc != GRMHD_OK) return rc;
+  double *t = s->P;
+  s->P = s->Ph;
+  s->Ph = t;
+  return read_stats(s, nullptr, true);
+}
+
+extern "C" int grmhd_get_fluxes(grmhd_sim *s, double *F, double *ctop) {
+  if (!s || !F) return GRMHD_ERR_INVALID;
+  enqueue_fluxes(s, s->P);
+  {
+    ClassScope c(s, GRMHD_K_CT, 3);
+    launch_fix_ct(s->A, s->F, s->emf, s->st);
+  }
+  int rc = launched();
+  if (rc != GRMHD_OK) return rc;
+  const size_t per = sizeof(double) * NV * (size_t)s->D.ntot;
+  for (int d = 0; d < 3; d++)
+    CK(cudaMemcpyAsync((char *)F + d * per, s->F[d], per, cudaMemcpyDeviceToHost, s->st));
+  Clock c;
+  CK(cudaMemcpyAsync(&c, s->clk, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (ctop) {
+    for (int d = 0; d < 3; d++) {
+      double v;
+      memcpy(&v, &c.ctop_bits[d], sizeof(v));
+      ctop[d] = v;
+    }
+  }
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_next_dt(grmhd_sim *s, double *dt) {
+  if (!s || !dt) return GRMHD_ERR_INVALID;
+  Clock c0, c1;
+  CK(cudaMemcpyAsync(&c0, s->clk, sizeof(c0), cudaMemcpyDeviceToHost, s->st));
+  enqueue_fluxes(s, s->P);
+  {
+    ClassScope c(s, GRMHD_K_DT, 1);
+    launch_dt(s->A, s->st);
+  }
+  int rc = launched();
+  if (rc != GRMHD_OK) return rc;
+  CK(cudaMemcpyAsync(&c1, s->clk, sizeof(c1), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  *dt = c1.dt;
+  c1.dt = c0.dt;  // leave the reported last-step dt unchanged
+  CK(cudaMemcpyAsync(s->clk, &c1, sizeof(c1), cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_get_flags(grmhd_sim *s, int *pflag, int *fflag) {
+  if (!s || !pflag || !fflag) return GRMHD_ERR_INVALID;
+  const Dims &D = s->D;
+  std::vector<int> a((size_t)D.ntot), b((size_t)D.ntot);
+  CK(cudaMemcpyAsync(a.data(), s->pflag, sizeof(int) * a.size(), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(b.data(), s->fflag, sizeof(int) * b.size(), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  long long o = 0;
+  for (int k = 0; k < D.n[2]; k++)
+    for (int j = 0; j < D.n[1]; j++)
+      for (int i = 0; i < D.n[0]; i++, o++) {
+        const long long c = ((long long)(k + NG) * D.s[1] + (j + NG)) * D.s[0] + (i + NG);
+        pflag[o] = a[(size_t)c];
+        fflag[o] = b[(size_t)c];
+      }
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_get_geometry(grmhd_sim *s, int loc, double *out) {
+  if (!s || !out || loc < 0 || loc > 3) return GRMHD_ERR_INVALID;
+  const long long n2d = s->D.n2d;
+  if (loc == 3) {
+    std::vector<double> c((size_t)(C_NCOMP * n2d));
+    CK(cudaMemcpyAsync(c.data(), s->conn, sizeof(double) * c.size(), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int l = 0; l < 4; l++)
+      for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++)
+          memcpy(out + ((l * 4 + m) * 4 + n) * n2d, c.data() + (l * 10 + SY(m, n)) * n2d,
+                 sizeof(double) * (size_t)n2d);
+    return GRMHD_OK;
+  }
+  std::vector<double> g((size_t)(G_NCOMP * n2d));
+  CK(cudaMemcpyAsync(g.data(), s->geom + (long long)loc * G_NCOMP * n2d, sizeof(double) * g.size(),
+                     cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  for (int m = 0; m < 4; m++)
+    for (int n = 0; n < 4; n++) {
+      memcpy(out + (m * 4 + n) * n2d, g.data() + (G_GCOV + SY(m, n)) * n2d, sizeof(double) * (size_t)n2d);
+      memcpy(out + (16 + m * 4 + n) * n2d, g.data() + (G_GCON + SY(m, n)) * n2d,
+             sizeof(double) * (size_t)n2d);
+    }
+  memcpy(out + 32 * n2d, g.data() + G_GDET * n2d, sizeof(double) * (size_t)n2d);
+  memcpy(out + 33 * n2d, g.data() + G_ALPHA * n2d, sizeof(double) * (size_t)n2d);
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
+  if (!s || !in || loc < 0 || loc > 3) return GRMHD_ERR_INVALID;
+  const long long n2d = s->D.n2d;
+  if (loc == 3) {
+    std::vector<double> c((size_t)(C_NCOMP * n2d));
+    for (int l = 0; l < 4; l++)
+      for (int m = 0; m < 4; m++)
+        for (int n = m; n < 4; n++)
+          memcpy(c.data() + (l * 10 + SY(m, n)) * n2d, in + ((l * 4 + m) * 4 + n) * n2d,
+                 sizeof(double) * (size_t)n2d);
+    CK(cudaMemcpyAsync(s->conn, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return GRMHD_OK;
+  }
+  std::vector<double> g((size_t)(G_NCOMP * n2d));
+  for (int m = 0; m < 4; m++)
+    for (int n = m; n < 4; n++) {
+      memcpy(g.data() + (G_GCOV + SY(m, n)) * n2d, in + (m * 4 + n) * n2d, sizeof(double) * (size_t)n2d);
+      memcpy(g.data() + (G_GCON + SY(m, n)) * n2d, in + (16 + m * 4 + n) * n2d,
+             sizeof(double) * (size_t)n2d);
+    }
+  memcpy(g.data() + G_GDET * n2d, in + 32 * n2d, sizeof(double) * (size_t)n2d);
+  memcpy(g.data() + G_ALPHA * n2d, in + 33 * n2d, sizeof(double) * (size_t)n2d);
+  CK(cudaMemcpyAsync(s->geom + (long long)loc * G_NCOMP * n2d, g.data(), sizeof(double) * g.size(),
+                     cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_profile(grmhd_sim *s, int enable) {
+  if (!s) return GRMHD_ERR_INVALID;
+  s->prof_on = enable ? 1 : 0;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_get_profile(grmhd_sim *s, grmhd_profile_data *out, int reset) {
+  if (!s || !out) return GRMHD_ERR_INVALID;
+  CK(cudaStreamSynchronize(s->st));
+  collect_profile(s);
+  for (int c = 0; c < GRMHD_NKCLASS; c++) {
+    out->ms[c] = s->prof_ms[c];
+    out->launches[c] = s->launches[c];
+  }
+  if (reset) {
+    for (int c = 0; c < GRMHD_NKCLASS; c++) {
+      s->prof_ms[c] = 0.0;
+      s->launches[c] = 0;
+    }
+  }
+  return GRMHD_OK;
+}
+
+extern "C" const char *grmhd_strerror(int code) {
+  switch (code) {
+    case GRMHD_OK: return "ok";
+    case GRMHD_ERR_INVALID: return "invalid argument";
+    case GRMHD_ERR_NOMEM: return "device allocation failed";
+    case GRMHD_ERR_CUDA: return "CUDA runtime error";
+    case GRMHD_ERR_INVERSION: return "failed zone with no valid neighbour";
+    case GRMHD_ERR_DT: return "no finite time step";
+    default: return "unknown error";
+  }
+}

@@ -1,0 +1,349 @@
+// grmhd_dev.cuh -- device-side data layout and per-point physics of the
+// GB300 GRMHD step (HARM scheme as implemented by iharm3D, arXiv:2110.10191).
+//
+// Layout (HBM): every zone-centred or face-centred field is a
+// structure-of-arrays of float64, field[v][k][j][i] with i fastest and 3 ghost
+// layers per side.  Face arrays use the index of the zone whose low face
+// they sit on (face i-1/2 of zone i).  Geometry is X3-independent (both
+// supported metrics are), so it lives in 2D [comp][j][i] arrays that stay
+// resident in L2 for the whole step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace grmhd {
+
+constexpr int NV = 8;
+constexpr int NG = 3;
+enum { RHO = 0, UU, U1, U2, U3, B1, B2, B3 };
+
+// Packed symmetric 4x4 index: (0,0)0 (0,1)1 (0,2)2 (0,3)3 (1,1)4 (1,2)5
+// (1,3)6 (2,2)7 (2,3)8 (3,3)9.
+__host__ __device__ constexpr int SY(int m, int n) {
+  return (m <= n) ? (m * 4 - (m * (m - 1)) / 2 + (n - m)) : (n * 4 - (n * (n - 1)) / 2 + (m - n));
+}
+
+// geometry components of one location
+constexpr int G_GCOV = 0;    // 10 packed g_{mu nu}
+constexpr int G_GCON = 10;   // 10 packed g^{mu nu}
+constexpr int G_GDET = 20;   // sqrt(-g)
+constexpr int G_ALPHA = 21;  // lapse 1/sqrt(-g^{tt})
+constexpr int G_NCOMP = 22;
+constexpr int C_NCOMP = 40;  // connection Gamma^l_{(m n)}: l*10 + SY(m,n)
+enum { LOC_CENT = 0, LOC_FACE1 = 1, LOC_FACE2 = 2, NLOC = 3 };
+
+// bound constants (paper, "Implementation Notes", list of bounds)
+constexpr double FL_RHO_K = 1.0e-6;
+constexpr double FL_U_K = 1.0e-8;
+constexpr double FL_SIGMA = 400.0;
+constexpr double FL_BETA = 2.5e-5;
+constexpr double FL_TEMP = 100.0;
+constexpr double FL_GAMMA = 50.0;
+enum { FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32 };
+enum { PF_OK = 0, PF_NOCONV = 1, PF_W = 2, PF_VSQ = 3, PF_RHO = 4, PF_U = 5, PF_D = 6 };
+
+struct Dims {
+  int n[3];   // interior zones
+  int s[3];   // with ghosts
+  long long ntot;
+  long long n2d;  // s[0]*s[1]
+};
+
+__device__ __forceinline__ long long zid(const Dims &D, int i, int j, int k) {
+  return ((long long)k * D.s[1] + j) * D.s[0] + i;
+}
+
+struct Geo {
+  double gcov[10], gcon[10], gdet, alpha;
+};
+
+__device__ __forceinline__ void load_geo(const double *__restrict__ g, long long n2d, long long ij,
+                                         Geo &G) {
+#pragma unroll
+  for (int c = 0; c < 10; c++) G.gcov[c] = __ldg(g + (G_GCOV + c) * n2d + ij);
+#pragma unroll
+  for (int c = 0; c < 10; c++) G.gcon[c] = __ldg(g + (G_GCON + c) * n2d + ij);
+  G.gdet = __ldg(g + G_GDET * n2d + ij);
+  G.alpha = __ldg(g + G_ALPHA * n2d + ij);
+}
+
+// ---------------------------------------------------------------------------
+// Fluid state u^mu, u_mu, b^mu, b_mu, b^2 of one primitive vector.
+// u^t = gamma/alpha, u^i = utilde^i - gamma alpha g^{ti}; u_i = g_ij utilde^j,
+// u_t = -alpha gamma + g_tj utilde^j (the normal observer has n_i = 0);
+// b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t.
+// ---------------------------------------------------------------------------
+struct FState {
+  double ucon[4], ucov[4], bcon[4], bcov[4], bsq;
+};
+
+__device__ __forceinline__ void fluid_state(const double P[NV], const Geo &G, FState &s) {
+  const double v1 = P[U1], v2 = P[U2], v3 = P[U3];
+  const double l1 = G.gcov[SY(1, 1)] * v1 + G.gcov[SY(1, 2)] * v2 + G.gcov[SY(1, 3)] * v3;
+  const double l2 = G.gcov[SY(1, 2)] * v1 + G.gcov[SY(2, 2)] * v2 + G.gcov[SY(2, 3)] * v3;
+  const double l3 = G.gcov[SY(1, 3)] * v1 + G.gcov[SY(2, 3)] * v2 + G.gcov[SY(3, 3)] * v3;
+  const double gam = sqrt(1.0 + (l1 * v1 + l2 * v2 + l3 * v3));
+  const double ga = gam * G.alpha;
+  s.ucon[0] = gam / G.alpha;
+  s.ucon[1] = v1 - ga * G.gcon[SY(0, 1)];
+  s.ucon[2] = v2 - ga * G.gcon[SY(0, 2)];
+  s.ucon[3] = v3 - ga * G.gcon[SY(0, 3)];
+  s.ucov[0] = -ga + (G.gcov[SY(0, 1)] * v1 + G.gcov[SY(0, 2)] * v2 + G.gcov[SY(0, 3)] * v3);
+  s.ucov[1] = l1;
+  s.ucov[2] = l2;
+  s.ucov[3] = l3;
+  const double bt = P[B1] * l1 + P[B2] * l2 + P[B3] * l3;
+  const double iut = G.alpha / gam;  // 1/u^t
+  s.bcon[0] = bt;
+  s.bcon[1] = (P[B1] + bt * s.ucon[1]) * iut;
+  s.bcon[2] = (P[B2] + bt * s.ucon[2]) * iut;
+  s.bcon[3] = (P[B3] + bt * s.ucon[3]) * iut;
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    double a = 0.0;
+#pragma unroll
+    for (int n = 0; n < 4; n++) a += G.gcov[SY(m, n)] * s.bcon[n];
+    s.bcov[m] = a;
+  }
+  s.bsq = s.bcon[0] * s.bcov[0] + s.bcon[1] * s.bcov[1] + s.bcon[2] * s.bcov[2] +
+          s.bcon[3] * s.bcov[3];
+}
+
+// sqrt(-g)-weighted conserved densities (dir 0) or fluxes (dir 1..3):
+// rho u^d ; T^d_t + rho u^d ; T^d_i ; b^j u^d - b^d u^j, with
+// T^d_nu = (rho + u + p + b^2) u^d u_nu + (p + b^2/2) delta^d_nu - b^d b_nu.
+__device__ __forceinline__ void prim_flux(const double P[NV], const FState &s, const Geo &G,
+                                          double gam, int dir, double F[NV]) {
+  const double pg = (gam - 1.0) * P[UU];
+  const double w = P[RHO] + P[UU] + pg + s.bsq;
+  const double pt = pg + 0.5 * s.bsq;
+  const double wu = w * s.ucon[dir];
+  const double bd = s.bcon[dir];
+  double T[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; nu++) T[nu] = wu * s.ucov[nu] - bd * s.bcov[nu];
+  T[dir] += pt;
+  const double mflux = P[RHO] * s.ucon[dir];
+  F[RHO] = G.gdet * mflux;
+  F[UU] = G.gdet * (T[0] + mflux);
+  F[U1] = G.gdet * T[1];
+  F[U2] = G.gdet * T[2];
+  F[U3] = G.gdet * T[3];
+  const double ud = s.ucon[dir];
+  F[B1] = G.gdet * (s.bcon[1] * ud - bd * s.ucon[1]);
+  F[B2] = G.gdet * (s.bcon[2] * ud - bd * s.ucon[2]);
+  F[B3] = G.gdet * (s.bcon[3] * ud - bd * s.ucon[3]);
+}
+
+// Fast-magnetosonic coordinate speeds along dir: roots v of
+// (k.u)^2 = cms2 (k.k + (k.u)^2) for k_mu = delta^dir_mu - v delta^t_mu,
+// cms2 = cs2 + va2 - cs2 va2; a negative discriminant counts as zero.
+__device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, const Geo &G,
+                                          double gam, int dir, double &vmax, double &vmin) {
+  const double ef = P[RHO] + gam * P[UU];
+  const double ee = s.bsq + ef;
+  const double va2 = s.bsq / ee;
+  const double cs2 = gam * (gam - 1.0) * P[UU] / ef;
+  const double cms2 = cs2 + va2 - cs2 * va2;
+  const double Asq = G.gcon[SY(dir, dir)];
+  const double Bsq = G.gcon[SY(0, 0)];
+  const double AB = G.gcon[SY(0, dir)];
+  const double Au = s.ucon[dir];
+  const double Bu = s.ucon[0];
+  const double AuBu = Au * Bu;
+  const double qa = Bu * Bu - (Bsq + Bu * Bu) * cms2;
+  const double qb = -2.0 * (AuBu - (AB + AuBu) * cms2);
+  const double qc = Au * Au - (Asq + Au * Au) * cms2;
+  double disc = qb * qb - 4.0 * qa * qc;
+  disc = (disc > 0.0) ? sqrt(disc) : 0.0;
+  const double i2a = 0.5 / qa;
+  const double v1 = (-qb + disc) * i2a;
+  const double v2 = (-qb - disc) * i2a;
+  vmax = fmax(v1, v2);
+  vmin = fmin(v1, v2);
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction
+// ---------------------------------------------------------------------------
+// MC limited slope of x1 with neighbours x0, x2.
+__device__ __forceinline__ double mc_slope(double x0, double x1, double x2) {
+  const double dm = x1 - x0, dp = x2 - x1;
+  if (!(dm * dp > 0.0)) return 0.0;
+  const double dc = 0.5 * (dm + dp);
+  const double m = fmin(fmin(fabs(2.0 * dm), fabs(dc)), fabs(2.0 * dp));
+  return (dc > 0.0) ? m : -m;
+}
+
+// Jiang-Shu WENO5 value at the high face of the middle zone of a..e
+// (cell averages; epsilon 1e-26, weights d_k/(eps + beta_k)^2).
+__device__ __forceinline__ double weno5_hi(double a, double b, double c, double d, double e) {
+  const double eps = 1.0e-26;
+  const double t0 = a - 2.0 * b + c, t1 = b - 2.0 * c + d, t2 = c - 2.0 * d + e;
+  const double s0 = a - 4.0 * b + 3.0 * c, s1 = b - d, s2 = 3.0 * c - 4.0 * d + e;
+  const double b0 = (13.0 / 12.0) * t0 * t0 + 0.25 * s0 * s0;
+  const double b1 = (13.0 / 12.0) * t1 * t1 + 0.25 * s1 * s1;
+  const double b2 = (13.0 / 12.0) * t2 * t2 + 0.25 * s2 * s2;
+  const double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+  const double q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+  // alpha_k = d_k / q_k ; common denominator q0 q1 q2
+  const double a0 = 0.1 * (q1 * q2), a1 = 0.6 * (q0 * q2), a2 = 0.3 * (q0 * q1);
+  const double p0 = (2.0 * a - 7.0 * b + 11.0 * c) * (1.0 / 6.0);
+  const double p1 = (-b + 5.0 * c + 2.0 * d) * (1.0 / 6.0);
+  const double p2 = (2.0 * c + 5.0 * d - e) * (1.0 / 6.0);
+  return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------------------
+// 1D_W primitive recovery (Noble et al. 2006) in W' = W - D.
+// Iteration rule: guess W' from the guess primitives (clamped >= 0); Newton
+// until a step <= 1e-8 W, then 2 more steps; at most 16 (+2) iterations; a
+// step below W' = 0 halves W'; an iterate with v^2 > 1 - 1e-10 is replaced by
+// the bisection of the bracket known from sign(f), or doubles W while no
+// upper end is known.
+// ---------------------------------------------------------------------------
+constexpr int INV_MAXIT = 16;
+constexpr int INV_EXTRA = 2;
+constexpr double INV_TOL = 1.0e-8;
+constexpr double INV_VSQ_MAX = 1.0 - 1.0e-10;
+
+__device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, double gam,
+                                          const double Pg[NV], double P[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) P[v] = Pg[v];
+  const double igd = 1.0 / G.gdet;
+  const double al = G.alpha;
+  P[B1] = U[B1] * igd;
+  P[B2] = U[B2] * igd;
+  P[B3] = U[B3] * igd;
+  const double D = U[RHO] * al * igd;
+  if (!(D > 0.0)) return PF_D;
+  const double n1 = al * P[B1], n2 = al * P[B2], n3 = al * P[B3];  // normal-frame field
+  const double aig = al * igd;
+  const double Q1 = aig * U[U1], Q2 = aig * U[U2], Q3 = aig * U[U3];
+  // Q'.n = Q.n + D without the rest-mass cancellation
+  const double Qpn = (U[UU] - (1.0 - al) * U[RHO]) * igd -
+                     al * (Q1 * G.gcon[SY(0, 1)] + Q2 * G.gcon[SY(0, 2)] + Q3 * G.gcon[SY(0, 3)]);
+  // spatial inverse metric gamma^{ij} = g^{ij} - g^{it} g^{jt} / g^{tt}
+  const double ig00 = 1.0 / G.gcon[SY(0, 0)];
+  const double c1 = G.gcon[SY(0, 1)], c2 = G.gcon[SY(0, 2)], c3 = G.gcon[SY(0, 3)];
+  const double h11 = G.gcon[SY(1, 1)] - c1 * c1 * ig00, h12 = G.gcon[SY(1, 2)] - c1 * c2 * ig00;
+  const double h13 = G.gcon[SY(1, 3)] - c1 * c3 * ig00, h22 = G.gcon[SY(2, 2)] - c2 * c2 * ig00;
+  const double h23 = G.gcon[SY(2, 3)] - c2 * c3 * ig00, h33 = G.gcon[SY(3, 3)] - c3 * c3 * ig00;
+  const double Qt1 = h11 * Q1 + h12 * Q2 + h13 * Q3;
+  const double Qt2 = h12 * Q1 + h22 * Q2 + h23 * Q3;
+  const double Qt3 = h13 * Q1 + h23 * Q2 + h33 * Q3;
+  const double Qtsq = Qt1 * Q1 + Qt2 * Q2 + Qt3 * Q3;
+  const double QdB = Q1 * n1 + Q2 * n2 + Q3 * n3;
+  const double QdB2 = QdB * QdB;
+  const double Bsq = n1 * (G.gcov[SY(1, 1)] * n1 + G.gcov[SY(1, 2)] * n2 + G.gcov[SY(1, 3)] * n3) +
+                     n2 * (G.gcov[SY(1, 2)] * n1 + G.gcov[SY(2, 2)] * n2 + G.gcov[SY(2, 3)] * n3) +
+                     n3 * (G.gcov[SY(1, 3)] * n1 + G.gcov[SY(2, 3)] * n2 + G.gcov[SY(3, 3)] * n3);
+  // guess
+  const double g1 = Pg[U1], g2 = Pg[U2], g3 = Pg[U3];
+  const double qsq = g1 * (G.gcov[SY(1, 1)] * g1 + G.gcov[SY(1, 2)] * g2 + G.gcov[SY(1, 3)] * g3) +
+                     g2 * (G.gcov[SY(1, 2)] * g1 + G.gcov[SY(2, 2)] * g2 + G.gcov[SY(2, 3)] * g3) +
+                     g3 * (G.gcov[SY(1, 3)] * g1 + G.gcov[SY(2, 3)] * g2 + G.gcov[SY(3, 3)] * g3);
+  double Wp = (Pg[RHO] + gam * Pg[UU]) * (1.0 + qsq) - D;
+  if (Wp < 0.0) Wp = 0.0;
+
+  const double gf = (gam - 1.0) / gam;
+  int converged = 0, extra = 0, invalid = 0, have_hi = 0;
+  double lo = 0.0, hi = 0.0;
+  for (int it = 0; it < INV_MAXIT + INV_EXTRA; it++) {
+    const double W = Wp + D;
+    const double W2 = W * W;
+    const double BW = Bsq + W;
+    const double iBW2W2 = 1.0 / (BW * BW * W2);
+    double vsq = (Qtsq * W2 + QdB2 * (Bsq + 2.0 * W)) * iBW2W2;
+    invalid = 0;
+    if (vsq > INV_VSQ_MAX) {
+      lo = fmax(lo, Wp);
+      Wp = have_hi ? 0.5 * (lo + hi) : Wp + W;
+      invalid = 1;
+      if (converged || it + 1 >= INV_MAXIT) break;
+      continue;
+    }
+    if (vsq < 0.0) vsq = 0.0;
+    const double omv = 1.0 - vsq;
+    const double sq = sqrt(omv);
+    const double wmr = Wp * omv - D * vsq * sq / (1.0 + sq);
+    const double iW2 = 1.0 / W2;
+    const double f = Qpn + Wp - gf * wmr + 0.5 * (1.0 + vsq) * Bsq - 0.5 * QdB2 * iW2;
+    if (f > 0.0) {
+      hi = have_hi ? fmin(hi, Wp) : Wp;
+      have_hi = 1;
+    } else {
+      lo = fmax(lo, Wp);
+    }
+    const double dv = -2.0 * (Qtsq * W2 * W + QdB2 * (3.0 * W2 + 3.0 * W * Bsq + Bsq * Bsq)) *
+                      (iBW2W2 / (BW * W));
+    const double dpdW = gf * (omv + dv * (0.5 * D / sq - W));
+    const double df = 1.0 - dpdW + 0.5 * Bsq * dv + QdB2 * iW2 / W;
+    double Wn = Wp - f / df;
+    if (Wn < 0.0) Wn = 0.5 * Wp;
+    if (converged) {
+      Wp = Wn;
+      if (++extra >= INV_EXTRA) break;
+      continue;
+    }
+    if (fabs(Wn - Wp) <= INV_TOL * fabs(W)) converged = 1;
+    Wp = Wn;
+    if (!converged && it + 1 >= INV_MAXIT) break;
+  }
+  const double W = Wp + D;
+  if (!converged) return PF_NOCONV;
+  if (!(W > 0.0) || !isfinite(W)) return PF_W;
+  const double W2 = W * W;
+  const double BW = Bsq + W;
+  double vsq = (Qtsq * W2 + QdB2 * (Bsq + 2.0 * W)) / (BW * BW * W2);
+  if (!(vsq < 1.0) || invalid) return PF_VSQ;
+  if (vsq < 0.0) vsq = 0.0;
+  const double sq = sqrt(1.0 - vsq);
+  const double rho = D * sq;
+  const double uu = (Wp * (1.0 - vsq) - D * vsq * sq / (1.0 + sq)) / gam;
+  if (!(rho > 0.0)) return PF_RHO;
+  if (uu < 0.0) return PF_U;
+  const double fac = 1.0 / (sq * BW);  // gamma / (W + B^2)
+  const double qbw = QdB / W;
+  P[RHO] = rho;
+  P[UU] = uu;
+  P[U1] = fac * (Qt1 + qbw * n1);
+  P[U2] = fac * (Qt2 + qbw * n2);
+  P[U3] = fac * (Qt3 + qbw * n3);
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Bounds: Lorentz-factor cap first (it changes b^2), then rho and u raised in
+// the fluid frame in the order of the paper's list; every bound holds on exit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double rho_fl,
+                                            double u_fl, double gam) {
+  int fl = 0;
+  const double v1 = P[U1], v2 = P[U2], v3 = P[U3];
+  const double qsq = v1 * (G.gcov[SY(1, 1)] * v1 + G.gcov[SY(1, 2)] * v2 + G.gcov[SY(1, 3)] * v3) +
+                     v2 * (G.gcov[SY(1, 2)] * v1 + G.gcov[SY(2, 2)] * v2 + G.gcov[SY(2, 3)] * v3) +
+                     v3 * (G.gcov[SY(1, 3)] * v1 + G.gcov[SY(2, 3)] * v2 + G.gcov[SY(3, 3)] * v3);
+  if (sqrt(1.0 + qsq) > FL_GAMMA) {
+    const double f = sqrt((FL_GAMMA * FL_GAMMA - 1.0) / qsq);
+    P[U1] *= f;
+    P[U2] *= f;
+    P[U3] *= f;
+    fl |= FF_GAMMA;
+  }
+  FState s;
+  fluid_state(P, G, s);
+  if (P[RHO] < rho_fl) { P[RHO] = rho_fl; fl |= FF_RHO_GEOM; }
+  if (P[UU] < u_fl) { P[UU] = u_fl; fl |= FF_U_GEOM; }
+  const double rs = s.bsq / FL_SIGMA;
+  if (P[RHO] < rs) { P[RHO] = rs; fl |= FF_SIGMA; }
+  const double ub = FL_BETA * s.bsq / (2.0 * (gam - 1.0));
+  if (P[UU] < ub) { P[UU] = ub; fl |= FF_BETA; }
+  const double rt = P[UU] / FL_TEMP;
+  if (P[RHO] < rt) { P[RHO] = rt; fl |= FF_TEMP; }
+  return fl;
+}
+
+}  // namespace grmhd

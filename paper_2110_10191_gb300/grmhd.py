@@ -1,0 +1,268 @@
+"""ctypes binding of libgrmhd.so (include/grmhd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Host arrays are numpy float64; device arrays may be torch CUDA
+tensors (their data_ptr() is passed with on_device=1), and a torch CUDA
+stream may be passed as the simulation's stream.  There is no CPU
+fallback: if the library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+NPRIM = 8
+NG = 3
+GRMHD_OK = 0
+ERRORS = {-1: "invalid argument", -2: "device allocation failed", -3: "CUDA runtime error",
+          -4: "failed zone with no valid neighbour", -5: "no finite time step"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GrmhdError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s: %s (%d)" % (where, ERRORS.get(code, "unknown error"), code))
+        self.code = code
+
+
+class grmhd_grid(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+                ("x1min", ctypes.c_double), ("x1max", ctypes.c_double),
+                ("x2min", ctypes.c_double), ("x2max", ctypes.c_double),
+                ("x3min", ctypes.c_double), ("x3max", ctypes.c_double)]
+
+
+class grmhd_metric(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("hslope", ctypes.c_double)]
+
+
+class grmhd_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("t_final", ctypes.c_double),
+                ("recon", ctypes.c_int), ("floors_on", ctypes.c_int),
+                ("bc", (ctypes.c_int * 2) * 3)]
+
+
+KCLASSES = ["flux", "dt", "ct", "update", "fixup", "bounds", "other"]
+
+
+class grmhd_profile_data(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_longlong * 7)]
+
+
+class grmhd_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_longlong),
+                ("inv_failures", ctypes.c_longlong), ("floor_hits", ctypes.c_longlong),
+                ("unrecoverable", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_ghost",
+           "grmhd_get_prims", "grmhd_step", "grmhd_get_stats", "grmhd_set_time",
+           "grmhd_predictor", "grmhd_get_fluxes", "grmhd_next_dt", "grmhd_get_flags",
+           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_profile", "grmhd_get_profile", "grmhd_fp64_peak",
+           "grmhd_strerror"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgrmhd.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libgrmhd.so is not built (%s); run paper_2110_10191_gb300.build" % path)
+        L = ctypes.CDLL(path)
+        vp, i, d, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER
+        L.grmhd_create.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params), vp, P(vp)]
+        L.grmhd_destroy.argtypes = [vp]
+        L.grmhd_set_prims.argtypes = [vp, vp, i]
+        L.grmhd_set_prims_ghost.argtypes = [vp, vp, i]
+        L.grmhd_get_prims.argtypes = [vp, vp, i, i]
+        L.grmhd_step.argtypes = [vp, i, P(grmhd_stats)]
+        L.grmhd_get_stats.argtypes = [vp, P(grmhd_stats)]
+        L.grmhd_set_time.argtypes = [vp, d, d, ctypes.c_longlong]
+        L.grmhd_predictor.argtypes = [vp]
+        L.grmhd_get_fluxes.argtypes = [vp, vp, vp]
+        L.grmhd_next_dt.argtypes = [vp, P(d)]
+        L.grmhd_get_flags.argtypes = [vp, vp, vp]
+        L.grmhd_get_geometry.argtypes = [vp, i, vp]
+        L.grmhd_set_geometry.argtypes = [vp, i, vp]
+        L.grmhd_profile.argtypes = [vp, i]
+        L.grmhd_get_profile.argtypes = [vp, P(grmhd_profile_data), i]
+        L.grmhd_fp64_peak.argtypes = [ctypes.c_longlong, P(d)]
+        L.grmhd_strerror.argtypes = [i]
+        L.grmhd_strerror.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "grmhd_strerror":
+                getattr(L, name).restype = i
+        _lib = L
+        return L
+
+
+def _check(rc, where):
+    if rc != GRMHD_OK:
+        raise GrmhdError(rc, where)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def fp64_peak(iters: int = 1 << 16) -> float:
+    """Measured FP64 FMA throughput (FLOP/s) of the current device."""
+    out = ctypes.c_double()
+    _check(load().grmhd_fp64_peak(int(iters), ctypes.byref(out)), "grmhd_fp64_peak")
+    return out.value
+
+
+class Sim:
+    """One GRMHD simulation held on the current CUDA device.
+
+    ``problem`` has the attributes of ``problems.Problem`` (n, xmin, xmax,
+    metric, a, hslope, gamma, cfl, t_final, recon, floors, bc)."""
+
+    def __init__(self, problem, stream=None):
+        self.L = load()
+        pr = problem
+        self.n = tuple(int(x) for x in pr.n)
+        self.s = tuple(x + 2 * NG for x in self.n)
+        g = grmhd_grid(self.n[0], self.n[1], self.n[2], pr.xmin[0], pr.xmax[0], pr.xmin[1],
+                       pr.xmax[1], pr.xmin[2], pr.xmax[2])
+        m = grmhd_metric(int(pr.metric), float(pr.a), float(pr.hslope))
+        p = grmhd_params()
+        p.gamma, p.cfl, p.t_final = float(pr.gamma), float(pr.cfl), float(pr.t_final)
+        p.recon, p.floors_on = int(pr.recon), int(pr.floors)
+        for d in range(3):
+            for s in range(2):
+                p.bc[d][s] = int(pr.bc[d][s])
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.h = ctypes.c_void_p()
+        _check(self.L.grmhd_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
+                                   ctypes.c_void_p(stream or 0), ctypes.byref(self.h)),
+               "grmhd_create")
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.grmhd_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- state ----
+    def set_prims(self, P) -> None:
+        n1, n2, n3 = self.n
+        shape = tuple(P.shape)
+        ptr, dev = _ptr(P)
+        if shape == (NPRIM, n3, n2, n1):
+            _check(self.L.grmhd_set_prims(self.h, ptr, dev), "grmhd_set_prims")
+        elif shape == (NPRIM,) + self.s[::-1]:
+            _check(self.L.grmhd_set_prims_ghost(self.h, ptr, dev), "grmhd_set_prims_ghost")
+        else:
+            raise ValueError("bad primitive shape %s" % (shape,))
+
+    def get_prims(self, with_ghosts: bool = False, out=None):
+        shape = (NPRIM,) + (self.s[::-1] if with_ghosts else self.n[::-1])
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        if tuple(out.shape) != shape:
+            raise ValueError("bad output shape")
+        ptr, dev = _ptr(out)
+        _check(self.L.grmhd_get_prims(self.h, ptr, int(with_ghosts), dev), "grmhd_get_prims")
+        return out
+
+    def step(self, nsteps: int = 1, sync: bool = True):
+        if sync:
+            st = grmhd_stats()
+            _check(self.L.grmhd_step(self.h, int(nsteps), ctypes.byref(st)), "grmhd_step")
+            return st.as_dict()
+        _check(self.L.grmhd_step(self.h, int(nsteps), None), "grmhd_step")
+        return None
+
+    def stats(self):
+        st = grmhd_stats()
+        _check(self.L.grmhd_get_stats(self.h, ctypes.byref(st)), "grmhd_get_stats")
+        return st.as_dict()
+
+    def set_time(self, t: float, dt_prev: float, steps: int = 0) -> None:
+        _check(self.L.grmhd_set_time(self.h, float(t), float(dt_prev), int(steps)), "grmhd_set_time")
+
+    # ---- stage-level access ----
+    def predictor(self) -> None:
+        _check(self.L.grmhd_predictor(self.h), "grmhd_predictor")
+
+    def fluxes(self):
+        F = np.zeros((3, NPRIM) + self.s[::-1])
+        ct = np.zeros(3)
+        _check(self.L.grmhd_get_fluxes(self.h, F.ctypes.data, ct.ctypes.data), "grmhd_get_fluxes")
+        return F, ct
+
+    def next_dt(self) -> float:
+        out = ctypes.c_double()
+        _check(self.L.grmhd_next_dt(self.h, ctypes.byref(out)), "grmhd_next_dt")
+        return out.value
+
+    def flags(self):
+        n1, n2, n3 = self.n
+        pf = np.zeros((n3, n2, n1), dtype=np.int32)
+        ff = np.zeros((n3, n2, n1), dtype=np.int32)
+        _check(self.L.grmhd_get_flags(self.h, pf.ctypes.data, ff.ctypes.data), "grmhd_get_flags")
+        return pf, ff
+
+    def set_geom(self, loc: int, arr) -> None:
+        """Load geometry in the layout of geom(loc) (a tabulated metric)."""
+        nc = 64 if loc == 3 else 34
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        if a.shape != (nc, self.s[1], self.s[0]):
+            raise ValueError("bad geometry shape %s" % (a.shape,))
+        _check(self.L.grmhd_set_geometry(self.h, int(loc), a.ctypes.data), "grmhd_set_geometry")
+
+    def profile(self, enable: bool = True) -> None:
+        _check(self.L.grmhd_profile(self.h, int(enable)), "grmhd_profile")
+
+    def get_profile(self, reset: bool = False):
+        """{class: (ms, launches)} since the last reset."""
+        pd = grmhd_profile_data()
+        _check(self.L.grmhd_get_profile(self.h, ctypes.byref(pd), int(reset)), "grmhd_get_profile")
+        return {c: (pd.ms[q], pd.launches[q]) for q, c in enumerate(KCLASSES)}
+
+    def geom(self, loc: int) -> np.ndarray:
+        nc = 64 if loc == 3 else 34
+        out = np.zeros((nc, self.s[1], self.s[0]))
+        _check(self.L.grmhd_get_geometry(self.h, int(loc), out.ctypes.data), "grmhd_get_geometry")
+        return out
