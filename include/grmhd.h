@@ -193,6 +193,33 @@ int grmhd_get_profile(grmhd_sim *sim, grmhd_profile_data *out, int reset);
  * the FP64-bound kernels. */
 int grmhd_fp64_peak(long long iters, double *flops);
 
+/* Face-flux stage without any device allocation (no counterpart in the
+ * paper: it exists for callers of this library that cannot allocate).
+ * Serving processes that have reserved all device memory up front, code
+ * running under a framework allocator that must not be bypassed, and host
+ * threads that may not allocate while other work is in flight cannot call
+ * cudaMalloc; this call lets them run the flux stage (reconstruction + LLF
+ * fluxes, boundary flux fixes, flux-CT) of the step on buffers they own.
+ *   P:    device, primitives with ghosts [8][n3+6][n2+6][n1+6], ghosts
+ *         already filled (e.g. grmhd_get_prims(..., with_ghosts=1, ...)).
+ *   F:    device, output [3][8][n3+6][n2+6][n1+6], as grmhd_get_fluxes
+ *         fills it (entries outside the computed face ranges are zeroed).
+ *   ctop: host double[3] for the interior signal-speed maxima, or NULL;
+ *         when given, the call synchronises the stream to read them.
+ * Every intermediate (metric at centres and faces, EMFs, signal-speed
+ * maxima) lives in one file-scope device array of 64 MiB that every GPU
+ * loading this library holds until exit; the call rejects a grid needing
+ * more, i.e. 8 * (3 (n1+6)(n2+6)(n3+6) + 108 (n1+6)(n2+6)) bytes beyond
+ * 64 MiB, with GRMHD_ERR_INVALID.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents: calls that overlap on the
+ * GPU race and must be serialised. */
+int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *metric,
+                         const grmhd_params *params, const double *P, double *F,
+                         double *ctop, void *stream);
+
 /* Name of an error code. */
 const char *grmhd_strerror(int code);
 

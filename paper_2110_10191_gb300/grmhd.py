@@ -68,7 +68,7 @@ class grmhd_stats(ctypes.Structure):
 EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_ghost",
            "grmhd_get_prims", "grmhd_step", "grmhd_get_stats", "grmhd_set_time",
            "grmhd_predictor", "grmhd_get_fluxes", "grmhd_next_dt", "grmhd_get_flags",
-           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_profile", "grmhd_get_profile", "grmhd_fp64_peak",
+           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_fluxes_noalloc", "grmhd_profile", "grmhd_get_profile", "grmhd_fp64_peak",
            "grmhd_strerror"]
 
 
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_get_flags.argtypes = [vp, vp, vp]
         L.grmhd_get_geometry.argtypes = [vp, i, vp]
         L.grmhd_set_geometry.argtypes = [vp, i, vp]
+        L.grmhd_fluxes_noalloc.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params), vp,
+                                           vp, vp, vp]
         L.grmhd_profile.argtypes = [vp, i]
         L.grmhd_get_profile.argtypes = [vp, P(grmhd_profile_data), i]
         L.grmhd_fp64_peak.argtypes = [ctypes.c_longlong, P(d)]
@@ -138,6 +140,38 @@ def fp64_peak(iters: int = 1 << 16) -> float:
     out = ctypes.c_double()
     _check(load().grmhd_fp64_peak(int(iters), ctypes.byref(out)), "grmhd_fp64_peak")
     return out.value
+
+
+def _structs(pr):
+    g = grmhd_grid(int(pr.n[0]), int(pr.n[1]), int(pr.n[2]), pr.xmin[0], pr.xmax[0], pr.xmin[1],
+                   pr.xmax[1], pr.xmin[2], pr.xmax[2])
+    m = grmhd_metric(int(pr.metric), float(pr.a), float(pr.hslope))
+    p = grmhd_params()
+    p.gamma, p.cfl, p.t_final = float(pr.gamma), float(pr.cfl), float(pr.t_final)
+    p.recon, p.floors_on = int(pr.recon), int(pr.floors)
+    for d in range(3):
+        for s in range(2):
+            p.bc[d][s] = int(pr.bc[d][s])
+    return g, m, p
+
+
+def fluxes_noalloc(problem, P, F, stream=None):
+    """Flux stage of `problem`'s grid on caller-owned device tensors, with no
+    device allocation (see grmhd_fluxes_noalloc in include/grmhd.h).
+    P: device [8][n3+6][n2+6][n1+6] with ghosts filled; F: device
+    [3][8][n3+6][n2+6][n1+6] output.  Returns the signal-speed maxima."""
+    g, m, p = _structs(problem)
+    pp, pdev = _ptr(P)
+    fp, fdev = _ptr(F)
+    if not (pdev and fdev):
+        raise ValueError("P and F must be device tensors")
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    ct = np.zeros(3)
+    _check(load().grmhd_fluxes_noalloc(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p), pp, fp,
+                                       ct.ctypes.data, ctypes.c_void_p(stream or 0)),
+           "grmhd_fluxes_noalloc")
+    return ct
 
 
 class Sim:
