@@ -164,14 +164,15 @@ int grmhd_get_geometry(grmhd_sim *sim, int loc, double *out);
 int grmhd_set_geometry(grmhd_sim *sim, int loc, const double *in);
 
 /* Kernel classes of the step, for grmhd_get_profile(). */
-#define GRMHD_K_FLUX 0    /* reconstruction + LLF face fluxes (3 launches a stage) */
+#define GRMHD_K_FLUX 0    /* LLF face fluxes from reconstructed states (3 launches a stage) */
 #define GRMHD_K_DT 1      /* CFL time step */
 #define GRMHD_K_CT 2      /* boundary flux fixes + flux-CT */
 #define GRMHD_K_UPDATE 3  /* conserved update + 1D_W inversion + bounds */
 #define GRMHD_K_FIXUP 4   /* fixup of failed zones */
 #define GRMHD_K_BOUNDS 5  /* ghost fill */
 #define GRMHD_K_OTHER 6   /* clock advance, signal-speed reset */
-#define GRMHD_NKCLASS 7
+#define GRMHD_K_RECON 7   /* MC / WENO5 reconstruction of face states (3 launches a stage) */
+#define GRMHD_NKCLASS 8
 
 typedef struct {
   double ms[GRMHD_NKCLASS];            /* summed device time per class */

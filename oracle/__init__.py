@@ -269,12 +269,13 @@ def recon(kind, x):
     return float(out[0]), float(out[1])
 
 
-PHASES = ["flux", "ct", "update", "fixup", "other"]
+PHASES = ["flux", "ct", "update", "fixup", "other", "recon"]
 
 
 def op_counts(reset: bool = False):
-    """Counting build: {phase: {add, mul, div, sqrt}} since the last reset."""
-    out = np.zeros(20)
+    """Counting build: {phase: {add, mul, div, sqrt}} since the last reset
+    (flux: face fluxes from the reconstructed states; recon: reconstruction)."""
+    out = np.zeros(24)
     lib(True).oracle_op_counts(_dp(out), int(reset))
     return {ph: {"add": out[4 * q], "mul": out[4 * q + 1], "div": out[4 * q + 2],
                  "sqrt": out[4 * q + 3]} for q, ph in enumerate(PHASES)}

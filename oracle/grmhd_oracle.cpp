@@ -46,9 +46,10 @@
 struct OpCounts {
   double add, mul, div, sqrt;
 };
-/* phases: 0 face fluxes, 1 boundary fixes + flux-CT, 2 update + inversion +
- * floors, 3 fixup, 4 anything else */
-static OpCounts g_phase_ops[5];
+/* phases: 0 face fluxes (from the reconstructed states), 1 boundary fixes +
+ * flux-CT, 2 update + inversion + floors, 3 fixup, 4 anything else,
+ * 5 reconstruction of the face states */
+static OpCounts g_phase_ops[6];
 static int g_phase = 4;
 #define g_ops g_phase_ops[g_phase]
 struct real {
@@ -629,7 +630,14 @@ static void get_fluxes(Sim *S, const std::vector<real> &P) {
       for (int j = lo[1]; j <= hi[1]; j++)
         for (int i = lo[0]; i <= hi[0]; i++) {
           real PL[NPRIM], PR[NPRIM], Fo[NPRIM];
+#ifdef ORACLE_COUNT
+          int saved = g_phase;
+          g_phase = 5;
+#endif
           face_states(S, P, d, i, j, k, PL, PR);
+#ifdef ORACLE_COUNT
+          g_phase = saved;
+#endif
           const GeomPt &g = S->geom[loc][IJ(S, i, j)];
           real ctop = llf_face(S, g, d, PL, PR, Fo);
           long id = IDX(S, i, j, k);
@@ -1354,12 +1362,12 @@ int oracle_is_counting(void) {
 #endif
 }
 
-/* add/sub, mul, div, sqrt counts per phase since the last reset, out[5][4]
- * (phases: fluxes, flux fixes + flux-CT, update + inversion + floors,
- * fixup, other); zeros in the plain build. */
-void oracle_op_counts(double out[20], int reset) {
+/* add/sub, mul, div, sqrt counts per phase since the last reset, out[6][4]
+ * (phases: face fluxes, flux fixes + flux-CT, update + inversion + floors,
+ * fixup, other, reconstruction); zeros in the plain build. */
+void oracle_op_counts(double out[24], int reset) {
 #ifdef ORACLE_COUNT
-  for (int p = 0; p < 5; p++) {
+  for (int p = 0; p < 6; p++) {
     out[4 * p + 0] = g_phase_ops[p].add;
     out[4 * p + 1] = g_phase_ops[p].mul;
     out[4 * p + 2] = g_phase_ops[p].div;
@@ -1368,7 +1376,7 @@ void oracle_op_counts(double out[20], int reset) {
   }
 #else
   (void)reset;
-  for (int q = 0; q < 20; q++) out[q] = 0.0;
+  for (int q = 0; q < 24; q++) out[q] = 0.0;
 #endif
 }
 

@@ -19,7 +19,7 @@ struct grmhd_sim {
   grmhd_metric metric;
   grmhd_params params;
   cudaStream_t st;
-  double *P, *Ph, *F[3], *emf;
+  double *P, *Ph, *F[3], *emf, *Lf, *Rf;
   double *geom, *conn, *floors;
   int *pflag, *fflag;
   Clock *clk;
@@ -95,7 +95,8 @@ static void free_all(grmhd_sim *s) {
     s->prof_ev = nullptr;
     s->ev_pool = nullptr;
   }
-  double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->geom, s->conn, s->floors};
+  double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->Lf, s->Rf, s->geom, s->conn,
+                 s->floors};
   for (double *p : d)
     if (p) cudaFree(p);
   if (s->pflag) cudaFree(s->pflag);
@@ -158,7 +159,8 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   const size_t fb = sizeof(double) * NV * (size_t)tot;
   bool ok = cudaMalloc(&s->P, fb) == cudaSuccess && cudaMalloc(&s->Ph, fb) == cudaSuccess &&
             cudaMalloc(&s->F[0], fb) == cudaSuccess && cudaMalloc(&s->F[1], fb) == cudaSuccess &&
-            cudaMalloc(&s->F[2], fb) == cudaSuccess &&
+            cudaMalloc(&s->F[2], fb) == cudaSuccess && cudaMalloc(&s->Lf, fb) == cudaSuccess &&
+            cudaMalloc(&s->Rf, fb) == cudaSuccess &&
             cudaMalloc(&s->emf, sizeof(double) * 3 * (size_t)tot) == cudaSuccess &&
             cudaMalloc(&s->geom, sizeof(double) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
             cudaMalloc(&s->conn, sizeof(double) * C_NCOMP * (size_t)D.n2d) == cudaSuccess &&
@@ -214,7 +216,10 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   A.D = D;
   A.gam = params->gamma;
   A.cfl = params->cfl;
-  for (int d = 0; d < 3; d++) A.dx[d] = G.dx[d];
+  for (int d = 0; d < 3; d++) {
+    A.dx[d] = G.dx[d];
+    A.idx[d] = 1.0 / G.dx[d];
+  }
   A.recon = params->recon;
   A.floors_on = params->floors_on;
   for (int d = 0; d < 3; d++)
@@ -240,8 +245,14 @@ static void enqueue_fluxes(grmhd_sim *s, const double *P) {
     ClassScope c(s, GRMHD_K_OTHER, 1);
     launch_ctop_reset(s->A, s->st);
   }
-  ClassScope c(s, GRMHD_K_FLUX, 3);
-  launch_fluxes(s->A, P, s->F, s->st);
+  for (int d = 0; d < 3; d++) {
+    {
+      ClassScope c(s, GRMHD_K_RECON, 1);
+      launch_recon(s->A, d, P, s->Lf, s->Rf, s->st);
+    }
+    ClassScope c(s, GRMHD_K_FLUX, 1);
+    launch_face(s->A, d, s->F[d], s->Lf, s->Rf, s->st);
+  }
 }
 
 static void enqueue_bounds(grmhd_sim *s, double *P) {
@@ -495,6 +506,10 @@ extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
     }
   memcpy(g.data() + G_GDET * n2d, in + 32 * n2d, sizeof(double) * (size_t)n2d);
   memcpy(g.data() + G_ALPHA * n2d, in + 33 * n2d, sizeof(double) * (size_t)n2d);
+  for (long long q = 0; q < n2d; q++) {
+    g[(size_t)(G_IALPHA * n2d + q)] = 1.0 / in[33 * n2d + q];
+    g[(size_t)(G_IGDET * n2d + q)] = 1.0 / in[32 * n2d + q];
+  }
   CK(cudaMemcpyAsync(s->geom + (long long)loc * G_NCOMP * n2d, g.data(), sizeof(double) * g.size(),
                      cudaMemcpyHostToDevice, s->st));
   CK(cudaStreamSynchronize(s->st));

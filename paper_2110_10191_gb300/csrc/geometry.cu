@@ -104,8 +104,11 @@ __global__ void k_geometry(GeomArgs A) {
         out[(G_GCOV + SY(m, n)) * n2d + ij] = g[m][n];
         out[(G_GCON + SY(m, n)) * n2d + ij] = gi[m][n];
       }
-    out[G_GDET * n2d + ij] = sqrt(fabs(det));
-    out[G_ALPHA * n2d + ij] = 1.0 / sqrt(-gi[0][0]);
+    const double gd = sqrt(fabs(det)), al = 1.0 / sqrt(-gi[0][0]);
+    out[G_GDET * n2d + ij] = gd;
+    out[G_ALPHA * n2d + ij] = al;
+    out[G_IALPHA * n2d + ij] = 1.0 / al;
+    out[G_IGDET * n2d + ij] = 1.0 / gd;
     if (loc != LOC_CENT) continue;
     // connection at the centre: derivatives along X1, X2 (X3: the metric does
     // not depend on it, so that derivative is exactly zero)

@@ -29,7 +29,9 @@ constexpr int G_GCOV = 0;    // 10 packed g_{mu nu}
 constexpr int G_GCON = 10;   // 10 packed g^{mu nu}
 constexpr int G_GDET = 20;   // sqrt(-g)
 constexpr int G_ALPHA = 21;  // lapse 1/sqrt(-g^{tt})
-constexpr int G_NCOMP = 22;
+constexpr int G_IALPHA = 22; // 1/lapse
+constexpr int G_IGDET = 23;  // 1/sqrt(-g)
+constexpr int G_NCOMP = 24;
 constexpr int C_NCOMP = 40;  // connection Gamma^l_{(m n)}: l*10 + SY(m,n)
 enum { LOC_CENT = 0, LOC_FACE1 = 1, LOC_FACE2 = 2, NLOC = 3 };
 
@@ -43,6 +45,21 @@ constexpr double FL_GAMMA = 50.0;
 enum { FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32 };
 enum { PF_OK = 0, PF_NOCONV = 1, PF_W = 2, PF_VSQ = 3, PF_RHO = 4, PF_U = 5, PF_D = 6 };
 
+// Reciprocal without the IEEE division sequence: the hardware approximation
+// (PTX rcp.approx.ftz.f64) refined by two Newton-Raphson steps for 1/x,
+// r <- r + r (1 - x r), each of which doubles the correct bits; the result is
+// within a few ulp of 1/x for normal x.  Used where the quotient feeds
+// further arithmetic (WENO weights, signal speeds, the Newton iteration of
+// the inversion); decisions compared against constants keep IEEE division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 struct Dims {
   int n[3];   // interior zones
   int s[3];   // with ghosts
@@ -55,7 +72,7 @@ __device__ __forceinline__ long long zid(const Dims &D, int i, int j, int k) {
 }
 
 struct Geo {
-  double gcov[10], gcon[10], gdet, alpha;
+  double gcov[10], gcon[10], gdet, alpha, ialpha, igdet;
 };
 
 __device__ __forceinline__ void load_geo(const double *__restrict__ g, long long n2d, long long ij,
@@ -66,6 +83,8 @@ __device__ __forceinline__ void load_geo(const double *__restrict__ g, long long
   for (int c = 0; c < 10; c++) G.gcon[c] = __ldg(g + (G_GCON + c) * n2d + ij);
   G.gdet = __ldg(g + G_GDET * n2d + ij);
   G.alpha = __ldg(g + G_ALPHA * n2d + ij);
+  G.ialpha = __ldg(g + G_IALPHA * n2d + ij);
+  G.igdet = __ldg(g + G_IGDET * n2d + ij);
 }
 
 // ---------------------------------------------------------------------------
@@ -83,9 +102,12 @@ __device__ __forceinline__ void fluid_state(const double P[NV], const Geo &G, FS
   const double l1 = G.gcov[SY(1, 1)] * v1 + G.gcov[SY(1, 2)] * v2 + G.gcov[SY(1, 3)] * v3;
   const double l2 = G.gcov[SY(1, 2)] * v1 + G.gcov[SY(2, 2)] * v2 + G.gcov[SY(2, 3)] * v3;
   const double l3 = G.gcov[SY(1, 3)] * v1 + G.gcov[SY(2, 3)] * v2 + G.gcov[SY(3, 3)] * v3;
-  const double gam = sqrt(1.0 + (l1 * v1 + l2 * v2 + l3 * v3));
+  // gamma and 1/gamma from one reciprocal square root
+  const double g2 = 1.0 + (l1 * v1 + l2 * v2 + l3 * v3);
+  const double rg = rsqrt(g2);
+  const double gam = g2 * rg;
   const double ga = gam * G.alpha;
-  s.ucon[0] = gam / G.alpha;
+  s.ucon[0] = gam * G.ialpha;
   s.ucon[1] = v1 - ga * G.gcon[SY(0, 1)];
   s.ucon[2] = v2 - ga * G.gcon[SY(0, 2)];
   s.ucon[3] = v3 - ga * G.gcon[SY(0, 3)];
@@ -94,7 +116,7 @@ __device__ __forceinline__ void fluid_state(const double P[NV], const Geo &G, FS
   s.ucov[2] = l2;
   s.ucov[3] = l3;
   const double bt = P[B1] * l1 + P[B2] * l2 + P[B3] * l3;
-  const double iut = G.alpha / gam;  // 1/u^t
+  const double iut = G.alpha * rg;  // 1/u^t
   s.bcon[0] = bt;
   s.bcon[1] = (P[B1] + bt * s.ucon[1]) * iut;
   s.bcon[2] = (P[B2] + bt * s.ucon[2]) * iut;
@@ -136,6 +158,35 @@ __device__ __forceinline__ void prim_flux(const double P[NV], const FState &s, c
   F[B3] = G.gdet * (s.bcon[3] * ud - bd * s.ucon[3]);
 }
 
+// acc += F^dir + coef * U without the sqrt(-g) factor: the two rows T^dir_nu
+// and T^t_nu share (rho + u + p + b^2) u_nu and b_nu.
+__device__ __forceinline__ void flux_cons_acc(const double P[NV], const FState &s, double gam,
+                                              int dir, double coef, double acc[NV]) {
+  const double pg = (gam - 1.0) * P[UU];
+  const double w = P[RHO] + P[UU] + pg + s.bsq;
+  const double pt = pg + 0.5 * s.bsq;
+  const double ud = s.ucon[dir], ut = s.ucon[0];
+  const double bd = s.bcon[dir], bt = s.bcon[0];
+  // combined contravariant weights: F + coef U = (u^d + coef u^t) ... - (b^d + coef b^t) ...
+  const double uc = ud + coef * ut;
+  const double bc = bd + coef * bt;
+  const double wuc = w * uc;
+  double T[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; nu++) T[nu] = wuc * s.ucov[nu] - bc * s.bcov[nu];
+  T[dir] += pt;
+  T[0] += coef * pt;
+  const double mf = P[RHO] * uc;
+  acc[RHO] += mf;
+  acc[UU] += T[0] + mf;
+  acc[U1] += T[1];
+  acc[U2] += T[2];
+  acc[U3] += T[3];
+  acc[B1] += s.bcon[1] * uc - bc * s.ucon[1];
+  acc[B2] += s.bcon[2] * uc - bc * s.ucon[2];
+  acc[B3] += s.bcon[3] * uc - bc * s.ucon[3];
+}
+
 // Fast-magnetosonic coordinate speeds along dir: roots v of
 // (k.u)^2 = cms2 (k.k + (k.u)^2) for k_mu = delta^dir_mu - v delta^t_mu,
 // cms2 = cs2 + va2 - cs2 va2; a negative discriminant counts as zero.
@@ -143,8 +194,9 @@ __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, c
                                           double gam, int dir, double &vmax, double &vmin) {
   const double ef = P[RHO] + gam * P[UU];
   const double ee = s.bsq + ef;
-  const double va2 = s.bsq / ee;
-  const double cs2 = gam * (gam - 1.0) * P[UU] / ef;
+  const double iee = rcp_nr(ef * ee);  // one reciprocal for va2 and cs2
+  const double va2 = s.bsq * ef * iee;
+  const double cs2 = gam * (gam - 1.0) * P[UU] * ee * iee;
   const double cms2 = cs2 + va2 - cs2 * va2;
   const double Asq = G.gcon[SY(dir, dir)];
   const double Bsq = G.gcon[SY(0, 0)];
@@ -157,7 +209,7 @@ __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, c
   const double qc = Au * Au - (Asq + Au * Au) * cms2;
   double disc = qb * qb - 4.0 * qa * qc;
   disc = (disc > 0.0) ? sqrt(disc) : 0.0;
-  const double i2a = 0.5 / qa;
+  const double i2a = 0.5 * rcp_nr(qa);
   const double v1 = (-qb + disc) * i2a;
   const double v2 = (-qb - disc) * i2a;
   vmax = fmax(v1, v2);
@@ -195,6 +247,40 @@ __device__ __forceinline__ double weno5_hi(double a, double b, double c, double 
   return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
 }
 
+// Both WENO5 face values of the middle zone of a..e (zones c-2..c+2), written
+// in the stencil's first differences (dm2 = b-a, dm1 = c-b, dp1 = d-c,
+// dp2 = e-d) and second differences (D0 = a-2b+c, D1 = b-2c+d, D2 = c-2d+e):
+//   12 beta_0 = 13 D0^2 + 3 (D0 + 2 dm1)^2
+//   12 beta_1 = 13 D1^2 + 3 (dm1 + dp1)^2
+//   12 beta_2 = 13 D2^2 + 3 (D2 - 2 dp1)^2
+//   6 (q_0 - c) = 2 D0 + 3 dm1,  6 (q_1 - c) = dm1 + 2 dp1,  6 (q_2 - c) = 3 dp1 - D2
+// (q_k the candidate values at the high face), the low face by mirroring.
+// The weights d_k/(eps + beta_k)^2 are taken over the common denominator
+// q0 q1 q2 of the squared (12 eps + 12 beta_k), which leaves their ratios
+// unchanged, and one reciprocal serves both faces.
+__device__ __forceinline__ void weno5_pair(double a, double b, double c, double d, double e,
+                                           double &lo, double &hi) {
+  const double eps12 = 12.0e-26;
+  const double dm2 = b - a, dm1 = c - b, dp1 = d - c, dp2 = e - d;
+  const double D0 = dm1 - dm2, D1 = dp1 - dm1, D2 = dp2 - dp1;
+  const double s0 = D0 + 2.0 * dm1, s1 = dm1 + dp1, s2 = D2 - 2.0 * dp1;
+  const double e0 = eps12 + (13.0 * D0 * D0 + 3.0 * s0 * s0);
+  const double e1 = eps12 + (13.0 * D1 * D1 + 3.0 * s1 * s1);
+  const double e2 = eps12 + (13.0 * D2 * D2 + 3.0 * s2 * s2);
+  const double q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+  const double q12 = q1 * q2, q02 = q0 * q2, q01 = q0 * q1;
+  const double m3 = 3.0 * dm1, p3 = 3.0 * dp1;
+  // high face: weights 0.1 q12, 0.6 q02, 0.3 q01
+  const double nh = 0.1 * q12 * (2.0 * D0 + m3) + 0.6 * q02 * (dm1 + 2.0 * dp1) + 0.3 * q01 * (p3 - D2);
+  const double H = 6.0 * (0.1 * q12 + 0.6 * q02 + 0.3 * q01);
+  // low face (mirrored stencil): weights 0.1 q01, 0.6 q02, 0.3 q12
+  const double nl = 0.1 * q01 * (2.0 * D2 - p3) - 0.6 * q02 * (dp1 + 2.0 * dm1) - 0.3 * q12 * (m3 + D0);
+  const double L = 6.0 * (0.1 * q01 + 0.6 * q02 + 0.3 * q12);
+  const double r = rcp_nr(H * L);
+  hi = c + nh * (L * r);
+  lo = c + nl * (H * r);
+}
+
 // ---------------------------------------------------------------------------
 // 1D_W primitive recovery (Noble et al. 2006) in W' = W - D.
 // Iteration rule: guess W' from the guess primitives (clamped >= 0); Newton
@@ -212,7 +298,7 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
                                           const double Pg[NV], double P[NV]) {
 #pragma unroll
   for (int v = 0; v < NV; v++) P[v] = Pg[v];
-  const double igd = 1.0 / G.gdet;
+  const double igd = G.igdet;
   const double al = G.alpha;
   P[B1] = U[B1] * igd;
   P[B2] = U[B2] * igd;
@@ -225,8 +311,8 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
   // Q'.n = Q.n + D without the rest-mass cancellation
   const double Qpn = (U[UU] - (1.0 - al) * U[RHO]) * igd -
                      al * (Q1 * G.gcon[SY(0, 1)] + Q2 * G.gcon[SY(0, 2)] + Q3 * G.gcon[SY(0, 3)]);
-  // spatial inverse metric gamma^{ij} = g^{ij} - g^{it} g^{jt} / g^{tt}
-  const double ig00 = 1.0 / G.gcon[SY(0, 0)];
+  // spatial inverse metric gamma^{ij} = g^{ij} - g^{it} g^{jt} / g^{tt}, 1/g^{tt} = -alpha^2
+  const double ig00 = -al * al;
   const double c1 = G.gcon[SY(0, 1)], c2 = G.gcon[SY(0, 2)], c3 = G.gcon[SY(0, 3)];
   const double h11 = G.gcon[SY(1, 1)] - c1 * c1 * ig00, h12 = G.gcon[SY(1, 2)] - c1 * c2 * ig00;
   const double h13 = G.gcon[SY(1, 3)] - c1 * c3 * ig00, h22 = G.gcon[SY(2, 2)] - c2 * c2 * ig00;
@@ -255,7 +341,8 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
     const double W = Wp + D;
     const double W2 = W * W;
     const double BW = Bsq + W;
-    const double iBW2W2 = 1.0 / (BW * BW * W2);
+    const double ix = rcp_nr(BW * W);  // 1/W = BW ix, 1/(B^2+W) = W ix
+    const double iBW2W2 = ix * ix;
     double vsq = (Qtsq * W2 + QdB2 * (Bsq + 2.0 * W)) * iBW2W2;
     invalid = 0;
     if (vsq > INV_VSQ_MAX) {
@@ -267,9 +354,11 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
     }
     if (vsq < 0.0) vsq = 0.0;
     const double omv = 1.0 - vsq;
-    const double sq = sqrt(omv);
-    const double wmr = Wp * omv - D * vsq * sq / (1.0 + sq);
-    const double iW2 = 1.0 / W2;
+    const double rsq = rsqrt(omv);  // 1/sqrt(1 - v^2)
+    const double sq = omv * rsq;
+    const double wmr = Wp * omv - D * vsq * sq * rcp_nr(1.0 + sq);
+    const double iW = BW * ix;
+    const double iW2 = iW * iW;
     const double f = Qpn + Wp - gf * wmr + 0.5 * (1.0 + vsq) * Bsq - 0.5 * QdB2 * iW2;
     if (f > 0.0) {
       hi = have_hi ? fmin(hi, Wp) : Wp;
@@ -278,10 +367,10 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
       lo = fmax(lo, Wp);
     }
     const double dv = -2.0 * (Qtsq * W2 * W + QdB2 * (3.0 * W2 + 3.0 * W * Bsq + Bsq * Bsq)) *
-                      (iBW2W2 / (BW * W));
-    const double dpdW = gf * (omv + dv * (0.5 * D / sq - W));
-    const double df = 1.0 - dpdW + 0.5 * Bsq * dv + QdB2 * iW2 / W;
-    double Wn = Wp - f / df;
+                      (iBW2W2 * ix);
+    const double dpdW = gf * (omv + dv * (0.5 * D * rsq - W));
+    const double df = 1.0 - dpdW + 0.5 * Bsq * dv + QdB2 * iW2 * iW;
+    double Wn = Wp - f * rcp_nr(df);
     if (Wn < 0.0) Wn = 0.5 * Wp;
     if (converged) {
       Wp = Wn;

@@ -31,7 +31,7 @@ struct Clock {
 struct StepArgs {
   Dims D;
   double gam, cfl;
-  double dx[3];
+  double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   int bc[3][2];
   const double *geom;
@@ -48,6 +48,13 @@ void launch_bounds(const StepArgs &A, double *P, cudaStream_t st);
 void launch_ctop_reset(const StepArgs &A, cudaStream_t st);
 // fluxes of P (recon + LLF), with the interior ctop maxima into clk->ctop_bits
 void launch_fluxes(const StepArgs &A, const double *P, double *F[3], cudaStream_t st);
+// the same fluxes in two passes per direction: zone-centric reconstruction of
+// both face values of every zone along dir into Lf (low face) / Rf (high face),
+// scratch of 8 x ntot doubles each, then the face fluxes from them
+void launch_recon(const StepArgs &A, int dir, const double *P, double *Lf, double *Rf,
+                  cudaStream_t st);
+void launch_face(const StepArgs &A, int dir, double *F, const double *Lf, const double *Rf,
+                 cudaStream_t st);
 // time step from clk->ctop_bits (stage 1 only)
 void launch_dt(const StepArgs &A, cudaStream_t st);
 // boundary flux fixes + flux-CT (emf scratch: 3 x ntot)

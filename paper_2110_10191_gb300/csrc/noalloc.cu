@@ -114,7 +114,10 @@ extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *
   A.D = D;
   A.gam = params->gamma;
   A.cfl = params->cfl;
-  for (int d = 0; d < 3; d++) A.dx[d] = G.dx[d];
+  for (int d = 0; d < 3; d++) {
+    A.dx[d] = G.dx[d];
+    A.idx[d] = 1.0 / G.dx[d];
+  }
   A.recon = params->recon;
   A.floors_on = params->floors_on;
   for (int d = 0; d < 3; d++)

@@ -215,6 +215,136 @@ static void launch_flux_dir(const StepArgs &A, const double *P, double *F, cudaS
     k_flux<DIR, 0><<<nb, BS, 0, st>>>(A, P, F);
 }
 
+// ---------------------------------------------------------------------------
+// Split flux stage.  k_recon: one thread per zone reconstructs both face
+// values of its 8 primitives along DIR (zones NG-1 .. n+NG along DIR and the
+// extended transverse range), so each zone's WENO smoothness indicators are
+// formed once.  Lf = value at the zone's low face, Rf = at its high face.
+// k_face: one thread per face combines Rf of zone c-1 (left state) and Lf of
+// zone c (right state) into the LLF flux.
+// ---------------------------------------------------------------------------
+template <int DIR, int RECON>
+__global__ void __launch_bounds__(BS) k_recon(StepArgs A, const double *__restrict__ P,
+                                              double *__restrict__ Lf, double *__restrict__ Rf) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2, e2 = D.n[2] + 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)e0 * e1 * e2) return;
+  const int i = NG - 1 + (int)(t % e0);
+  const int j = NG - 1 + (int)((t / e0) % e1);
+  const int k = NG - 1 + (int)(t / ((long long)e0 * e1));
+  const long long c = zid(D, i, j, k);
+  const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const double *p = P + v * D.ntot + c;
+    double lo, hi;
+    if (RECON == 1) {
+      weno5_pair(__ldg(p - 2 * st), __ldg(p - st), __ldg(p), __ldg(p + st), __ldg(p + 2 * st), lo, hi);
+    } else {
+      const double x1 = __ldg(p), h = 0.5 * mc_slope(__ldg(p - st), x1, __ldg(p + st));
+      lo = x1 - h;
+      hi = x1 + h;
+    }
+    Lf[v * D.ntot + c] = lo;
+    Rf[v * D.ntot + c] = hi;
+  }
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(BS) k_face(StepArgs A, const double *__restrict__ Lf,
+                                             const double *__restrict__ Rf, double *__restrict__ F) {
+  const Dims &D = A.D;
+  int lo[3], ext[3];
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    lo[e] = (e == DIR) ? NG : NG - 1;
+    ext[e] = (e == DIR) ? D.n[e] + 1 : D.n[e] + 2;
+  }
+  const long long nface = (long long)ext[0] * ext[1] * ext[2];
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool active = t < nface;
+  double ctop = 0.0;
+  if (active) {
+    const int i = lo[0] + (int)(t % ext[0]);
+    const int j = lo[1] + (int)((t / ext[0]) % ext[1]);
+    const int k = lo[2] + (int)(t / ((long long)ext[0] * ext[1]));
+    const long long c = zid(D, i, j, k);
+    const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+    double PL[NV], PR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      PL[v] = __ldg(Rf + v * D.ntot + c - st);
+      PR[v] = __ldg(Lf + v * D.ntot + c);
+    }
+    const int loc = (DIR == 0) ? LOC_FACE1 : (DIR == 1) ? LOC_FACE2 : LOC_CENT;
+    Geo G;
+    load_geo(A.geom + (long long)loc * G_NCOMP * D.n2d, D.n2d, (long long)j * D.s[0] + i, G);
+    FState sL, sR;
+    fluid_state(PL, G, sL);
+    fluid_state(PR, G, sR);
+    double vmaxL, vminL, vmaxR, vminR;
+    mhd_vchar(PL, sL, G, A.gam, DIR + 1, vmaxL, vminL);
+    mhd_vchar(PR, sR, G, A.gam, DIR + 1, vmaxR, vminR);
+    const double cmax = fmax(fmax(0.0, vmaxL), vmaxR);
+    const double cmin = fmax(fmax(0.0, -vminL), -vminR);
+    const double ct = fmax(cmax, cmin);
+    // LLF: F = 1/2 sqrt(-g) [(F_L + ct U_L) + (F_R - ct U_R)]
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) acc[v] = 0.0;
+    flux_cons_acc(PL, sL, A.gam, DIR + 1, ct, acc);
+    flux_cons_acc(PR, sR, A.gam, DIR + 1, -ct, acc);
+    const double hg = 0.5 * G.gdet;
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v * D.ntot + c] = hg * acc[v];
+    bool interior = true;
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      if (e == DIR) continue;
+      const int q = (e == 0) ? i : (e == 1) ? j : k;
+      interior = interior && (q >= NG) && (q < D.n[e] + NG);
+    }
+    if (interior) ctop = ct;
+  }
+  warp_block_max(ctop, &A.clk->ctop_bits[DIR]);
+}
+
+template <int DIR>
+static void launch_recon_dir(const StepArgs &A, const double *P, double *Lf, double *Rf,
+                             cudaStream_t st) {
+  const Dims &D = A.D;
+  const long long nz = (long long)(D.n[0] + 2) * (D.n[1] + 2) * (D.n[2] + 2);
+  const unsigned nbz = (unsigned)((nz + BS - 1) / BS);
+  if (A.recon == 1)
+    k_recon<DIR, 1><<<nbz, BS, 0, st>>>(A, P, Lf, Rf);
+  else
+    k_recon<DIR, 0><<<nbz, BS, 0, st>>>(A, P, Lf, Rf);
+}
+
+template <int DIR>
+static void launch_face_dir(const StepArgs &A, double *F, const double *Lf, const double *Rf,
+                            cudaStream_t st) {
+  const Dims &D = A.D;
+  long long nf = 1;
+  for (int e = 0; e < 3; e++) nf *= (e == DIR) ? D.n[e] + 1 : D.n[e] + 2;
+  k_face<DIR><<<(unsigned)((nf + BS - 1) / BS), BS, 0, st>>>(A, Lf, Rf, F);
+}
+
+void launch_recon(const StepArgs &A, int dir, const double *P, double *Lf, double *Rf,
+                  cudaStream_t st) {
+  if (dir == 0) launch_recon_dir<0>(A, P, Lf, Rf, st);
+  if (dir == 1) launch_recon_dir<1>(A, P, Lf, Rf, st);
+  if (dir == 2) launch_recon_dir<2>(A, P, Lf, Rf, st);
+}
+
+void launch_face(const StepArgs &A, int dir, double *F, const double *Lf, const double *Rf,
+                 cudaStream_t st) {
+  if (dir == 0) launch_face_dir<0>(A, F, Lf, Rf, st);
+  if (dir == 1) launch_face_dir<1>(A, F, Lf, Rf, st);
+  if (dir == 2) launch_face_dir<2>(A, F, Lf, Rf, st);
+}
+
 __global__ void k_reset_ctop(Clock *clk) {
   clk->ctop_bits[0] = clk->ctop_bits[1] = clk->ctop_bits[2] = 0ull;
 }
@@ -428,13 +558,13 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs A, const double *Pi,
       fluid_state(ps, G, ss);
       geo_source(ps, ss, G, A.conn, D.n2d, ij, A.gam, S);
     }
-    const double idx1 = A.dx[0], idx2 = A.dx[1], idx3 = A.dx[2];
+    const double idx1 = A.idx[0], idx2 = A.idx[1], idx3 = A.idx[2];
     double Un[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       const long long o = v * N + c;
-      const double div = (F1[o + 1] - F1[o]) / idx1 + (F2[o + D.s[0]] - F2[o]) / idx2 +
-                         (F3[o + D.n2d] - F3[o]) / idx3;
+      const double div = (F1[o + 1] - F1[o]) * idx1 + (F2[o + D.s[0]] - F2[o]) * idx2 +
+                         (F3[o + D.n2d] - F3[o]) * idx3;
       const double src = (v >= UU && v <= U3) ? S[v - UU] : 0.0;
       Un[v] = Ui[v] + dtp * (src - div);
     }

@@ -49,11 +49,11 @@ class grmhd_params(ctypes.Structure):
                 ("bc", (ctypes.c_int * 2) * 3)]
 
 
-KCLASSES = ["flux", "dt", "ct", "update", "fixup", "bounds", "other"]
+KCLASSES = ["flux", "dt", "ct", "update", "fixup", "bounds", "other", "recon"]
 
 
 class grmhd_profile_data(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_longlong * 7)]
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_longlong * 8)]
 
 
 class grmhd_stats(ctypes.Structure):
