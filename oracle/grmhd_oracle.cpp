@@ -1101,6 +1101,8 @@ void oracle_destroy(void *h) { delete (Sim *)h; }
 
 /* P: [8][n3][n2][n1] interior primitives; ghosts are filled by the BCs
  * (BC_FIXED ghosts are left as they are). */
+/* READING (fixed boundaries): the ghosts of a BC_FIXED side hold their set
+ * values in both stage arrays, so the half-step state starts as a copy. */
 void oracle_set_prims(void *h, const double *P) {
   Sim *S = (Sim *)h;
   for (int v = 0; v < NPRIM; v++)
@@ -1110,6 +1112,7 @@ void oracle_set_prims(void *h, const double *P) {
           S->P[v * S->ntot + IDX(S, i + NG, j + NG, k + NG)] =
               P[(((long)v * S->n[2] + k) * S->n[1] + j) * S->n[0] + i];
   bounds(S, S->P);
+  S->Ph = S->P;
 }
 
 /* P: [8][s3][s2][s1] including ghosts; then the BCs are applied. */
@@ -1117,6 +1120,7 @@ void oracle_set_prims_ghost(void *h, const double *P) {
   Sim *S = (Sim *)h;
   for (long q = 0; q < NPRIM * S->ntot; q++) S->P[q] = P[q];
   bounds(S, S->P);
+  S->Ph = S->P;
 }
 
 void oracle_get_prims(void *h, double *P, int with_ghosts) {
