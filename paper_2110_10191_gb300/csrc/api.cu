@@ -19,7 +19,7 @@ struct grmhd_sim {
   grmhd_metric metric;
   grmhd_params params;
   cudaStream_t st;
-  double *P, *Ph, *F[3], *emf, *Lf, *Rf;
+  double *P, *Ph, *F[3], *emf, *Lf, *Rf, *Uc;
   double *geom, *conn, *floors;
   int *pflag, *fflag;
   Clock *clk;
@@ -95,8 +95,8 @@ static void free_all(grmhd_sim *s) {
     s->prof_ev = nullptr;
     s->ev_pool = nullptr;
   }
-  double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->Lf, s->Rf, s->geom, s->conn,
-                 s->floors};
+  double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->Lf, s->Rf, s->Uc, s->geom,
+                 s->conn, s->floors};
   for (double *p : d)
     if (p) cudaFree(p);
   if (s->pflag) cudaFree(s->pflag);
@@ -160,7 +160,7 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   bool ok = cudaMalloc(&s->P, fb) == cudaSuccess && cudaMalloc(&s->Ph, fb) == cudaSuccess &&
             cudaMalloc(&s->F[0], fb) == cudaSuccess && cudaMalloc(&s->F[1], fb) == cudaSuccess &&
             cudaMalloc(&s->F[2], fb) == cudaSuccess && cudaMalloc(&s->Lf, fb) == cudaSuccess &&
-            cudaMalloc(&s->Rf, fb) == cudaSuccess &&
+            cudaMalloc(&s->Rf, fb) == cudaSuccess && cudaMalloc(&s->Uc, fb) == cudaSuccess &&
             cudaMalloc(&s->emf, sizeof(double) * 3 * (size_t)tot) == cudaSuccess &&
             cudaMalloc(&s->geom, sizeof(double) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
             cudaMalloc(&s->conn, sizeof(double) * C_NCOMP * (size_t)D.n2d) == cudaSuccess &&
@@ -215,6 +215,7 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   StepArgs &A = s->A;
   A.D = D;
   A.gam = params->gamma;
+  A.igam = 1.0 / params->gamma;
   A.cfl = params->cfl;
   for (int d = 0; d < 3; d++) {
     A.dx[d] = G.dx[d];
@@ -260,8 +261,10 @@ static void enqueue_bounds(grmhd_sim *s, double *P) {
   launch_bounds(s->A, P, s->st);
 }
 
+// ucache_mode: 1 the predictor keeps U(P^n) for the corrector, 2 the
+// corrector reads it back, 0 neither (a predictor run on its own).
 static void enqueue_stage(grmhd_sim *s, const double *Pi, const double *Ps, double *Pout,
-                          double dtfac, bool first) {
+                          double dtfac, bool first, int ucache_mode) {
   cudaStream_t st = s->st;
   enqueue_fluxes(s, Ps);
   if (first) {
@@ -274,7 +277,7 @@ static void enqueue_stage(grmhd_sim *s, const double *Pi, const double *Ps, doub
   }
   {
     ClassScope c(s, GRMHD_K_UPDATE, 1);
-    launch_update(s->A, Pi, Ps, Pout, s->F, s->pflag, s->fflag, dtfac, st);
+    launch_update(s->A, Pi, Ps, Pout, s->F, s->pflag, s->fflag, dtfac, s->Uc, ucache_mode, st);
   }
   {
     ClassScope c(s, GRMHD_K_FIXUP, 1);
@@ -296,6 +299,9 @@ static int set_common(grmhd_sim *s, const double *P, int on_device, int ghost) {
     launch_pack(D, s->Ph, s->P, 1, s->st);
   }
   enqueue_bounds(s, s->P);
+  // the ghosts of a fixed side keep their set values in both stage arrays
+  CK(cudaMemcpyAsync(s->Ph, s->P, sizeof(double) * NV * (size_t)D.ntot, cudaMemcpyDeviceToDevice,
+                     s->st));
   int rc = launched();
   if (rc != GRMHD_OK) return rc;
   if (!on_device) CK(cudaStreamSynchronize(s->st));
@@ -350,8 +356,8 @@ static int read_stats(grmhd_sim *s, grmhd_stats *out, bool check) {
 extern "C" int grmhd_step(grmhd_sim *s, int nsteps, grmhd_stats *stats) {
   if (!s || nsteps < 0) return GRMHD_ERR_INVALID;
   for (int n = 0; n < nsteps; n++) {
-    enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true);   // predictor
-    enqueue_stage(s, s->P, s->Ph, s->P, 1.0, false);  // corrector
+    enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true, 1);   // predictor
+    enqueue_stage(s, s->P, s->Ph, s->P, 1.0, false, 2);  // corrector
     ClassScope c(s, GRMHD_K_OTHER, 1);
     launch_advance(s->A, s->st);
   }
@@ -382,7 +388,7 @@ extern "C" int grmhd_set_time(grmhd_sim *s, double t, double dt_prev, long long 
 
 extern "C" int grmhd_predictor(grmhd_sim *s) {
   if (!s) return GRMHD_ERR_INVALID;
-  enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true);
+  enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true, 0);
   int rc = launched();
   if (rc != GRMHD_OK) return rc;
   double *t = s->P;

@@ -256,8 +256,8 @@ __device__ __forceinline__ double weno5_hi(double a, double b, double c, double 
 //   6 (q_0 - c) = 2 D0 + 3 dm1,  6 (q_1 - c) = dm1 + 2 dp1,  6 (q_2 - c) = 3 dp1 - D2
 // (q_k the candidate values at the high face), the low face by mirroring.
 // The weights d_k/(eps + beta_k)^2 are taken over the common denominator
-// q0 q1 q2 of the squared (12 eps + 12 beta_k), which leaves their ratios
-// unchanged, and one reciprocal serves both faces.
+// q0 q1 q2 of the squared (12 eps + 12 beta_k) and scaled by 10, which
+// leaves their ratios unchanged, and one reciprocal serves both faces.
 __device__ __forceinline__ void weno5_pair(double a, double b, double c, double d, double e,
                                            double &lo, double &hi) {
   const double eps12 = 12.0e-26;
@@ -268,14 +268,16 @@ __device__ __forceinline__ void weno5_pair(double a, double b, double c, double 
   const double e1 = eps12 + (13.0 * D1 * D1 + 3.0 * s1 * s1);
   const double e2 = eps12 + (13.0 * D2 * D2 + 3.0 * s2 * s2);
   const double q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
-  const double q12 = q1 * q2, q02 = q0 * q2, q01 = q0 * q1;
+  // linear weights in the ratio 1 : 6 : 3 (only ratios enter)
+  const double q12 = q1 * q2, q02 = 6.0 * (q0 * q2), q01 = q0 * q1;
+  const double t01 = 3.0 * q01, t12 = 3.0 * q12;
   const double m3 = 3.0 * dm1, p3 = 3.0 * dp1;
-  // high face: weights 0.1 q12, 0.6 q02, 0.3 q01
-  const double nh = 0.1 * q12 * (2.0 * D0 + m3) + 0.6 * q02 * (dm1 + 2.0 * dp1) + 0.3 * q01 * (p3 - D2);
-  const double H = 6.0 * (0.1 * q12 + 0.6 * q02 + 0.3 * q01);
-  // low face (mirrored stencil): weights 0.1 q01, 0.6 q02, 0.3 q12
-  const double nl = 0.1 * q01 * (2.0 * D2 - p3) - 0.6 * q02 * (dp1 + 2.0 * dm1) - 0.3 * q12 * (m3 + D0);
-  const double L = 6.0 * (0.1 * q01 + 0.6 * q02 + 0.3 * q12);
+  // high face: weights q12, 6 q02, 3 q01
+  const double nh = q12 * (2.0 * D0 + m3) + q02 * (dm1 + 2.0 * dp1) + t01 * (p3 - D2);
+  const double H = 6.0 * (q12 + q02 + t01);
+  // low face (mirrored stencil): weights q01, 6 q02, 3 q12
+  const double nl = q01 * (2.0 * D2 - p3) - q02 * (dp1 + 2.0 * dm1) - t12 * (m3 + D0);
+  const double L = 6.0 * (q01 + q02 + t12);
   const double r = rcp_nr(H * L);
   hi = c + nh * (L * r);
   lo = c + nl * (H * r);
@@ -294,8 +296,12 @@ constexpr int INV_EXTRA = 2;
 constexpr double INV_TOL = 1.0e-8;
 constexpr double INV_VSQ_MAX = 1.0 - 1.0e-10;
 
+// On success also returns b^2 = B^2 (1 - v^2) + (Q.B / W)^2 (normal-frame
+// field B, B.v = Q.B/W) and the Lorentz factor of the recovered state, so the
+// bounds need not rebuild the fluid state.
 __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, double gam,
-                                          const double Pg[NV], double P[NV]) {
+                                          double igam, const double Pg[NV], double P[NV],
+                                          double &bsq_out, double &lorentz_out) {
 #pragma unroll
   for (int v = 0; v < NV; v++) P[v] = Pg[v];
   const double igd = G.igdet;
@@ -386,16 +392,21 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
   if (!(W > 0.0) || !isfinite(W)) return PF_W;
   const double W2 = W * W;
   const double BW = Bsq + W;
-  double vsq = (Qtsq * W2 + QdB2 * (Bsq + 2.0 * W)) / (BW * BW * W2);
+  const double ix = rcp_nr(BW * W);
+  double vsq = (Qtsq * W2 + QdB2 * (Bsq + 2.0 * W)) * (ix * ix);
   if (!(vsq < 1.0) || invalid) return PF_VSQ;
   if (vsq < 0.0) vsq = 0.0;
-  const double sq = sqrt(1.0 - vsq);
+  const double omv = 1.0 - vsq;
+  const double rsq = rsqrt(omv);  // Lorentz factor
+  const double sq = omv * rsq;
   const double rho = D * sq;
-  const double uu = (Wp * (1.0 - vsq) - D * vsq * sq / (1.0 + sq)) / gam;
+  const double uu = (Wp * omv - D * vsq * sq * rcp_nr(1.0 + sq)) * igam;
   if (!(rho > 0.0)) return PF_RHO;
   if (uu < 0.0) return PF_U;
-  const double fac = 1.0 / (sq * BW);  // gamma / (W + B^2)
-  const double qbw = QdB / W;
+  const double fac = rsq * (W * ix);  // gamma / (W + B^2)
+  const double qbw = QdB * (BW * ix);  // Q.B / W
+  bsq_out = Bsq * omv + qbw * qbw;
+  lorentz_out = rsq;
   P[RHO] = rho;
   P[UU] = uu;
   P[U1] = fac * (Qt1 + qbw * n1);
@@ -408,6 +419,26 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
 // Bounds: Lorentz-factor cap first (it changes b^2), then rho and u raised in
 // the fluid frame in the order of the paper's list; every bound holds on exit.
 // ---------------------------------------------------------------------------
+// The bounds with b^2 and the Lorentz factor already known (from the
+// inversion); zones that need the Lorentz-factor cap take the general path.
+__device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double rho_fl,
+                                            double u_fl, double gam);
+__device__ __forceinline__ int apply_floors_known(double P[NV], const Geo &G, double rho_fl,
+                                                  double u_fl, double gam, double bsq,
+                                                  double lorentz) {
+  if (lorentz > FL_GAMMA) return apply_floors(P, G, rho_fl, u_fl, gam);
+  int fl = 0;
+  if (P[RHO] < rho_fl) { P[RHO] = rho_fl; fl |= FF_RHO_GEOM; }
+  if (P[UU] < u_fl) { P[UU] = u_fl; fl |= FF_U_GEOM; }
+  const double rs = bsq / FL_SIGMA;
+  if (P[RHO] < rs) { P[RHO] = rs; fl |= FF_SIGMA; }
+  const double ub = FL_BETA * bsq / (2.0 * (gam - 1.0));
+  if (P[UU] < ub) { P[UU] = ub; fl |= FF_BETA; }
+  const double rt = P[UU] / FL_TEMP;
+  if (P[RHO] < rt) { P[RHO] = rt; fl |= FF_TEMP; }
+  return fl;
+}
+
 __device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double rho_fl,
                                             double u_fl, double gam) {
   int fl = 0;

@@ -30,7 +30,7 @@ struct Clock {
 
 struct StepArgs {
   Dims D;
-  double gam, cfl;
+  double gam, igam, cfl;  // adiabatic index, its reciprocal, Courant number
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   int bc[3][2];
@@ -59,9 +59,12 @@ void launch_face(const StepArgs &A, int dir, double *F, const double *Lf, const 
 void launch_dt(const StepArgs &A, cudaStream_t st);
 // boundary flux fixes + flux-CT (emf scratch: 3 x ntot)
 void launch_fix_ct(const StepArgs &A, double *F[3], double *emf, cudaStream_t st);
-// U(Pi) + dt' (S(Ps) - div F) -> invert -> floors; dtfac 0.5 (predictor) or 1
+// U(Pi) + dt' (S(Ps) - div F) -> invert -> floors; dtfac 0.5 (predictor) or 1;
+// ucache_mode 1: store U(Pi) in Ucache (needs Ps == Pi), 2: read U(Pi) from it,
+// 0: neither
 void launch_update(const StepArgs &A, const double *Pi, const double *Ps, double *Pout,
-                   double *const F[3], int *pflag, int *fflag, double dtfac, cudaStream_t st);
+                   double *const F[3], int *pflag, int *fflag, double dtfac, double *Ucache,
+                   int ucache_mode, cudaStream_t st);
 void launch_fixup(const StepArgs &A, double *Pout, const int *pflag, int *fflag, cudaStream_t st);
 // t += dt, steps++ (when dt > 0)
 void launch_advance(const StepArgs &A, cudaStream_t st);

@@ -113,6 +113,7 @@ extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *
   memset(&A, 0, sizeof(A));
   A.D = D;
   A.gam = params->gamma;
+  A.igam = 1.0 / params->gamma;
   A.cfl = params->cfl;
   for (int d = 0; d < 3; d++) {
     A.dx[d] = G.dx[d];

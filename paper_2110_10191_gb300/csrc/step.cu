@@ -520,12 +520,15 @@ __device__ __forceinline__ void geo_source(const double P[NV], const FState &s, 
   }
 }
 
+// Ucache: the predictor stores U(P^n) there and the corrector, whose P_i is
+// the same P^n, reads it back instead of recomputing it (null: neither).
 __global__ void __launch_bounds__(BS) k_update(StepArgs A, const double *Pi,
                                                const double *__restrict__ Ps, double *Pout,
                                                const double *__restrict__ F1,
                                                const double *__restrict__ F2,
                                                const double *__restrict__ F3, int *pflag,
-                                               int *fflag, double dtfac) {
+                                               int *fflag, double dtfac, double *Ucache,
+                                               int ucache_mode) {
   const Dims &D = A.D;
   const double dt = A.clk->dt;
   if (!(dt > 0.0)) return;  // uniform across the grid: no warp divergence
@@ -545,13 +548,25 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs A, const double *Pi,
     double pi[NV], ps[NV], Ui[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) pi[v] = Pi[v * N + c];
-    FState si;
-    fluid_state(pi, G, si);
-    prim_flux(pi, si, G, A.gam, 0, Ui);
     double S[4];
     if (Ps == Pi) {
+      FState si;
+      fluid_state(pi, G, si);
+      prim_flux(pi, si, G, A.gam, 0, Ui);
+      if (ucache_mode == 1) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ucache[v * N + c] = Ui[v];
+      }
       geo_source(pi, si, G, A.conn, D.n2d, ij, A.gam, S);
     } else {
+      if (ucache_mode == 2) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ui[v] = Ucache[v * N + c];
+      } else {
+        FState si;
+        fluid_state(pi, G, si);
+        prim_flux(pi, si, G, A.gam, 0, Ui);
+      }
 #pragma unroll
       for (int v = 0; v < NV; v++) ps[v] = Ps[v * N + c];
       FState ss;
@@ -568,10 +583,11 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs A, const double *Pi,
       const double src = (v >= UU && v <= U3) ? S[v - UU] : 0.0;
       Un[v] = Ui[v] + dtp * (src - div);
     }
-    double pn[NV];
-    pf = invert_1dw(Un, G, A.gam, pi, pn);
+    double pn[NV], bsq_n = 0.0, lor_n = 1.0;
+    pf = invert_1dw(Un, G, A.gam, A.igam, pi, pn, bsq_n, lor_n);
     if (pf == PF_OK && A.floors_on)
-      ff = apply_floors(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam);
+      ff = apply_floors_known(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
+                              bsq_n, lor_n);
 #pragma unroll
     for (int v = 0; v < NV; v++) Pout[v * N + c] = pn[v];
     pflag[c] = pf;
@@ -582,10 +598,11 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs A, const double *Pi,
 }
 
 void launch_update(const StepArgs &A, const double *Pi, const double *Ps, double *Pout,
-                   double *const F[3], int *pflag, int *fflag, double dtfac, cudaStream_t st) {
+                   double *const F[3], int *pflag, int *fflag, double dtfac, double *Ucache,
+                   int ucache_mode, cudaStream_t st) {
   const long long nz = (long long)A.D.n[0] * A.D.n[1] * A.D.n[2];
   k_update<<<(unsigned)((nz + BS - 1) / BS), BS, 0, st>>>(A, Pi, Ps, Pout, F[0], F[1], F[2],
-                                                          pflag, fflag, dtfac);
+                                                          pflag, fflag, dtfac, Ucache, ucache_mode);
 }
 
 // ---------------------------------------------------------------------------

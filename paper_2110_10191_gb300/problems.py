@@ -456,3 +456,120 @@ def random_states(n: int, seed: int = 0, metric: int = METRIC_MKS_KERR, a: float
     bd = rng.normal(size=(n, 3))
     P[:, B1:B3 + 1] = bd
     return X, P, rng.uniform(0, 1, n) * sigma_max
+
+
+# --------------------------------------------------------------------------
+# Michel (relativistic Bondi) inflow on Schwarzschild
+# --------------------------------------------------------------------------
+
+def michel_state(r, gamma=4.0 / 3.0, r_c=8.0, mdot=1.0):
+    """Spherical polytropic inflow p = K rho^gamma onto a Schwarzschild black
+    hole (M = 1) through the sonic radius r_c (Michel 1972).  With n =
+    1/(gamma-1) and T = p/rho, the mass flux r^2 T^n u^r = -C1 and the
+    Bernoulli constant (1 + (1+n) T)^2 (1 - 2/r + (u^r)^2) = C2 fix T(r) on
+    the inflow branch; K follows from mdot = 4 pi r^2 rho |u^r|.
+    Returns rho, u (internal energy density), u^r (< 0)."""
+    r = np.asarray(r, dtype=float)
+    n = 1.0 / (gamma - 1.0)
+    uc2 = 1.0 / (2.0 * r_c)
+    vc2 = uc2 / (1.0 - 3.0 * uc2)
+    Tc = -n * vc2 / ((n + 1.0) * (n * vc2 - 1.0))
+    C1 = math.sqrt(uc2) * r_c ** 2 * Tc ** n
+    C2 = (1.0 + (1.0 + n) * Tc) ** 2 * (1.0 - 2.0 / r_c + uc2)
+
+    lC2 = math.log(C2)
+
+    def logF(T, rr):
+        # log of the Bernoulli function; T -> 0 and T -> inf both send it up
+        w = C1 / (rr * rr * T ** n)
+        return 2.0 * math.log1p((1.0 + n) * T) + math.log(1.0 - 2.0 / rr + w * w)
+
+    def dlogF(T, rr):  # derivative with respect to log T
+        w = C1 / (rr * rr * T ** n)
+        return (2.0 * (1.0 + n) * T / (1.0 + (1.0 + n) * T)
+                - 2.0 * n * w * w / (1.0 - 2.0 / rr + w * w))
+
+    def bisect(lo, hi, fun):
+        flo = fun(lo)
+        for _ in range(200):
+            mid = math.sqrt(lo * hi)
+            fm = fun(mid)
+            if (fm > 0) == (flo > 0):
+                lo, flo = mid, fm
+            else:
+                hi = mid
+        return math.sqrt(lo * hi)
+
+    T = np.empty_like(r)
+    lo0, hi0 = Tc * 1e-12, Tc * 1e12
+    for q, rr in np.ndenumerate(r):
+        rr = float(rr)
+        if rr <= 2.0:
+            # inside the horizon 1 - 2/r + w^2 > 0 needs T below T_max, where the
+            # function falls from +inf to -inf: one (supersonic) root
+            tmax = (C1 / (rr * rr * math.sqrt(max(2.0 / rr - 1.0, 1e-300)))) ** (1.0 / n)
+            T[q] = bisect(lo0, tmax * (1.0 - 1e-15), lambda t: logF(t, rr) - lC2)
+            continue
+        # the minimum over T of the Bernoulli function (sonic condition)
+        tm = bisect(lo0, hi0, lambda t: dlogF(t, rr))
+        if logF(tm, rr) >= lC2:
+            T[q] = tm  # at the sonic radius (or within rounding of it)
+            continue
+        # the two roots of F = C2 straddle the minimum: the smaller T (faster
+        # flow) is the supersonic branch taken inside r_c, the larger T outside
+        if rr < r_c:
+            T[q] = bisect(lo0, tm, lambda t: logF(t, rr) - lC2)
+        else:
+            T[q] = bisect(tm, hi0, lambda t: logF(t, rr) - lC2)
+    ur = -C1 / (r * r * T ** n)
+    Kn = 4.0 * math.pi * C1 / mdot  # rho = (T/K)^n with K^n = 4 pi C1 / mdot
+    rho = T ** n / Kn
+    u = n * rho * T
+    return rho, u, ur
+
+
+def bondi(n1: int = 64, n2: int = 64, r_out: float = 20.0, r_c: float = 8.0, mdot: float = 1.0,
+          gamma: float = 4.0 / 3.0, hslope: float = 1.0, recon: int = RECON_MC, cfl: float = 0.9,
+          t_final: float = 0.0, n3: int = 1, r_in: Optional[float] = None) -> Problem:
+    """Stationary Michel inflow on Schwarzschild in MKS, n1 x n2 x n3 zones,
+    inner radius r_in (default: 5.5 radial zones inside the horizon); the X1
+    ghosts hold the analytic solution (BC_FIXED), X2 reflects at the poles,
+    X3 periodic.  ``info['P_ghost']`` is the full array with ghosts for
+    set_prims."""
+    ng = 3
+    a = 0.0
+    rin = mks_rin(n1, a, r_out) if r_in is None else float(r_in)
+    x1min, x1max = math.log(rin), math.log(r_out)
+    dx1, dx2 = (x1max - x1min) / n1, 1.0 / n2
+    X1 = x1min + (np.arange(-ng, n1 + ng) + 0.5) * dx1
+    X2 = (np.arange(-ng, n2 + ng) + 0.5) * dx2
+    X1g, X2g = np.meshgrid(X1, X2, indexing="xy")
+    r = np.exp(X1g)
+    rho1, u1d, ur1 = michel_state(np.exp(X1), gamma, r_c, mdot)
+    rho = np.broadcast_to(rho1[None, :], r.shape)
+    u = np.broadcast_to(u1d[None, :], r.shape)
+    ur = np.broadcast_to(ur1[None, :], r.shape)
+    g = mks_gcov(r, X2g, a, hslope)
+    gcon = np.linalg.inv(g)
+    alpha = 1.0 / np.sqrt(-gcon[..., 0, 0])
+    u1 = ur / r  # MKS radial component
+    # u^t from g_tt (u^t)^2 + 2 g_t1 u^t u^1 + g_11 (u^1)^2 = -1: the root that
+    # stays finite through the horizon (g_tt = 0 there), in the form without
+    # cancellation, 2 qc / (-qb + sqrt(qb^2 - 4 qa qc))  (-qb > 0 for inflow)
+    qa, qb, qc = g[..., 0, 0], 2.0 * g[..., 0, 1] * u1, g[..., 1, 1] * u1 * u1 + 1.0
+    ut = 2.0 * qc / (-qb + np.sqrt(qb * qb - 4.0 * qa * qc))
+    gam_n = alpha * ut
+    util1 = u1 + gam_n * alpha * gcon[..., 0, 1]
+    util2 = gam_n * alpha * gcon[..., 0, 2]
+    util3 = gam_n * alpha * gcon[..., 0, 3]
+    s = (n3 + 2 * ng, n2 + 2 * ng, n1 + 2 * ng)
+    Pg = np.zeros((NPRIM,) + s)
+    for v, arr in ((RHO, rho), (UU, u), (U1, util1), (U2, util2), (U3, util3)):
+        Pg[v] = arr[None]
+    P = Pg[:, ng:-ng, ng:-ng, ng:-ng].copy()
+    return Problem(
+        name="bondi_%dx%dx%d" % (n1, n2, n3), n=(n1, n2, n3), xmin=(x1min, 0.0, 0.0),
+        xmax=(x1max, 1.0, 2.0 * math.pi), metric=METRIC_MKS_KERR, a=a, hslope=hslope,
+        gamma=gamma, cfl=cfl, t_final=t_final, recon=recon, floors=1,
+        bc=((BC_FIXED, BC_FIXED), (BC_POLAR, BC_POLAR), (BC_PERIODIC, BC_PERIODIC)), P=P,
+        info={"P_ghost": Pg, "r_c": r_c, "mdot": mdot, "r_in_grid": rin})

@@ -215,6 +215,22 @@ def test_step_parity_torus(grmhd, shape, recon):
     assert st["t"] == pytest.approx(o.time()[0], rel=1e-14)
 
 
+def test_bondi_fixed_boundary_parity(grmhd):
+    """Michel inflow with X1 ghosts held at the analytic solution (fixed
+    boundaries) and the bounds on: three steps against the oracle."""
+    pr = pb.bondi(32, 24, n3=2, recon=pb.RECON_WENO5)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.info["P_ghost"])
+    s = grmhd.Sim(pr)
+    for loc in range(4):
+        s.set_geom(loc, o.geom(loc))
+    s.set_prims(pr.info["P_ghost"])
+    o.step(3)
+    s.step(3)
+    compare(s.get_prims(), o.get_prims(), tol_norm=1e-11, what="bondi")
+    assert np.array_equal(s.get_prims(True)[:, :, :, :3], o.get_prims(True)[:, :, :, :3])
+
+
 def test_predictor_parity(grmhd):
     pr = pb.fm_torus(24, 24, 8)
     o, s = _pair(pr, grmhd)

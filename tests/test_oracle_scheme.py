@@ -273,3 +273,24 @@ def test_torus_step_respects_floors():
                 assert p[1] >= gv["u_floor_coef"] * kk ** pr.gamma * (1 - 1e-15)
                 assert bsq <= gv["sigma_max"] * p[0] * (1 + 1e-12)
                 assert p[1] <= gv["u_over_rho_max"] * p[0] * (1 + 1e-15)
+
+
+def _bondi_drift(n):
+    pr = pb.bondi(n, n, t_final=5.0, r_in=1.5)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.info["P_ghost"])
+    assert o.step(100000) == 0
+    assert o.counters()["inv_failures"] == 0
+    P = o.get_prims()
+    return np.abs(P[0] - pr.P[0]).mean() / np.abs(pr.P[0]).mean()
+
+
+def test_bondi_stationary_second_order():
+    """Stationary Michel inflow on Schwarzschild (the paper's Bondi
+    convergence test, "Tests" section): the L1 drift of rho after t = 5
+    falls at second order, on a fixed domain (r_in = 1.5 inside the
+    horizon, R_out = 20, X1 ghosts held at the analytic solution)."""
+    e = np.array([_bondi_drift(n) for n in (16, 32, 64)])
+    orders = np.log2(e[:-1] / e[1:])
+    assert np.all(orders > 1.7), (e, orders)
+    assert e[-1] < 1e-4

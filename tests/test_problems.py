@@ -92,3 +92,15 @@ def test_splitmix_reproducible():
     assert 0.0 <= a.min() and a.max() < 1.0
     assert abs(a.mean() - 0.5) < 0.05
     assert not np.array_equal(a, pb.splitmix_uniform(8, idx))
+
+
+def test_michel_solution():
+    """Michel inflow: constant mass flux 4 pi r^2 rho |u^r| = mdot, the sonic
+    point where (u^r)^2 = 1/(2 r_c), temperature rising inward, through the
+    horizon."""
+    r = np.array([1.2, 1.9, 2.5, 4.0, 8.0, 12.0, 30.0])
+    rho, u, ur = pb.michel_state(r, r_c=8.0, mdot=1.0)
+    assert np.allclose(4 * math.pi * r * r * rho * np.abs(ur), 1.0, rtol=1e-10)
+    assert abs(ur[4]) == pytest.approx(math.sqrt(1 / 16.0), rel=1e-6)
+    T = (4 / 3 - 1) * u / rho
+    assert np.all(np.diff(T) < 0) and np.all(ur < 0)
