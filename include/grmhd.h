@@ -57,6 +57,10 @@ extern "C" {
 #define GRMHD_RECON_MC 0
 #define GRMHD_RECON_WENO5 1
 
+#define GRMHD_PREC_FP64 0  /* every step in FP64 */
+#define GRMHD_PREC_MIXED 1 /* reconstruction, fluid states, signal speeds and LLF fluxes
+                              in FP32; geometry, flux-CT, update, inversion, bounds FP64 */
+
 typedef struct grmhd_sim grmhd_sim; /* opaque, library-owned */
 
 /* Logically Cartesian mesh of n1 x n2 x n3 zones on [xmin, xmax] per
@@ -77,11 +81,14 @@ typedef struct {
 /* gamma: adiabatic index; cfl: Courant number; t_final > 0 clamps the last
  * step to land on it (steps after it do nothing); recon: GRMHD_RECON_*;
  * floors_on: apply the paper's bounds (needs the MKS radius); bc[d][side]:
- * GRMHD_BC_* for direction d, side 0 = low, 1 = high. */
+ * GRMHD_BC_* for direction d, side 0 = low, 1 = high; precision:
+ * GRMHD_PREC_* (the state, geometry and conserved variables are FP64 in
+ * both modes). */
 typedef struct {
   double gamma, cfl, t_final;
   int recon, floors_on;
   int bc[3][2];
+  int precision;
 } grmhd_params;
 
 /* Running statistics of a simulation (totals over all stages so far). */

@@ -21,6 +21,7 @@ struct grmhd_sim {
   cudaStream_t st;
   double *P, *Ph, *F[3], *emf, *Lf, *Rf, *Uc;
   double *geom, *conn, *floors;
+  float *Pf, *geomf;  // FP32 copies (mixed precision only)
   int *pflag, *fflag;
   Clock *clk;
   unsigned long long unrec_seen, dterr_seen;
@@ -99,6 +100,8 @@ static void free_all(grmhd_sim *s) {
                  s->conn, s->floors};
   for (double *p : d)
     if (p) cudaFree(p);
+  if (s->Pf) cudaFree(s->Pf);
+  if (s->geomf) cudaFree(s->geomf);
   if (s->pflag) cudaFree(s->pflag);
   if (s->fflag) cudaFree(s->fflag);
   if (s->clk) cudaFree(s->clk);
@@ -123,6 +126,8 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   if (metric->kind == GRMHD_METRIC_MKS_KERR && !(fabs(metric->a) < 1.0)) return GRMHD_ERR_INVALID;
   if (!(params->gamma > 1.0) || !(params->cfl > 0.0)) return GRMHD_ERR_INVALID;
   if (params->recon != GRMHD_RECON_MC && params->recon != GRMHD_RECON_WENO5) return GRMHD_ERR_INVALID;
+  if (params->precision != GRMHD_PREC_FP64 && params->precision != GRMHD_PREC_MIXED)
+    return GRMHD_ERR_INVALID;
   if (params->floors_on && metric->kind != GRMHD_METRIC_MKS_KERR) return GRMHD_ERR_INVALID;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) {
@@ -168,6 +173,9 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
             cudaMalloc(&s->pflag, sizeof(int) * (size_t)tot) == cudaSuccess &&
             cudaMalloc(&s->fflag, sizeof(int) * (size_t)tot) == cudaSuccess &&
             cudaMalloc(&s->clk, sizeof(Clock)) == cudaSuccess;
+  if (ok && params->precision == GRMHD_PREC_MIXED)
+    ok = cudaMalloc(&s->Pf, sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
+         cudaMalloc(&s->geomf, sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -204,6 +212,7 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   G.floors = s->floors;
   if (rc == GRMHD_OK) {
     launch_geometry(G, st);
+    if (s->geomf) launch_to_f32((long long)NLOC * G_NCOMP * D.n2d, s->geom, s->geomf, st);
     rc = launched();
   }
   if (rc == GRMHD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
@@ -245,6 +254,22 @@ static void enqueue_fluxes(grmhd_sim *s, const double *P) {
   {
     ClassScope c(s, GRMHD_K_OTHER, 1);
     launch_ctop_reset(s->A, s->st);
+  }
+  if (s->params.precision == GRMHD_PREC_MIXED) {
+    float *Lf = (float *)s->Lf, *Rf = (float *)s->Rf;
+    {
+      ClassScope c(s, GRMHD_K_RECON, 1);
+      launch_to_f32((long long)NV * s->D.ntot, P, s->Pf, s->st);
+    }
+    for (int d = 0; d < 3; d++) {
+      {
+        ClassScope c(s, GRMHD_K_RECON, 1);
+        launch_recon_f32(s->A, d, s->Pf, Lf, Rf, s->st);
+      }
+      ClassScope c(s, GRMHD_K_FLUX, 1);
+      launch_face_f32(s->A, d, s->geomf, s->F[d], Lf, Rf, s->st);
+    }
+    return;
   }
   for (int d = 0; d < 3; d++) {
     {
@@ -513,11 +538,17 @@ extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
   memcpy(g.data() + G_GDET * n2d, in + 32 * n2d, sizeof(double) * (size_t)n2d);
   memcpy(g.data() + G_ALPHA * n2d, in + 33 * n2d, sizeof(double) * (size_t)n2d);
   for (long long q = 0; q < n2d; q++) {
-    g[(size_t)(G_IALPHA * n2d + q)] = 1.0 / in[33 * n2d + q];
+    const double al = in[33 * n2d + q];
+    g[(size_t)(G_IALPHA * n2d + q)] = 1.0 / al;
     g[(size_t)(G_IGDET * n2d + q)] = 1.0 / in[32 * n2d + q];
+    g[(size_t)(G_OMALPHA * n2d + q)] = (1.0 + 1.0 / in[(16 + 0) * n2d + q]) / (1.0 + al);
   }
   CK(cudaMemcpyAsync(s->geom + (long long)loc * G_NCOMP * n2d, g.data(), sizeof(double) * g.size(),
                      cudaMemcpyHostToDevice, s->st));
+  if (s->geomf)
+    launch_to_f32((long long)G_NCOMP * n2d, s->geom + (long long)loc * G_NCOMP * n2d,
+                  s->geomf + (long long)loc * G_NCOMP * n2d, s->st);
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s->st));
   return GRMHD_OK;
 }

@@ -109,6 +109,8 @@ __global__ void k_geometry(GeomArgs A) {
     out[G_ALPHA * n2d + ij] = al;
     out[G_IALPHA * n2d + ij] = 1.0 / al;
     out[G_IGDET * n2d + ij] = 1.0 / gd;
+    // 1 - alpha = (1 - alpha^2)/(1 + alpha) with alpha^2 = -1/g^{tt}: no cancellation
+    out[G_OMALPHA * n2d + ij] = (1.0 + 1.0 / gi[0][0]) / (1.0 + al);
     if (loc != LOC_CENT) continue;
     // connection at the centre: derivatives along X1, X2 (X3: the metric does
     // not depend on it, so that derivative is exactly zero)

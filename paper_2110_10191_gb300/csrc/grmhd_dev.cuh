@@ -31,7 +31,8 @@ constexpr int G_GDET = 20;   // sqrt(-g)
 constexpr int G_ALPHA = 21;  // lapse 1/sqrt(-g^{tt})
 constexpr int G_IALPHA = 22; // 1/lapse
 constexpr int G_IGDET = 23;  // 1/sqrt(-g)
-constexpr int G_NCOMP = 24;
+constexpr int G_OMALPHA = 24; // 1 - lapse, formed in FP64 (for the FP32 energy flux)
+constexpr int G_NCOMP = 25;
 constexpr int C_NCOMP = 40;  // connection Gamma^l_{(m n)}: l*10 + SY(m,n)
 enum { LOC_CENT = 0, LOC_FACE1 = 1, LOC_FACE2 = 2, NLOC = 3 };
 

@@ -55,6 +55,12 @@ void launch_recon(const StepArgs &A, int dir, const double *P, double *Lf, doubl
                   cudaStream_t st);
 void launch_face(const StepArgs &A, int dir, double *F, const double *Lf, const double *Rf,
                  cudaStream_t st);
+// mixed precision: FP32 copies and the FP32 flux stage (fluxes written in FP64)
+void launch_to_f32(long long n, const double *src, float *dst, cudaStream_t st);
+void launch_recon_f32(const StepArgs &A, int dir, const float *P, float *Lf, float *Rf,
+                      cudaStream_t st);
+void launch_face_f32(const StepArgs &A, int dir, const float *geomf, double *F, const float *Lf,
+                     const float *Rf, cudaStream_t st);
 // time step from clk->ctop_bits (stage 1 only)
 void launch_dt(const StepArgs &A, cudaStream_t st);
 // boundary flux fixes + flux-CT (emf scratch: 3 x ntot)

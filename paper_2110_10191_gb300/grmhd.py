@@ -43,10 +43,13 @@ class grmhd_metric(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("hslope", ctypes.c_double)]
 
 
+PREC_FP64, PREC_MIXED = 0, 1
+
+
 class grmhd_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("t_final", ctypes.c_double),
                 ("recon", ctypes.c_int), ("floors_on", ctypes.c_int),
-                ("bc", (ctypes.c_int * 2) * 3)]
+                ("bc", (ctypes.c_int * 2) * 3), ("precision", ctypes.c_int)]
 
 
 KCLASSES = ["flux", "dt", "ct", "update", "fixup", "bounds", "other", "recon"]
@@ -152,6 +155,7 @@ def _structs(pr):
     for d in range(3):
         for s in range(2):
             p.bc[d][s] = int(pr.bc[d][s])
+    p.precision = int(getattr(pr, "precision", PREC_FP64))
     return g, m, p
 
 
@@ -185,15 +189,7 @@ class Sim:
         pr = problem
         self.n = tuple(int(x) for x in pr.n)
         self.s = tuple(x + 2 * NG for x in self.n)
-        g = grmhd_grid(self.n[0], self.n[1], self.n[2], pr.xmin[0], pr.xmax[0], pr.xmin[1],
-                       pr.xmax[1], pr.xmin[2], pr.xmax[2])
-        m = grmhd_metric(int(pr.metric), float(pr.a), float(pr.hslope))
-        p = grmhd_params()
-        p.gamma, p.cfl, p.t_final = float(pr.gamma), float(pr.cfl), float(pr.t_final)
-        p.recon, p.floors_on = int(pr.recon), int(pr.floors)
-        for d in range(3):
-            for s in range(2):
-                p.bc[d][s] = int(pr.bc[d][s])
+        g, m, p = _structs(pr)
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
         self.h = ctypes.c_void_p()

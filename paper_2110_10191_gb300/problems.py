@@ -56,6 +56,7 @@ class Problem:
     bc: tuple                    # ((x1 lo, x1 hi), (x2 lo, x2 hi), (x3 lo, x3 hi))
     P: np.ndarray                # [8][n3][n2][n1] float64
     info: dict = dataclasses.field(default_factory=dict)
+    precision: int = 0           # 0 FP64, 1 mixed (FP32 reconstruction and fluxes)
     exact: Optional[Callable[[float], np.ndarray]] = None
 
     @property

@@ -1,0 +1,108 @@
+"""Mixed-precision mode (FP32 reconstruction, fluid states, signal speeds
+and LLF fluxes; FP64 geometry, flux-CT, update, 1D_W inversion, bounds):
+its error against the FP64 oracle, div B at round-off, second-order
+convergence of the linear mode."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_10191_gb300 import problems as pb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def grmhd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2110_10191_gb300 import grmhd as g
+    g.load()
+    return g
+
+
+def _scales(b):
+    sc = [max(np.abs(b[v]).max() for v in grp) for grp in ((0,), (1,), (2, 3, 4), (5, 6, 7))]
+    sc[2] = max(sc[2], 1.0)
+    return [sc[0], sc[1], sc[2], sc[2], sc[2], sc[3], sc[3], sc[3]]
+
+
+def corner_divb(P, gdet, dx, n):
+    """max |corner-centred div(sqrt(-g) B)| over interior corners."""
+    GB = P[5:8] * gdet[None, None]
+    ng = 3
+    def box(comp, off, d):
+        tot = 0.0
+        for a in (0, -1):
+            for b in (0, -1):
+                o3 = [a, b]
+                o3.insert(d, off)
+                tot = tot + GB[comp][ng + o3[2]: ng + n[2] + o3[2], ng + o3[1]: ng + n[1] + o3[1],
+                                     ng + o3[0]: ng + n[0] + o3[0]]
+        return tot
+    div = 0.0
+    for d in range(3):
+        if n[d] > 1:
+            div = div + (box(d, 0, d) - box(d, -1, d)) / (4 * dx[d])
+    return np.abs(div[1:-1, 1:-1, 1:-1]).max(), np.abs(GB).max() / min(dx[d] for d in range(3) if n[d] > 1)
+
+
+def test_mixed_one_step_error_vs_fp64_oracle(grmhd):
+    pr = pb.fm_torus(32, 32, 16)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.step(1)
+    pm = pb.fm_torus(32, 32, 16)
+    pm.precision = 1
+    s = grmhd.Sim(pm)
+    for loc in range(4):
+        s.set_geom(loc, o.geom(loc))
+    s.set_prims(pm.P)
+    s.step(1)
+    a, b = s.get_prims(), o.get_prims()
+    sc = _scales(b)
+    err = [np.abs(a[v] - b[v]).max() / sc[v] for v in range(8)]
+    # FP32 fluxes: errors of order the FP32 epsilon, far below the scheme's truncation
+    assert max(err) < 1e-5, err
+    assert max(err) > 1e-12  # it is genuinely the FP32 path
+
+
+def test_mixed_divb_round_off(grmhd):
+    pr = pb.fm_torus(24, 24, 8)
+    pr.precision = 1
+    s = grmhd.Sim(pr)
+    s.set_prims(pr.P)
+    gdet = s.geom(0)[32]
+    dx = [(pr.xmax[d] - pr.xmin[d]) / pr.n[d] for d in range(3)]
+    d0, scale = corner_divb(s.get_prims(True), gdet, dx, pr.n)
+    s.step(5)
+    d1, _ = corner_divb(s.get_prims(True), gdet, dx, pr.n)
+    assert d0 <= 1e-12 * scale and d1 <= 1e-12 * scale
+
+
+def test_mixed_linear_mode_converges(grmhd):
+    errs = []
+    for n in (32, 64, 128):
+        pr = pb.linear_mode(n)
+        pr.precision = 1
+        s = grmhd.Sim(pr)
+        s.set_prims(pr.P)
+        s.step(100000)
+        errs.append(np.abs(s.get_prims() - pr.exact(pr.t_final)).mean(axis=(1, 2, 3)).sum())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders[0] > 1.7, (errs, orders)
+
+
+def test_mixed_orszag_tang_close_to_fp64(grmhd):
+    pr = pb.orszag_tang(64, recon=pb.RECON_WENO5)
+    s64 = grmhd.Sim(pr)
+    s64.set_prims(pr.P)
+    s64.step(10)
+    pm = pb.orszag_tang(64, recon=pb.RECON_WENO5)
+    pm.precision = 1
+    sm = grmhd.Sim(pm)
+    sm.set_prims(pm.P)
+    sm.step(10)
+    a, b = sm.get_prims(), s64.get_prims()
+    sc = _scales(b)
+    assert max(np.abs(a[v] - b[v]).max() / sc[v] for v in range(8)) < 1e-4
