@@ -228,6 +228,55 @@ int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *metric,
                          const grmhd_params *params, const double *P, double *F,
                          double *ctop, void *stream);
 
+/* ---- Batches: many independent grids advanced by one set of launches ----
+ *
+ * The paper scales by giving each node its own mesh block ("Scaling"
+ * section) and tests that the evolution does not depend on how the domain
+ * is split (end of its "Tests" section).  On one GPU, independent grids are
+ * the units: one launch of each kernel of the stage covers every grid of a
+ * batch, so small grids (2D problems, many served requests) do not leave
+ * most SMs idle, and a step costs the same launches whatever the number of
+ * grids (32 when every grid is FP64; mixed-precision grids add the FP32
+ * flux kernels).  Each grid keeps its own buffers, geometry, boundary
+ * conditions, reconstruction, precision, CFL time step and clock (t_final
+ * included).  A simulation stepped alone runs the same kernels as a batch
+ * of one, so a grid's state after n batched steps is bitwise its state
+ * after grmhd_step(sim, n) alone. */
+typedef struct grmhd_batch grmhd_batch; /* opaque, library-owned */
+
+typedef struct {
+  int ngrid;              /* grids in the batch */
+  long long zones;        /* interior zones over all grids */
+  int launches_per_step;  /* kernels launched per batched step (0 before the first) */
+  long long launches;     /* kernels launched by grmhd_batch_step so far */
+  int graph;              /* 1 once a CUDA graph of the step has been captured */
+} grmhd_batch_info;
+
+/* Group nsims simulations (created by grmhd_create on the current device;
+ * each at most once) into a batch.  The batch references them and owns
+ * none: destroy the batch before any of its simulations.  It has its own
+ * CUDA stream.  GRMHD_ERR_INVALID: a NULL or repeated simulation, or more
+ * than 2^31 - 1 blocks in one launch. */
+int grmhd_batch_create(grmhd_sim *const *sims, int nsims, grmhd_batch **out);
+
+/* Free the batch (its simulations are untouched).  NULL is accepted. */
+int grmhd_batch_destroy(grmhd_batch *batch);
+
+/* Advance every grid nsteps predictor-corrector steps, asynchronously:
+ * the batch's stream first waits for the work already enqueued on each
+ * member's stream, and each member's stream then waits for the batch, so
+ * calls on a member (grmhd_get_prims, grmhd_get_stats, grmhd_step) stay
+ * ordered after it.  use_graph != 0: the first call captures one step into
+ * a CUDA graph and every step replays it.  Per-grid statistics and the
+ * unrecoverable-zone check: grmhd_get_stats / grmhd_step(sim, 0, &stats). */
+int grmhd_batch_step(grmhd_batch *batch, int nsteps, int use_graph);
+
+/* Size and launch counts of the batch. */
+int grmhd_batch_get_info(grmhd_batch *batch, grmhd_batch_info *out);
+
+/* Wait for the batch's stream. */
+int grmhd_batch_sync(grmhd_batch *batch);
+
 /* Name of an error code. */
 const char *grmhd_strerror(int code);
 

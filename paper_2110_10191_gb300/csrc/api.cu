@@ -10,51 +10,33 @@
 #include "../../include/grmhd.h"
 #include "grmhd_dev.cuh"
 #include "grmhd_impl.h"
+#include "plan.h"
+#include "sim_impl.h"
 
 using namespace grmhd;
 
-struct grmhd_sim {
-  Dims D;
-  grmhd_grid grid;
-  grmhd_metric metric;
-  grmhd_params params;
-  cudaStream_t st;
-  double *P, *Ph, *F[3], *emf, *Lf, *Rf, *Uc;
-  double *geom, *conn, *floors;
-  float *Pf, *geomf;  // FP32 copies (mixed precision only)
-  int *pflag, *fflag;
-  Clock *clk;
-  unsigned long long unrec_seen, dterr_seen;
-  StepArgs A;
-  // profiling: event pairs per class, launches per class
-  int prof_on;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *prof_ev;
-  std::vector<cudaEvent_t> *ev_pool;
-  long long launches[GRMHD_NKCLASS];
-  double prof_ms[GRMHD_NKCLASS];
-};
 
-// Brackets the launches of one kernel class: counts them and, when
-// profiling, records an event pair on the stream around them.
-struct ClassScope {
+// Counts the launches of each kernel class and, when profiling, records an
+// event pair on the stream around each launch.
+struct SimHook : PlanHook {
   grmhd_sim *s;
-  int cls;
-  cudaEvent_t e0, e1;
-  ClassScope(grmhd_sim *s_, int cls_, int nlaunch) : s(s_), cls(cls_), e0(nullptr), e1(nullptr) {
+  cudaEvent_t e0;
+  explicit SimHook(grmhd_sim *s_) : s(s_), e0(nullptr) {}
+  void begin(int cls, int nlaunch) override {
     s->launches[cls] += nlaunch;
     if (s->prof_on) {
-      e0 = take_event(s);
-      e1 = take_event(s);
+      e0 = take_event();
       cudaEventRecord(e0, s->st);
     }
   }
-  ~ClassScope() {
+  void end(int cls) override {
     if (s->prof_on) {
+      cudaEvent_t e1 = take_event();
       cudaEventRecord(e1, s->st);
       s->prof_ev->push_back({cls, {e0, e1}});
     }
   }
-  static cudaEvent_t take_event(grmhd_sim *s) {
+  cudaEvent_t take_event() {
     if (!s->ev_pool->empty()) {
       cudaEvent_t e = s->ev_pool->back();
       s->ev_pool->pop_back();
@@ -96,6 +78,7 @@ static void free_all(grmhd_sim *s) {
     s->prof_ev = nullptr;
     s->ev_pool = nullptr;
   }
+  plan_free(s->plan);
   double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->Lf, s->Rf, s->Uc, s->geom,
                  s->conn, s->floors};
   for (double *p : d)
@@ -234,10 +217,32 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   A.floors_on = params->floors_on;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
+  A.flat3 = (n[2] == 1 && params->bc[2][0] == GRMHD_BC_PERIODIC) ? 1 : 0;
   A.geom = s->geom;
   A.conn = s->conn;
   A.floors = s->floors;
   A.clk = s->clk;
+  StageItem it;
+  memset(&it, 0, sizeof(it));
+  it.A = A;
+  it.P = s->P;
+  it.Ph = s->Ph;
+  for (int d = 0; d < 3; d++) it.F[d] = s->F[d];
+  it.emf = s->emf;
+  it.Lf = s->Lf;
+  it.Rf = s->Rf;
+  it.Uc = s->Uc;
+  it.pflag = s->pflag;
+  it.fflag = s->fflag;
+  it.Pf = s->Pf;
+  it.geomf = s->geomf;
+  it.mixed = (params->precision == GRMHD_PREC_MIXED) ? 1 : 0;
+  rc = plan_build(s->plan, &it, 1);
+  if (rc != GRMHD_OK) {
+    free_all(s);
+    delete s;
+    return rc;
+  }
   *out = s;
   return GRMHD_OK;
 }
@@ -248,67 +253,6 @@ extern "C" int grmhd_destroy(grmhd_sim *s) {
   free_all(s);
   delete s;
   return GRMHD_OK;
-}
-
-static void enqueue_fluxes(grmhd_sim *s, const double *P) {
-  {
-    ClassScope c(s, GRMHD_K_OTHER, 1);
-    launch_ctop_reset(s->A, s->st);
-  }
-  if (s->params.precision == GRMHD_PREC_MIXED) {
-    float *Lf = (float *)s->Lf, *Rf = (float *)s->Rf;
-    {
-      ClassScope c(s, GRMHD_K_RECON, 1);
-      launch_to_f32((long long)NV * s->D.ntot, P, s->Pf, s->st);
-    }
-    for (int d = 0; d < 3; d++) {
-      {
-        ClassScope c(s, GRMHD_K_RECON, 1);
-        launch_recon_f32(s->A, d, s->Pf, Lf, Rf, s->st);
-      }
-      ClassScope c(s, GRMHD_K_FLUX, 1);
-      launch_face_f32(s->A, d, s->geomf, s->F[d], Lf, Rf, s->st);
-    }
-    return;
-  }
-  for (int d = 0; d < 3; d++) {
-    {
-      ClassScope c(s, GRMHD_K_RECON, 1);
-      launch_recon(s->A, d, P, s->Lf, s->Rf, s->st);
-    }
-    ClassScope c(s, GRMHD_K_FLUX, 1);
-    launch_face(s->A, d, s->F[d], s->Lf, s->Rf, s->st);
-  }
-}
-
-static void enqueue_bounds(grmhd_sim *s, double *P) {
-  ClassScope c(s, GRMHD_K_BOUNDS, 3);
-  launch_bounds(s->A, P, s->st);
-}
-
-// ucache_mode: 1 the predictor keeps U(P^n) for the corrector, 2 the
-// corrector reads it back, 0 neither (a predictor run on its own).
-static void enqueue_stage(grmhd_sim *s, const double *Pi, const double *Ps, double *Pout,
-                          double dtfac, bool first, int ucache_mode) {
-  cudaStream_t st = s->st;
-  enqueue_fluxes(s, Ps);
-  if (first) {
-    ClassScope c(s, GRMHD_K_DT, 1);
-    launch_dt(s->A, st);
-  }
-  {
-    ClassScope c(s, GRMHD_K_CT, 3);
-    launch_fix_ct(s->A, s->F, s->emf, st);
-  }
-  {
-    ClassScope c(s, GRMHD_K_UPDATE, 1);
-    launch_update(s->A, Pi, Ps, Pout, s->F, s->pflag, s->fflag, dtfac, s->Uc, ucache_mode, st);
-  }
-  {
-    ClassScope c(s, GRMHD_K_FIXUP, 1);
-    launch_fixup(s->A, Pout, s->pflag, s->fflag, st);
-  }
-  enqueue_bounds(s, Pout);
 }
 
 static int set_common(grmhd_sim *s, const double *P, int on_device, int ghost) {
@@ -323,7 +267,10 @@ static int set_common(grmhd_sim *s, const double *P, int on_device, int ghost) {
     CK(cudaMemcpyAsync(s->Ph, P, bytes, kind, s->st));  // Ph is scratch between steps
     launch_pack(D, s->Ph, s->P, 1, s->st);
   }
-  enqueue_bounds(s, s->P);
+  {
+    SimHook h(s);
+    plan_bounds(s->plan, 0, s->st, &h);
+  }
   // the ghosts of a fixed side keep their set values in both stage arrays
   CK(cudaMemcpyAsync(s->Ph, s->P, sizeof(double) * NV * (size_t)D.ntot, cudaMemcpyDeviceToDevice,
                      s->st));
@@ -380,11 +327,9 @@ static int read_stats(grmhd_sim *s, grmhd_stats *out, bool check) {
 
 extern "C" int grmhd_step(grmhd_sim *s, int nsteps, grmhd_stats *stats) {
   if (!s || nsteps < 0) return GRMHD_ERR_INVALID;
-  for (int n = 0; n < nsteps; n++) {
-    enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true, 1);   // predictor
-    enqueue_stage(s, s->P, s->Ph, s->P, 1.0, false, 2);  // corrector
-    ClassScope c(s, GRMHD_K_OTHER, 1);
-    launch_advance(s->A, s->st);
+  {
+    SimHook h(s);
+    plan_steps(s->plan, nsteps, s->st, &h);
   }
   int rc = launched();
   if (rc != GRMHD_OK) return rc;
@@ -413,21 +358,24 @@ extern "C" int grmhd_set_time(grmhd_sim *s, double t, double dt_prev, long long 
 
 extern "C" int grmhd_predictor(grmhd_sim *s) {
   if (!s) return GRMHD_ERR_INVALID;
-  enqueue_stage(s, s->P, s->P, s->Ph, 0.5, true, 0);
+  {
+    SimHook h(s);
+    plan_stage(s->plan, 0, 0, s->st, &h);
+  }
   int rc = launched();
   if (rc != GRMHD_OK) return rc;
-  double *t = s->P;
-  s->P = s->Ph;
-  s->Ph = t;
+  // P <- P^{n+1/2} (ghosts included)
+  CK(cudaMemcpyAsync(s->P, s->Ph, sizeof(double) * NV * (size_t)s->D.ntot, cudaMemcpyDeviceToDevice,
+                     s->st));
   return read_stats(s, nullptr, true);
 }
 
 extern "C" int grmhd_get_fluxes(grmhd_sim *s, double *F, double *ctop) {
   if (!s || !F) return GRMHD_ERR_INVALID;
-  enqueue_fluxes(s, s->P);
   {
-    ClassScope c(s, GRMHD_K_CT, 3);
-    launch_fix_ct(s->A, s->F, s->emf, s->st);
+    SimHook h(s);
+    plan_fluxes(s->plan, 0, s->st, &h);
+    plan_fix_ct(s->plan, s->st, &h);
   }
   int rc = launched();
   if (rc != GRMHD_OK) return rc;
@@ -451,10 +399,10 @@ extern "C" int grmhd_next_dt(grmhd_sim *s, double *dt) {
   if (!s || !dt) return GRMHD_ERR_INVALID;
   Clock c0, c1;
   CK(cudaMemcpyAsync(&c0, s->clk, sizeof(c0), cudaMemcpyDeviceToHost, s->st));
-  enqueue_fluxes(s, s->P);
   {
-    ClassScope c(s, GRMHD_K_DT, 1);
-    launch_dt(s->A, s->st);
+    SimHook h(s);
+    plan_fluxes(s->plan, 0, s->st, &h);
+    plan_clock(s->plan, 1, s->st, &h);
   }
   int rc = launched();
   if (rc != GRMHD_OK) return rc;

@@ -1,0 +1,148 @@
+// batch.cu -- the C ABI of batches: many independent grids advanced by one
+// set of launches per step.
+//
+// A batch is a launch plan (plan.h) over its member simulations' buffers:
+// each grid keeps its own buffers, geometry, boundary conditions,
+// reconstruction, precision and device clock (so its own CFL time step and
+// t_final), and the plan kernels are the ones a simulation stepped alone
+// runs, so a grid's results are bitwise those of the same grid alone.  One
+// step is the same number of launches whatever the number of grids;
+// grmhd_batch_step can capture them once into a CUDA graph and replay it.
+#include <cstring>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "../../include/grmhd.h"
+#include "grmhd_impl.h"
+#include "plan.h"
+#include "sim_impl.h"
+
+using namespace grmhd;
+
+struct grmhd_batch {
+  int ngrid;
+  std::vector<grmhd_sim *> sims;
+  std::vector<cudaStream_t> member_streams;  // distinct streams of the members
+  cudaStream_t st;                           // the batch's own stream
+  cudaEvent_t ev;
+  Plan plan;
+  int launches_per_step;
+  long long launches;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+static void batch_free(grmhd_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  plan_free(b->plan);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->st) cudaStreamDestroy(b->st);
+}
+
+extern "C" int grmhd_batch_create(grmhd_sim *const *sims, int nsims, grmhd_batch **out) {
+  if (!sims || !out || nsims < 1) return GRMHD_ERR_INVALID;
+  *out = nullptr;
+  std::set<grmhd_sim *> seen;
+  for (int g = 0; g < nsims; g++)
+    if (!sims[g] || !seen.insert(sims[g]).second) return GRMHD_ERR_INVALID;  // null or repeated
+  grmhd_batch *b = new (std::nothrow) grmhd_batch();
+  if (!b) return GRMHD_ERR_NOMEM;
+  b->ngrid = nsims;
+  b->sims.assign(sims, sims + nsims);
+  std::vector<StageItem> items(nsims);
+  for (int g = 0; g < nsims; g++) {
+    // the member's own one-grid plan item, read back from the device
+    if (cudaMemcpy(&items[g], sims[g]->plan.items, sizeof(StageItem), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      delete b;
+      return GRMHD_ERR_CUDA;
+    }
+    bool dup = false;
+    for (cudaStream_t q : b->member_streams) dup = dup || (q == sims[g]->st);
+    if (!dup) b->member_streams.push_back(sims[g]->st);
+  }
+  int rc = plan_build(b->plan, items.data(), nsims);
+  if (rc != GRMHD_OK) {
+    delete b;
+    return rc;
+  }
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    delete b;
+    return GRMHD_ERR_CUDA;
+  }
+  *out = b;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_destroy(grmhd_batch *b) {
+  if (!b) return GRMHD_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  batch_free(b);
+  delete b;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_step(grmhd_batch *b, int nsteps, int use_graph) {
+  if (!b || nsteps < 0) return GRMHD_ERR_INVALID;
+  if (nsteps == 0) return GRMHD_OK;
+  // the batch's work follows everything already enqueued for its grids
+  for (cudaStream_t q : b->member_streams) {
+    if (cudaEventRecord(b->ev, q) != cudaSuccess) return GRMHD_ERR_CUDA;
+    if (cudaStreamWaitEvent(b->st, b->ev, 0) != cudaSuccess) return GRMHD_ERR_CUDA;
+  }
+  if (use_graph && !b->exec) {
+    if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return GRMHD_ERR_CUDA;
+    const int nl = plan_steps(b->plan, 1, b->st, nullptr);
+    cudaGraph_t gph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->st, &gph);
+    if (e != cudaSuccess || !gph) {
+      if (gph) cudaGraphDestroy(gph);
+      cudaGetLastError();
+      return GRMHD_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&b->exec, gph, 0) != cudaSuccess) {
+      cudaGraphDestroy(gph);
+      b->exec = nullptr;
+      cudaGetLastError();
+      return GRMHD_ERR_CUDA;
+    }
+    b->graph = gph;
+    b->launches_per_step = nl;
+  }
+  for (int n = 0; n < nsteps; n++) {
+    if (use_graph) {
+      if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return GRMHD_ERR_CUDA;
+      b->launches += b->launches_per_step;
+    } else {
+      b->launches_per_step = plan_steps(b->plan, 1, b->st, nullptr);
+      b->launches += b->launches_per_step;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
+  // and everything enqueued for a grid later follows the batch's work
+  if (cudaEventRecord(b->ev, b->st) != cudaSuccess) return GRMHD_ERR_CUDA;
+  for (cudaStream_t q : b->member_streams)
+    if (cudaStreamWaitEvent(q, b->ev, 0) != cudaSuccess) return GRMHD_ERR_CUDA;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_get_info(grmhd_batch *b, grmhd_batch_info *out) {
+  if (!b || !out) return GRMHD_ERR_INVALID;
+  out->ngrid = b->ngrid;
+  out->zones = b->plan.zones;
+  out->launches_per_step = b->launches_per_step;
+  out->launches = b->launches;
+  out->graph = b->exec ? 1 : 0;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_sync(grmhd_batch *b) {
+  if (!b) return GRMHD_ERR_INVALID;
+  return cudaStreamSynchronize(b->st) == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}

@@ -1,0 +1,33 @@
+// sim_impl.h -- host-side state of one simulation (the opaque grmhd_sim of
+// include/grmhd.h), shared by the translation units that enqueue its work.
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "../../include/grmhd.h"
+#include "grmhd_impl.h"
+#include "plan.h"
+
+struct grmhd_sim {
+  grmhd::Dims D;
+  grmhd_grid grid;
+  grmhd_metric metric;
+  grmhd_params params;
+  cudaStream_t st;
+  double *P, *Ph, *F[3], *emf, *Lf, *Rf, *Uc;
+  double *geom, *conn, *floors;
+  float *Pf, *geomf;  // FP32 copies (mixed precision only)
+  int *pflag, *fflag;
+  grmhd::Clock *clk;
+  unsigned long long unrec_seen, dterr_seen;
+  grmhd::StepArgs A;
+  grmhd::Plan plan;  // the one-grid launch plan of the step
+  // profiling: event pairs per class, launches per class
+  int prof_on;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *prof_ev;
+  std::vector<cudaEvent_t> *ev_pool;
+  long long launches[GRMHD_NKCLASS];
+  double prof_ms[GRMHD_NKCLASS];
+};
+

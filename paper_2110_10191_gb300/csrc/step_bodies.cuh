@@ -1,0 +1,579 @@
+// step_bodies.cuh -- the per-thread bodies of the kernels of one
+// predictor-corrector stage of the HARM scheme (iharm3D, arXiv:2110.10191):
+//   bounds (ghost fill) -> zone-centric reconstruction -> face fluxes (LLF,
+//   with a warp/block max of the signal speed for the CFL step) -> dt ->
+//   boundary flux fixes -> flux-CT EMFs (Toth 2000; paper, "Implementation
+//   Notes", first paragraph) -> update + 1D_W inversion + bounds (same
+//   section) -> fixup of failed zones.
+//
+// Each body takes the step arguments of one grid and the linear index t of
+// its thread within that grid's launch range, so the same code runs in the
+// single-grid kernels (step.cu, t from blockIdx) and in the batched kernels
+// (batch.cu, t from the block's offset within its grid).  A block never
+// spans two grids: the block reductions (signal speed maxima, warp counts)
+// see the threads of one grid only.
+//
+// Every thread owns one face, edge or zone; fields are SoA float64 in HBM
+// with i fastest, so warps read and write 256-byte contiguous runs.
+//
+// Flat X3 (A.flat3: n3 = 1 with periodic X3): every k layer of the
+// primitives is an exact copy of the single interior layer, so the fluxes
+// along X1 and X2 are computed on that layer only and copied to the layers
+// above and below it (replicate_body), and the X3 faces read the primitives
+// themselves as their face states (reconstruction of constant data returns
+// the data exactly).  The results are bitwise those of the full extent.
+#pragma once
+
+#include "grmhd_dev.cuh"
+#include "grmhd_impl.h"
+
+namespace grmhd {
+
+constexpr int BS = 128;  // threads per block of every stage kernel
+
+__device__ __forceinline__ int wrap(int g, int n) {  // periodic image of ghost index g
+  int q = (g - NG) % n;
+  if (q < 0) q += n;
+  return NG + q;
+}
+
+// ---------------------------------------------------------------------------
+// Launch extents (threads per grid) of each body
+// ---------------------------------------------------------------------------
+__host__ __device__ inline long long n_bounds_x1(const Dims &D) {
+  return (long long)D.n[1] * D.n[2] * 2 * NG;
+}
+__host__ __device__ inline long long n_bounds_x2(const Dims &D) {
+  return (long long)D.s[0] * D.n[2] * 2 * NG;
+}
+__host__ __device__ inline long long n_bounds_x3(const Dims &D) { return D.n2d * 2 * NG; }
+// zones whose two face values are reconstructed along one direction
+__host__ __device__ inline long long n_recon(const Dims &D, int flat3) {
+  return (long long)(D.n[0] + 2) * (D.n[1] + 2) * (flat3 ? 1 : D.n[2] + 2);
+}
+// faces along dir: dir index NG .. n+NG, transverse NG-1 .. n+NG (flux-CT
+// needs one transverse layer on each side); flat X3 keeps the k = NG layer
+__host__ __device__ inline void face_box(const Dims &D, int dir, int flat3, int lo[3], int ext[3]) {
+  for (int e = 0; e < 3; e++) {
+    lo[e] = (e == dir) ? NG : NG - 1;
+    ext[e] = (e == dir) ? D.n[e] + 1 : D.n[e] + 2;
+  }
+  if (flat3) {
+    lo[2] = NG;
+    ext[2] = 1;
+  }
+}
+__host__ __device__ inline long long n_face(const Dims &D, int dir, int flat3) {
+  int lo[3], ext[3];
+  face_box(D, dir, flat3, lo, ext);
+  return (long long)ext[0] * ext[1] * ext[2];
+}
+__host__ __device__ inline long long n_replicate(const Dims &D) { return D.n2d * NV; }
+__host__ __device__ inline long long n_fix(const Dims &D) {
+  return (long long)((D.n[0] > D.n[1]) ? D.n[0] + 2 : D.n[1] + 2) * (D.n[2] + 2);
+}
+__host__ __device__ inline long long n_edge(const Dims &D) {
+  return (long long)(D.n[0] + 1) * (D.n[1] + 1) * (D.n[2] + 1);
+}
+__host__ __device__ inline long long n_zone(const Dims &D) {
+  return (long long)D.n[0] * D.n[1] * D.n[2];
+}
+
+// ---------------------------------------------------------------------------
+// Boundary conditions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void copy_zone(const Dims &D, double *P, long long dst, long long src) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) P[v * D.ntot + dst] = P[v * D.ntot + src];
+}
+
+// X1 ghosts for interior (j, k); one thread per (ghost layer, side, j, k)
+__device__ __forceinline__ void bounds_x1_body(const StepArgs &A, double *P, long long t) {
+  const Dims &D = A.D;
+  if (t >= n_bounds_x1(D)) return;
+  const int g = (int)(t % NG);
+  const int side = (int)((t / NG) % 2);
+  const long long r = t / (2 * NG);
+  const int j = NG + (int)(r % D.n[1]);
+  const int k = NG + (int)(r / D.n[1]);
+  const int bc = A.bc[0][side];
+  const int ig = side ? D.n[0] + NG + g : g;
+  const long long d = zid(D, ig, j, k);
+  if (bc == 0) {
+    copy_zone(D, P, d, zid(D, wrap(ig, D.n[0]), j, k));
+  } else if (bc == 1) {
+    const int ia = side ? D.n[0] + NG - 1 : NG;
+    copy_zone(D, P, d, zid(D, ia, j, k));
+    const double *gd = A.geom + (LOC_CENT * G_NCOMP + G_GDET) * D.n2d;
+    const double rs = gd[(long long)j * D.s[0] + ia] / gd[(long long)j * D.s[0] + ig];
+    P[B1 * D.ntot + d] *= rs;
+    P[B2 * D.ntot + d] *= rs;
+    P[B3 * D.ntot + d] *= rs;
+    const double u1 = P[U1 * D.ntot + d];
+    if (side == 0 ? (u1 > 0.0) : (u1 < 0.0)) P[U1 * D.ntot + d] = 0.0;
+  }
+}
+
+// X2 ghosts for all i and interior k
+__device__ __forceinline__ void bounds_x2_body(const StepArgs &A, double *P, long long t) {
+  const Dims &D = A.D;
+  if (t >= n_bounds_x2(D)) return;
+  const int i = (int)(t % D.s[0]);
+  const long long r = t / D.s[0];
+  const int g = (int)(r % NG);
+  const int side = (int)((r / NG) % 2);
+  const int k = NG + (int)(r / (2 * NG));
+  const int bc = A.bc[1][side];
+  const int jg = side ? D.n[1] + NG + g : NG - 1 - g;
+  const long long d = zid(D, i, jg, k);
+  if (bc == 0) {
+    copy_zone(D, P, d, zid(D, i, wrap(jg, D.n[1]), k));
+  } else if (bc == 2) {
+    const int jm = side ? D.n[1] + NG - 1 - g : NG + g;
+    copy_zone(D, P, d, zid(D, i, jm, k));
+    P[U2 * D.ntot + d] = -P[U2 * D.ntot + d];
+    P[B2 * D.ntot + d] = -P[B2 * D.ntot + d];
+  } else if (bc == 1) {
+    copy_zone(D, P, d, zid(D, i, side ? D.n[1] + NG - 1 : NG, k));
+  }
+}
+
+// X3 ghosts for all i, j
+__device__ __forceinline__ void bounds_x3_body(const StepArgs &A, double *P, long long t) {
+  const Dims &D = A.D;
+  const long long nrow = D.n2d;
+  if (t >= n_bounds_x3(D)) return;
+  const long long ij = t % nrow;
+  const long long r = t / nrow;
+  const int g = (int)(r % NG);
+  const int side = (int)(r / NG);
+  const int bc = A.bc[2][side];
+  const int kg = side ? D.n[2] + NG + g : NG - 1 - g;
+  const long long d = (long long)kg * D.n2d + ij;
+  if (bc == 0) {
+    copy_zone(D, P, d, (long long)wrap(kg, D.n[2]) * D.n2d + ij);
+  } else if (bc == 1) {
+    copy_zone(D, P, d, (long long)(side ? D.n[2] + NG - 1 : NG) * D.n2d + ij);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Face fluxes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_block_max(double v, unsigned long long *dst) {
+  // v >= 0: its bit pattern orders like the value
+  unsigned long long b = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
+    b = (x > b) ? x : b;
+  }
+  __shared__ unsigned long long sm[BS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = sm[0];
+    for (int q = 1; q < BS / 32; q++) m = (sm[q] > m) ? sm[q] : m;
+    if (m) atomicMax(dst, m);
+  }
+}
+
+// Zone-centric reconstruction: one thread per zone reconstructs both face
+// values of its 8 primitives along DIR (zones NG-1 .. n+NG along DIR and the
+// extended transverse range), so each zone's WENO smoothness indicators are
+// formed once.  Lf = value at the zone's low face, Rf = at its high face.
+template <int DIR, int RECON>
+__device__ __forceinline__ void recon_body(const StepArgs &A, const double *__restrict__ P,
+                                           double *__restrict__ Lf, double *__restrict__ Rf,
+                                           long long t) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2;
+  if (t >= n_recon(D, A.flat3)) return;
+  const int i = NG - 1 + (int)(t % e0);
+  const int j = NG - 1 + (int)((t / e0) % e1);
+  const int k = (A.flat3 ? NG : NG - 1) + (int)(t / ((long long)e0 * e1));
+  const long long c = zid(D, i, j, k);
+  const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const double *p = P + v * D.ntot + c;
+    double lo, hi;
+    if (RECON == 1) {
+      weno5_pair(__ldg(p - 2 * st), __ldg(p - st), __ldg(p), __ldg(p + st), __ldg(p + 2 * st), lo, hi);
+    } else {
+      const double x1 = __ldg(p), h = 0.5 * mc_slope(__ldg(p - st), x1, __ldg(p + st));
+      lo = x1 - h;
+      hi = x1 + h;
+    }
+    Lf[v * D.ntot + c] = lo;
+    Rf[v * D.ntot + c] = hi;
+  }
+}
+
+// One thread per face combines Rf of zone c-1 (left state) and Lf of zone c
+// (right state) into the LLF flux; every thread of the block must call it.
+template <int DIR>
+__device__ __forceinline__ void face_body(const StepArgs &A, const double *__restrict__ Lf,
+                                          const double *__restrict__ Rf, double *__restrict__ F,
+                                          long long t) {
+  const Dims &D = A.D;
+  int lo[3], ext[3];
+  face_box(D, DIR, A.flat3, lo, ext);
+  const long long nface = (long long)ext[0] * ext[1] * ext[2];
+  const bool active = t < nface;
+  double ctop = 0.0;
+  if (active) {
+    const int i = lo[0] + (int)(t % ext[0]);
+    const int j = lo[1] + (int)((t / ext[0]) % ext[1]);
+    const int k = lo[2] + (int)(t / ((long long)ext[0] * ext[1]));
+    const long long c = zid(D, i, j, k);
+    const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+    double PL[NV], PR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      PL[v] = __ldg(Rf + v * D.ntot + c - st);
+      PR[v] = __ldg(Lf + v * D.ntot + c);
+    }
+    const int loc = (DIR == 0) ? LOC_FACE1 : (DIR == 1) ? LOC_FACE2 : LOC_CENT;
+    Geo G;
+    load_geo(A.geom + (long long)loc * G_NCOMP * D.n2d, D.n2d, (long long)j * D.s[0] + i, G);
+    FState sL, sR;
+    fluid_state(PL, G, sL);
+    fluid_state(PR, G, sR);
+    double vmaxL, vminL, vmaxR, vminR;
+    mhd_vchar(PL, sL, G, A.gam, DIR + 1, vmaxL, vminL);
+    mhd_vchar(PR, sR, G, A.gam, DIR + 1, vmaxR, vminR);
+    const double cmax = fmax(fmax(0.0, vmaxL), vmaxR);
+    const double cmin = fmax(fmax(0.0, -vminL), -vminR);
+    const double ct = fmax(cmax, cmin);
+    // LLF: F = 1/2 sqrt(-g) [(F_L + ct U_L) + (F_R - ct U_R)]
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) acc[v] = 0.0;
+    flux_cons_acc(PL, sL, A.gam, DIR + 1, ct, acc);
+    flux_cons_acc(PR, sR, A.gam, DIR + 1, -ct, acc);
+    const double hg = 0.5 * G.gdet;
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v * D.ntot + c] = hg * acc[v];
+    bool interior = true;
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      if (e == DIR) continue;
+      const int q = (e == 0) ? i : (e == 1) ? j : k;
+      interior = interior && (q >= NG) && (q < D.n[e] + NG);
+    }
+    if (interior) ctop = ct;
+  }
+  warp_block_max(ctop, &A.clk->ctop_bits[DIR]);
+}
+
+// Flat X3: copy the k = NG layer of F1 and F2 to k = NG-1 and NG+1, and of
+// F3 to k = NG+1 (one thread per (variable, i, j)).
+__device__ __forceinline__ void replicate_body(const StepArgs &A, double *F1, double *F2, double *F3,
+                                               long long t) {
+  const Dims &D = A.D;
+  if (t >= n_replicate(D)) return;
+  const long long v = t / D.n2d, ij = t % D.n2d;
+  const long long c = v * D.ntot + NG * D.n2d + ij;
+  const double f1 = F1[c], f2 = F2[c], f3 = F3[c];
+  F1[c - D.n2d] = f1;
+  F1[c + D.n2d] = f1;
+  F2[c - D.n2d] = f2;
+  F2[c + D.n2d] = f2;
+  F3[c + D.n2d] = f3;
+}
+
+__device__ __forceinline__ void reset_ctop_body(Clock *clk) {
+  clk->ctop_bits[0] = clk->ctop_bits[1] = clk->ctop_bits[2] = 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// Time step: ndt_d = cfl dx_d / max ctop_d over directions with n_d > 1,
+// dt = 1/sum(1/ndt_d), dt <= 1.3 dt_prev, last step lands on t_final.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dt_body(const StepArgs &A) {
+  Clock *c = A.clk;
+  double inv = 0.0;
+  for (int d = 0; d < 3; d++) {
+    if (A.D.n[d] <= 1) continue;
+    const double ct = __longlong_as_double((long long)c->ctop_bits[d]);
+    if (ct > 0.0) {
+      const double ndt = __ddiv_rn(A.cfl * A.dx[d], ct);
+      inv = __dadd_rn(inv, __ddiv_rn(1.0, ndt));
+    }
+  }
+  double dt = (inv > 0.0) ? __ddiv_rn(1.0, inv) : __longlong_as_double(0x7ff0000000000000ll);
+  if (c->dt_prev > 0.0 && dt > 1.3 * c->dt_prev) dt = 1.3 * c->dt_prev;
+  if (c->t_final > 0.0 && __dadd_rn(c->t, dt) > c->t_final) dt = __dadd_rn(c->t_final, -c->t);
+  if (!isfinite(dt)) {  // every signal speed zero: no CFL step exists
+    c->counters[3] += 1;
+    dt = 0.0;
+  }
+  if (!(dt > 0.0)) dt = 0.0;
+  c->dt = dt;
+}
+
+__device__ __forceinline__ void advance_body(const StepArgs &A) {
+  Clock *c = A.clk;
+  if (c->dt > 0.0 && isfinite(c->dt)) {
+    c->t = __dadd_rn(c->t, c->dt);
+    c->dt_prev = c->dt;
+    c->steps += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary flux fixes and flux-CT
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fix_flux_body(const StepArgs &A, double *F1, double *F2, long long t) {
+  const Dims &D = A.D;
+  // polar faces: (i, k) over the extended ranges
+  const long long np = (long long)(D.n[0] + 2) * (D.n[2] + 2);
+  const long long nr = (long long)(D.n[1] + 2) * (D.n[2] + 2);
+  if (t < np) {
+    const int i = NG - 1 + (int)(t % (D.n[0] + 2));
+    const int k = NG - 1 + (int)(t / (D.n[0] + 2));
+    if (A.bc[1][0] == 2) {
+      const long long c = zid(D, i, NG, k);
+      for (int v = 0; v < NV; v++) F2[v * D.ntot + c] = 0.0;
+    }
+    if (A.bc[1][1] == 2) {
+      const long long c = zid(D, i, D.n[1] + NG, k);
+      for (int v = 0; v < NV; v++) F2[v * D.ntot + c] = 0.0;
+    }
+  }
+  if (t < nr) {
+    const int j = NG - 1 + (int)(t % (D.n[1] + 2));
+    const int k = NG - 1 + (int)(t / (D.n[1] + 2));
+    if (A.bc[0][0] == 1) {
+      double *f = F1 + RHO * D.ntot + zid(D, NG, j, k);
+      if (*f > 0.0) *f = 0.0;
+    }
+    if (A.bc[0][1] == 1) {
+      double *f = F1 + RHO * D.ntot + zid(D, D.n[0] + NG, j, k);
+      if (*f < 0.0) *f = 0.0;
+    }
+  }
+}
+
+// Edge EMFs over i, j, k in [NG, n+NG]:
+// e3 = (F1[B2] + F1[B2](j-1) - F2[B1] - F2[B1](i-1))/4, cyclic for e1, e2.
+__device__ __forceinline__ void emf_body(const StepArgs &A, const double *__restrict__ F1,
+                                         const double *__restrict__ F2,
+                                         const double *__restrict__ F3, double *__restrict__ emf,
+                                         long long t) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 1, e1 = D.n[1] + 1;
+  if (t >= n_edge(D)) return;
+  const int i = NG + (int)(t % e0);
+  const int j = NG + (int)((t / e0) % e1);
+  const int k = NG + (int)(t / ((long long)e0 * e1));
+  const long long c = zid(D, i, j, k), N = D.ntot;
+  const long long im = c - 1, jm = c - D.s[0], km = c - D.n2d;
+  emf[2 * N + c] = 0.25 * (F1[B2 * N + c] + F1[B2 * N + jm] - F2[B1 * N + c] - F2[B1 * N + im]);
+  emf[1 * N + c] = 0.25 * (F3[B1 * N + c] + F3[B1 * N + im] - F1[B3 * N + c] - F1[B3 * N + km]);
+  emf[0 * N + c] = 0.25 * (F2[B3 * N + c] + F2[B3 * N + km] - F3[B2 * N + c] - F3[B2 * N + jm]);
+}
+
+// Induction fluxes from the EMFs on every face the update reads.
+__device__ __forceinline__ void ct_body(const StepArgs &A, double *F1, double *F2, double *F3,
+                                        const double *__restrict__ emf, long long t) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 1, e1 = D.n[1] + 1;
+  if (t >= n_edge(D)) return;
+  const int i = NG + (int)(t % e0);
+  const int j = NG + (int)((t / e0) % e1);
+  const int k = NG + (int)(t / ((long long)e0 * e1));
+  const long long c = zid(D, i, j, k), N = D.ntot;
+  const double *E1 = emf, *E2 = emf + N, *E3 = emf + 2 * N;
+  const bool in1 = i < D.n[0] + NG, in2 = j < D.n[1] + NG, in3 = k < D.n[2] + NG;
+  if (in2 && in3) {  // X1 face
+    F1[B1 * N + c] = 0.0;
+    F1[B2 * N + c] = 0.5 * (E3[c] + E3[c + D.s[0]]);
+    F1[B3 * N + c] = -0.5 * (E2[c] + E2[c + D.n2d]);
+  }
+  if (in1 && in3) {  // X2 face
+    F2[B1 * N + c] = -0.5 * (E3[c] + E3[c + 1]);
+    F2[B2 * N + c] = 0.0;
+    F2[B3 * N + c] = 0.5 * (E1[c] + E1[c + D.n2d]);
+  }
+  if (in1 && in2) {  // X3 face
+    F3[B1 * N + c] = 0.5 * (E2[c] + E2[c + 1]);
+    F3[B2 * N + c] = -0.5 * (E1[c] + E1[c + D.s[0]]);
+    F3[B3 * N + c] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Update + inversion + floors, one thread per interior zone.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void count_warp(bool pred, unsigned long long *ctr) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m && (threadIdx.x & 31) == 0) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+__device__ __forceinline__ void geo_source(const double P[NV], const FState &s, const Geo &G,
+                                           const double *__restrict__ conn, long long n2d,
+                                           long long ij, double gam, double S[4]) {
+  // S_nu = sqrt(-g) T^k_l Gamma^l_{nu k}
+  const double pg = (gam - 1.0) * P[UU];
+  const double w = P[RHO] + P[UU] + pg + s.bsq;
+  const double pt = pg + 0.5 * s.bsq;
+  double T[4][4];
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+#pragma unroll
+    for (int n = 0; n < 4; n++) T[m][n] = w * s.ucon[m] * s.ucov[n] - s.bcon[m] * s.bcov[n];
+    T[m][m] += pt;
+  }
+#pragma unroll
+  for (int nu = 0; nu < 4; nu++) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int l = 0; l < 4; l++) acc += T[k][l] * __ldg(conn + (l * 10 + SY(nu, k)) * n2d + ij);
+    S[nu] = acc * G.gdet;
+  }
+}
+
+// Ucache: the predictor stores U(P^n) there and the corrector, whose P_i is
+// the same P^n, reads it back instead of recomputing it (null: neither).
+// Every thread of the block must call it (warp counters).
+__device__ __forceinline__ void update_body(const StepArgs &A, const double *Pi,
+                                            const double *__restrict__ Ps, double *Pout,
+                                            const double *__restrict__ F1,
+                                            const double *__restrict__ F2,
+                                            const double *__restrict__ F3, int *pflag, int *fflag,
+                                            double dtfac, double *Ucache, int ucache_mode,
+                                            long long t) {
+  const Dims &D = A.D;
+  const double dt = A.clk->dt;
+  if (!(dt > 0.0)) return;  // uniform across the grid: no warp divergence
+  const double dtp = dtfac * dt;
+  const long long nz = n_zone(D);
+  const bool active = t < nz;
+  int pf = 0, ff = 0;
+  if (active) {
+    const int i = NG + (int)(t % D.n[0]);
+    const int j = NG + (int)((t / D.n[0]) % D.n[1]);
+    const int k = NG + (int)(t / ((long long)D.n[0] * D.n[1]));
+    const long long c = zid(D, i, j, k), N = D.ntot;
+    const long long ij = (long long)j * D.s[0] + i;
+    Geo G;
+    load_geo(A.geom, D.n2d, ij, G);
+    double pi[NV], ps[NV], Ui[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) pi[v] = Pi[v * N + c];
+    double S[4];
+    if (Ps == Pi) {
+      FState si;
+      fluid_state(pi, G, si);
+      prim_flux(pi, si, G, A.gam, 0, Ui);
+      if (ucache_mode == 1) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ucache[v * N + c] = Ui[v];
+      }
+      geo_source(pi, si, G, A.conn, D.n2d, ij, A.gam, S);
+    } else {
+      if (ucache_mode == 2) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ui[v] = Ucache[v * N + c];
+      } else {
+        FState si;
+        fluid_state(pi, G, si);
+        prim_flux(pi, si, G, A.gam, 0, Ui);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; v++) ps[v] = Ps[v * N + c];
+      FState ss;
+      fluid_state(ps, G, ss);
+      geo_source(ps, ss, G, A.conn, D.n2d, ij, A.gam, S);
+    }
+    const double idx1 = A.idx[0], idx2 = A.idx[1], idx3 = A.idx[2];
+    double Un[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const long long o = v * N + c;
+      const double div = (F1[o + 1] - F1[o]) * idx1 + (F2[o + D.s[0]] - F2[o]) * idx2 +
+                         (F3[o + D.n2d] - F3[o]) * idx3;
+      const double src = (v >= UU && v <= U3) ? S[v - UU] : 0.0;
+      Un[v] = Ui[v] + dtp * (src - div);
+    }
+    double pn[NV], bsq_n = 0.0, lor_n = 1.0;
+    pf = invert_1dw(Un, G, A.gam, A.igam, pi, pn, bsq_n, lor_n);
+    if (pf == PF_OK && A.floors_on)
+      ff = apply_floors_known(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
+                              bsq_n, lor_n);
+#pragma unroll
+    for (int v = 0; v < NV; v++) Pout[v * N + c] = pn[v];
+    pflag[c] = pf;
+    fflag[c] = ff;
+  }
+  count_warp(active && pf != 0, &A.clk->counters[0]);
+  count_warp(active && ff != 0, &A.clk->counters[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Fixup: a failed zone takes the mean of rho, u, utilde over the non-failed
+// interior zones of its 3x3x3 neighbourhood (B is kept), then the bounds.
+// Every thread of the block must call it (warp counters).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fixup_body(const StepArgs &A, double *P, const int *__restrict__ pflag,
+                                           int *fflag, long long t) {
+  const Dims &D = A.D;
+  if (!(A.clk->dt > 0.0)) return;
+  const long long nz = n_zone(D);
+  const bool active = t < nz;
+  bool hit = false, lost = false;
+  if (active) {
+    const int i = NG + (int)(t % D.n[0]);
+    const int j = NG + (int)((t / D.n[0]) % D.n[1]);
+    const int k = NG + (int)(t / ((long long)D.n[0] * D.n[1]));
+    const long long c = zid(D, i, j, k), N = D.ntot;
+    if (pflag[c] != 0) {
+      double sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      int cnt = 0;
+      for (int dk = -1; dk <= 1; dk++)
+        for (int dj = -1; dj <= 1; dj++)
+          for (int di = -1; di <= 1; di++) {
+            if (di == 0 && dj == 0 && dk == 0) continue;
+            const int ii = i + di, jj = j + dj, kk = k + dk;
+            if (ii < NG || ii >= D.n[0] + NG || jj < NG || jj >= D.n[1] + NG || kk < NG ||
+                kk >= D.n[2] + NG)
+              continue;
+            const long long nb = zid(D, ii, jj, kk);
+            if (pflag[nb] != 0) continue;
+#pragma unroll
+            for (int v = 0; v < 5; v++) sum[v] += P[v * N + nb];
+            cnt++;
+          }
+      if (cnt == 0) {
+        lost = true;
+      } else {
+        double p[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) p[v] = P[v * N + c];
+#pragma unroll
+        for (int v = 0; v < 5; v++) p[v] = sum[v] / (double)cnt;
+        if (A.floors_on) {
+          const long long ij = (long long)j * D.s[0] + i;
+          Geo G;
+          load_geo(A.geom, D.n2d, ij, G);
+          const int f = apply_floors(p, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam);
+          if (f) {
+            fflag[c] |= f;
+            hit = true;
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) P[v * N + c] = p[v];
+      }
+    }
+  }
+  count_warp(hit, &A.clk->counters[1]);
+  count_warp(lost, &A.clk->counters[2]);
+}
+
+}  // namespace grmhd

@@ -68,11 +68,21 @@ class grmhd_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class grmhd_batch_info(ctypes.Structure):
+    _fields_ = [("ngrid", ctypes.c_int), ("zones", ctypes.c_longlong),
+                ("launches_per_step", ctypes.c_int), ("launches", ctypes.c_longlong),
+                ("graph", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_ghost",
            "grmhd_get_prims", "grmhd_step", "grmhd_get_stats", "grmhd_set_time",
            "grmhd_predictor", "grmhd_get_fluxes", "grmhd_next_dt", "grmhd_get_flags",
-           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_fluxes_noalloc", "grmhd_profile", "grmhd_get_profile", "grmhd_fp64_peak",
-           "grmhd_strerror"]
+           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_profile", "grmhd_get_profile",
+           "grmhd_fp64_peak", "grmhd_fluxes_noalloc", "grmhd_batch_create", "grmhd_batch_destroy",
+           "grmhd_batch_step", "grmhd_batch_get_info", "grmhd_batch_sync", "grmhd_strerror"]
 
 
 def lib_path() -> str:
@@ -111,6 +121,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_profile.argtypes = [vp, i]
         L.grmhd_get_profile.argtypes = [vp, P(grmhd_profile_data), i]
         L.grmhd_fp64_peak.argtypes = [ctypes.c_longlong, P(d)]
+        L.grmhd_batch_create.argtypes = [P(vp), i, P(vp)]
+        L.grmhd_batch_destroy.argtypes = [vp]
+        L.grmhd_batch_step.argtypes = [vp, i, i]
+        L.grmhd_batch_get_info.argtypes = [vp, P(grmhd_batch_info)]
+        L.grmhd_batch_sync.argtypes = [vp]
         L.grmhd_strerror.argtypes = [i]
         L.grmhd_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -296,3 +311,47 @@ class Sim:
         out = np.zeros((nc, self.s[1], self.s[0]))
         _check(self.L.grmhd_get_geometry(self.h, int(loc), out.ctypes.data), "grmhd_get_geometry")
         return out
+
+
+class Batch:
+    """Several simulations advanced together by one set of launches per
+    step (``grmhd_batch_*``).  The batch references the ``Sim`` objects and
+    keeps them alive; each grid's result is bitwise its result alone."""
+
+    def __init__(self, sims):
+        self.L = load()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        self.h = ctypes.c_void_p()
+        _check(self.L.grmhd_batch_create(arr, len(self.sims), ctypes.byref(self.h)),
+               "grmhd_batch_create")
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.grmhd_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, nsteps: int = 1, graph: bool = True, sync: bool = False) -> None:
+        _check(self.L.grmhd_batch_step(self.h, int(nsteps), int(graph)), "grmhd_batch_step")
+        if sync:
+            self.sync()
+
+    def sync(self) -> None:
+        _check(self.L.grmhd_batch_sync(self.h), "grmhd_batch_sync")
+
+    def info(self):
+        out = grmhd_batch_info()
+        _check(self.L.grmhd_batch_get_info(self.h, ctypes.byref(out)), "grmhd_batch_get_info")
+        return out.as_dict()

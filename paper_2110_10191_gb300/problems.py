@@ -19,6 +19,8 @@ Problems (all with GM = c = 1, the paper's units, "Implementation Notes"):
   poloidal field from A_phi ~ max(rho/rho_max - 0.2, 0) normalised to a
   gas-to-magnetic pressure ratio, seeded perturbation of u.
 * ``orszag_tang``  -- flat periodic Orszag-Tang vortex (batched workloads).
+* ``batch_2d``     -- many uneven flat 2D grids of modes and vortices (batched
+  workload).
 
 Random numbers come from a counter-based generator (splitmix64 of
 seed and zone index), so a zone's value does not depend on the grid split.
@@ -208,6 +210,51 @@ def orszag_tang(n: int = 128, scale: float = 1.0, gamma: float = 5.0 / 3.0, cfl:
                    xmax=(1.0, 1.0, 1.0), metric=METRIC_MINKOWSKI, a=0.0, hslope=1.0,
                    gamma=gamma, cfl=cfl, t_final=t_final, recon=recon, floors=0,
                    bc=((BC_PERIODIC,) * 2,) * 3, P=P, info={"scale": scale})
+
+
+# --------------------------------------------------------------------------
+# Many uneven flat 2D grids (batched workload)
+# --------------------------------------------------------------------------
+
+BATCH_KINDS = ("slow", "alfven", "fast", "orszag_tang")
+# integer wavenumber pairs (k = 2 pi (kx, ky) keeps the unit square periodic),
+# oblique to the background field B = (1, 0, 0) so that the slow, Alfven and
+# fast speeds are distinct and non-zero
+BATCH_WAVENUMBERS = ((1, 1), (1, -1), (1, 2), (1, -2), (2, 1), (2, -1), (2, 2), (2, -2))
+
+
+def batch_2d(ngrid: int = 64, nmin: int = 32, nmax: int = 256, seed: int = 0,
+             t_final: float = 0.0) -> list:
+    """``ngrid`` flat periodic square grids, N x N x 1 with N uniform in
+    [nmin, nmax], in equal shares of slow, Alfven and fast linear modes and
+    Orszag-Tang vortices (in a seeded order).  Modes: wavenumber pair drawn
+    from BATCH_WAVENUMBERS, amplitude log-uniform in [1e-4, 1e-2]; Orszag-Tang:
+    field scale s uniform in [0.5, 1.5].  Reconstruction MC or WENO5 with
+    probability 1/2 each.  Every draw comes from splitmix_uniform(seed,
+    8 g + field) for grid g, so grid g does not depend on ngrid."""
+    idx = np.arange(8 * ngrid, dtype=np.uint64)
+    u = splitmix_uniform(seed, idx).reshape(ngrid, 8)
+    order = np.argsort(u[:, 0], kind="stable")
+    kinds = [None] * ngrid
+    for r, g in enumerate(order):
+        kinds[g] = BATCH_KINDS[(r * len(BATCH_KINDS)) // ngrid]
+    out = []
+    for g in range(ngrid):
+        n = min(nmin + int(u[g, 1] * (nmax - nmin + 1)), nmax)
+        recon = RECON_WENO5 if u[g, 2] < 0.5 else RECON_MC
+        if kinds[g] == "orszag_tang":
+            pr = orszag_tang(n, scale=0.5 + u[g, 3], recon=recon, t_final=t_final)
+        else:
+            kx, ky = BATCH_WAVENUMBERS[min(int(u[g, 4] * len(BATCH_WAVENUMBERS)),
+                                           len(BATCH_WAVENUMBERS) - 1)]
+            amp = 10.0 ** (-4.0 + 2.0 * u[g, 5])
+            pr = linear_mode(n, kinds[g], amp=amp, kvec=(2 * math.pi * kx, 2 * math.pi * ky),
+                             recon=recon)
+            pr.t_final = t_final
+        pr.name = "g%02d_%s" % (g, pr.name)
+        pr.info["kind"] = kinds[g]
+        out.append(pr)
+    return out
 
 
 # --------------------------------------------------------------------------
