@@ -11,7 +11,11 @@ zone-cycles/s (zones advanced by one full cycle per second).
 
 N > 1 runs under torchrun, one process per GPU; every rank advances its own
 replica (the single-grid path is not decomposed), scaling "weak".  Rank 0
-prints one JSON line.
+prints one JSON line.  Besides the headline it carries the same workload in
+the mixed-precision mode ("mixed"), 64 uneven flat 2D grids stepped as one
+batch against the same grids stepped one by one ("batched"), and the
+mixed-precision error of 100 cycles of the 288x128x128 torus against the
+FP64 path ("mixed_accuracy"); --no-extras skips them.
 """
 import argparse
 import json
@@ -37,6 +41,28 @@ WORKLOADS = {
                      r_out=1000.0),
     "mode64": dict(n=(64, 64, 1), recon=0, label="linear_fast_mode_64x64_mc_fp64"),
 }
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each FP64-bound kernel class on the 128^3 torus, from the ncu captures whose
+# summaries are under profiles/ (kp_recon<0>, kp_face<0>, kp_update).  The
+# figures hold while the kernel sources hash to SRC_HASH; otherwise the
+# bench reports the traffic as unknown (null).
+NCU_TRAFFIC = {"src_hash": "571b3679352ec592",
+               "torus128": {"recon": 152246272 + 229885440, "flux": 297845504 + 113438976,
+                            "update": 593725184 + 271228160}}
+
+
+def kernel_source_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2110_10191_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def make_problem(name, n3_override=None):
@@ -182,6 +208,145 @@ def reference_arm(args, rank, world):
     print(json.dumps(line))
 
 
+def reduce_max(x, world, device):
+    """The maximum of x over the ranks of the default process group (the
+    slowest rank's time); x itself when world == 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(zones_per_rank, steps, world, seconds):
+    """Whole-job zone-cycles/s: every rank advances its own replica of
+    zones_per_rank zones by `steps` cycles; seconds is the slowest rank's."""
+    return world * zones_per_rank * steps / seconds
+
+
+def _timed(stream, fn):
+    """Device time (ms) of the work fn enqueues on stream."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def mixed_throughput(grmhd, pr, steps, warmup, stream):
+    """The same workload in the mixed-precision mode."""
+    import dataclasses
+    pm = dataclasses.replace(pr, precision=1)
+    s = grmhd.Sim(pm, stream=stream)
+    s.set_prims(pm.P)
+    s.step(warmup)
+    ms = _timed(stream, lambda: s.step(steps, sync=False))
+    s.close()
+    z = pr.n[0] * pr.n[1] * pr.n[2]
+    return {"value": z * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "dtype": "mixed: FP32 reconstruction, fluid states, signal speeds, LLF fluxes; "
+                     "FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
+            "steps": steps}
+
+
+def batched_throughput(grmhd, steps, warmup, stream):
+    """64 uneven flat 2D grids (slow/Alfven/fast modes, Orszag-Tang) stepped
+    as one batch (one CUDA graph per step) and, for comparison, one after
+    the other as single simulations."""
+    from paper_2110_10191_gb300 import problems as pb
+    probs = pb.batch_2d(ngrid=64, nmin=32, nmax=256, seed=0)
+    zones = sum(p.zones for p in probs)
+    sims = [grmhd.Sim(p, stream=stream) for p in probs]
+    for s, p in zip(sims, probs):
+        s.set_prims(p.P)
+        s.step(warmup, sync=False)
+    ms_single = _timed(stream, lambda: [s.step(steps, sync=False) for s in sims])
+    b = grmhd.Batch(sims)
+    b.step(warmup, graph=True, sync=True)
+    l0 = b.info()["launches"]
+    ms_batch = _timed(stream, lambda: b.step(steps, graph=True))
+    info = b.info()
+    b.close()
+    for s in sims:
+        s.close()
+    return {"workload": "64 flat periodic 2D grids, N uniform in [32, 256] (seed 0), equal shares of "
+                        "slow/Alfven/fast linear modes and Orszag-Tang vortices, MC or WENO5 per grid",
+            "zones": zones, "value": zones * steps / (ms_batch * 1e-3), "unit": UNIT,
+            "ms_per_step": ms_batch / steps, "launches_per_step": info["launches_per_step"],
+            "gpu_launches": info["launches"] - l0, "cuda_graph": bool(info["graph"]),
+            "singles_value": zones * steps / (ms_single * 1e-3),
+            "singles_ms_per_step": ms_single / steps,
+            "speedup_vs_singles": ms_single / ms_batch, "steps": steps}
+
+
+def corner_divb(P, gdet, dx, n):
+    """max |div(sqrt(-g) B)| at interior zone corners, the discrete
+    divergence flux-CT keeps at round-off, and the scale max|sqrt(-g) B|/dx."""
+    import numpy as np
+    GB = P[5:8] * gdet[None, None]
+    ng = 3
+
+    def box(comp, off, d):
+        tot = 0.0
+        for a in (0, -1):
+            for b in (0, -1):
+                o3 = [a, b]
+                o3.insert(d, off)
+                tot = tot + GB[comp][ng + o3[2]: ng + n[2] + o3[2], ng + o3[1]: ng + n[1] + o3[1],
+                                     ng + o3[0]: ng + n[0] + o3[0]]
+        return tot
+    div = 0.0
+    for d in range(3):
+        if n[d] > 1:
+            div = div + (box(d, 0, d) - box(d, -1, d)) / (4 * dx[d])
+    return (float(np.abs(div[1:-1, 1:-1, 1:-1]).max()),
+            float(np.abs(GB).max() / min(dx[d] for d in range(3) if n[d] > 1)))
+
+
+def mixed_accuracy(grmhd, steps, stream):
+    """The 288x128x128 torus (R_out = 1000) advanced `steps` cycles in FP64
+    and in the mixed mode: per-primitive L1 and Linf of the difference,
+    relative to the FP64 state's mean |value| and max |value|, and the
+    corner divergence of both."""
+    import dataclasses
+    import numpy as np
+    pr = make_problem("torus288")
+    out = {}
+    states = {}
+    for prec in (0, 1):
+        p = dataclasses.replace(pr, precision=prec)
+        s = grmhd.Sim(p, stream=stream)
+        s.set_prims(p.P)
+        s.step(steps)
+        states[prec] = s.get_prims(with_ghosts=True)
+        gdet = s.geom(0)[32]
+        s.close()
+    names = ["rho", "u", "u1", "u2", "u3", "B1", "B2", "B3"]
+    a, b = states[1][:, 3:-3, 3:-3, 3:-3], states[0][:, 3:-3, 3:-3, 3:-3]
+    body = b[0] > 1e-2  # the torus itself (max rho = 1), without the floor-held atmosphere
+    for v, nm in enumerate(names):
+        d = np.abs(a[v] - b[v])
+        out[nm] = {"l1_rel": float(d.mean() / max(np.abs(b[v]).mean(), 1e-300)),
+                   "linf_rel": float(d.max() / max(np.abs(b[v]).max(), 1e-300)),
+                   "torus_l1_rel": float(d[body].mean() / max(np.abs(b[v][body]).mean(), 1e-300)),
+                   "torus_linf_rel": float(d[body].max() / max(np.abs(b[v][body]).max(), 1e-300))}
+    dx = [(pr.xmax[d] - pr.xmin[d]) / pr.n[d] for d in range(3)]
+    for prec, key in ((0, "divb_fp64"), (1, "divb_mixed")):
+        m, sc = corner_divb(states[prec], gdet, dx, pr.n)
+        out[key] = {"max": m, "scale": sc, "rel": m / sc}
+    return {"workload": WORKLOADS["torus288"]["label"].replace("_fp64", ""), "steps": steps,
+            "reference": "the FP64 path (parity-tested against the FP64 oracle)",
+            "norms": "l1_rel: mean |mixed - fp64| / mean |fp64|, linf_rel: max / max, over all "
+                     "interior zones; torus_*: over zones with rho > 1e-2",
+            "primitives": out}
+
+
 def workload_config(name):
     w = WORKLOADS[name]
     cfg = {"workload": w["label"], "grid": list(w["n"]), "dtype": "fp64",
@@ -204,6 +369,9 @@ def main():
     ap.add_argument("--config", default="torus128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision, batched and accuracy legs")
+    ap.add_argument("--accuracy-steps", type=int, default=100)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -253,11 +421,8 @@ def main():
     sim.profile(False)
     clk = clocks.stop()
     st = sim.stats()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * zones * args.steps / (ms * 1e-3)
+    ms = reduce_max(ms, world, "cuda")
+    value = job_value(zones, args.steps, world, ms * 1e-3)
 
     # ---- end to end through the C ABI with host buffers ----
     io_bytes = 8 * 8 * zones
@@ -276,13 +441,17 @@ def main():
         sim2.get_prims(out=host_out)
         t1 = time.perf_counter()
         e2e_s = t1 - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = reduce_max(e2e_s, world, "cuda")
         sim2.close()
 
     peak_fp64 = grmhd.fp64_peak(1 << 16)
+
+    extras = {}
+    if not args.no_extras:
+        extras["mixed"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream)
+        extras["batched"] = batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, stream)
+        if rank == 0:
+            extras["mixed_accuracy"] = mixed_accuracy(grmhd, args.accuracy_steps, stream)
 
     if rank != 0:
         if world > 1:
@@ -304,16 +473,20 @@ def main():
                 hbm = float(json.load(f)["hbm_gbs"]) * 1e9
         except (OSError, KeyError, ValueError):
             pass
-        # algorithmic work and bytes per launch of each FP64-bound kernel class
+        # algorithmic work and bytes per launch of each FP64-bound kernel class:
+        # face: two states in, one flux out (24 doubles per face); recon: the
+        # primitives in, two face values out (24 doubles per zone of the
+        # extended range); update: predictor 48, corrector 56 doubles per zone
         work = {
-            "flux": ("k_face (LLF face fluxes from reconstructed states)",
-                     cpu["_face_flops_per_face"] * sum(faces) / 3.0, 16 * 8 * sum(faces) / 3.0),
-            "recon": ("k_recon (WENO5 face states, both faces of every zone)",
+            "flux": ("kp_face (LLF face fluxes from reconstructed states)",
+                     cpu["_face_flops_per_face"] * sum(faces) / 3.0, 24 * 8 * sum(faces) / 3.0),
+            "recon": ("kp_recon (WENO5 face states, both faces of every zone)",
                       cpu["_recon_flops_per_face"] * sum(faces) / 3.0,
                       24 * 8 * (pr.n[0] + 2) * (pr.n[1] + 2) * (pr.n[2] + 2)),
-            "update": ("k_update (conserved update + 1D_W inversion + bounds)",
-                       cpu["_update_flops_per_zone_stage"] * zones, 8 * (8 * 2 + 8 * 6 + 8) * zones),
+            "update": ("kp_update (conserved update + 1D_W inversion + bounds)",
+                       cpu["_update_flops_per_zone_stage"] * zones, 52 * 8 * zones),
         }
+        traffic = NCU_TRAFFIC.get(args.config) if kernel_source_hash() == NCU_TRAFFIC["src_hash"] else None
         for cls, (label, flops, nbytes) in work.items():
             ms_c, n_c = prof[cls]
             if not n_c:
@@ -322,7 +495,9 @@ def main():
             kernels[cls] = {"kernel": label, "avg_launch_ms": avg, "launches": n_c,
                             "achieved_tflops": flops / (avg * 1e-3) / 1e12,
                             "frac": flops / (avg * 1e-3) / peak_fp64,
-                            "hbm_frac": nbytes / (avg * 1e-3) / hbm}
+                            "hbm_frac": nbytes / (avg * 1e-3) / hbm,
+                            "algorithmic_bytes": nbytes,
+                            "traffic": None if traffic is None else traffic.get(cls)}
         dom = max(kernels, key=lambda k: prof[k][0]) if kernels else None
         if dom:
             kd = kernels[dom]
@@ -333,13 +508,15 @@ def main():
                                        "nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz = 1.259",
                         "work": "algorithmic FP64 flops of the oracle's counting build",
                         "avg_launch_ms": kd["avg_launch_ms"], "hbm_frac": kd["hbm_frac"],
-                        "traffic": None}
+                        "algorithmic_bytes": kd["algorithmic_bytes"], "traffic": kd["traffic"],
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one "
+                                          "launch, profiles/%s_fm_torus_128.md" % kd["kernel"].split()[0]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.config),
             "e2e": None if e2e_s is None else {
-                "value": world * zones * args.steps / e2e_s, "unit": UNIT,
+                "value": job_value(zones, args.steps, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes / args.steps,
                 "d2h_bytes_per_step": io_bytes / args.steps,
                 "note": "set_prims(pinned host) + %d steps + get_prims(pinned host) per job"
@@ -353,6 +530,7 @@ def main():
             "clocks": clk,
             "sim": {"t": st["t"], "steps": st["steps"], "inv_failures": st["inv_failures"],
                     "floor_hits": st["floor_hits"]}}
+    line.update(extras)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -104,3 +104,35 @@ def test_michel_solution():
     assert abs(ur[4]) == pytest.approx(math.sqrt(1 / 16.0), rel=1e-6)
     T = (4 / 3 - 1) * u / rho
     assert np.all(np.diff(T) < 0) and np.all(ur < 0)
+
+
+def test_batch_2d_recipe():
+    """64 grids: N in [32, 256], equal quarters of the four kinds, modes on
+    oblique integer wavenumbers with amplitude in [1e-4, 1e-2], vortex scale
+    in [0.5, 1.5], deterministic, and grid g independent of the grid count."""
+    import collections
+    probs = pb.batch_2d()
+    assert len(probs) == 64
+    kinds = collections.Counter(p.info["kind"] for p in probs)
+    assert kinds == {k: 16 for k in pb.BATCH_KINDS}
+    for p in probs:
+        n1, n2, n3 = p.n
+        assert n1 == n2 and n3 == 1 and 32 <= n1 <= 256
+        assert p.metric == pb.METRIC_MINKOWSKI and p.bc == ((pb.BC_PERIODIC,) * 2,) * 3
+        assert p.P.shape == (8, 1, n1, n1) and np.isfinite(p.P).all()
+        if p.info["kind"] == "orszag_tang":
+            assert 0.5 <= p.info["scale"] <= 1.5
+        else:
+            assert 1e-4 <= p.info["amp"] <= 1e-2
+            kx, ky = (k / (2 * np.pi) for k in p.info["k"])
+            assert (round(kx), round(ky)) in pb.BATCH_WAVENUMBERS
+            # the mode is the requested branch: slow < Alfven < fast
+            lam = sorted(x for x in p.info["eigenvalues"] if x > 1e-10)
+            pos = {"slow": 0, "alfven": 1, "fast": len(lam) - 1}[p.info["kind"]]
+            assert p.info["speed"] == pytest.approx(lam[pos])
+    again = pb.batch_2d()
+    assert all(np.array_equal(a.P, b.P) for a, b in zip(probs, again))
+    few = pb.batch_2d(ngrid=8)
+    # the kind shares depend on ngrid; sizes, reconstruction and draws do not
+    assert [p.n for p in few] == [p.n for p in probs[:8]]
+    assert [p.recon for p in few] == [p.recon for p in probs[:8]]
