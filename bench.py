@@ -48,9 +48,9 @@ WORKLOADS = {
 # summaries are under profiles/ (kp_recon<0>, kp_face<0>, kp_update).  The
 # figures hold while the kernel sources hash to SRC_HASH; otherwise the
 # bench reports the traffic as unknown (null).
-NCU_TRAFFIC = {"src_hash": "571b3679352ec592",
-               "torus128": {"recon": 152246272 + 229885440, "flux": 297845504 + 113438976,
-                            "update": 593725184 + 271228160}}
+NCU_TRAFFIC = {"src_hash": "76d8c53e2dfa0d22",
+               "torus128": {"recon": 152427520 + 229693440, "flux": 297958912 + 113437696,
+                            "update": 593855488 + 271379200}}
 # sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of the same
 # captures (the hardware's view of the same launches)
 NCU_FP64_PIPE = {"torus128": {"recon": 0.855, "flux": 0.889, "update": 0.887}}
@@ -258,12 +258,12 @@ def mixed_throughput(grmhd, pr, steps, warmup, stream):
             "steps": steps}
 
 
-def batched_throughput(grmhd, steps, warmup, stream):
+def batched_throughput(grmhd, steps, warmup, stream, nmin=32, nmax=256):
     """64 uneven flat 2D grids (slow/Alfven/fast modes, Orszag-Tang) stepped
-    as one batch (one CUDA graph per step) and, for comparison, one after
-    the other as single simulations."""
+    as one batch (one CUDA graph per step), before and after the autotuner,
+    and, for comparison, one after the other as single simulations."""
     from paper_2110_10191_gb300 import problems as pb
-    probs = pb.batch_2d(ngrid=64, nmin=32, nmax=256, seed=0)
+    probs = pb.batch_2d(ngrid=64, nmin=nmin, nmax=nmax, seed=0)
     zones = sum(p.zones for p in probs)
     sims = [grmhd.Sim(p, stream=stream) for p in probs]
     for s, p in zip(sims, probs):
@@ -272,17 +272,22 @@ def batched_throughput(grmhd, steps, warmup, stream):
     ms_single = _timed(stream, lambda: [s.step(steps, sync=False) for s in sims])
     b = grmhd.Batch(sims)
     b.step(warmup, graph=True, sync=True)
+    ms_untuned = _timed(stream, lambda: b.step(steps, graph=True))
+    b.autotune(trials=3)
+    b.step(1, graph=True, sync=True)
     l0 = b.info()["launches"]
     ms_batch = _timed(stream, lambda: b.step(steps, graph=True))
     info = b.info()
     b.close()
     for s in sims:
         s.close()
-    return {"workload": "64 flat periodic 2D grids, N uniform in [32, 256] (seed 0), equal shares of "
-                        "slow/Alfven/fast linear modes and Orszag-Tang vortices, MC or WENO5 per grid",
+    return {"workload": "64 flat periodic 2D grids, N uniform in [%d, %d] (seed 0), equal shares of "
+                        "slow/Alfven/fast linear modes and Orszag-Tang vortices, MC or WENO5 per grid"
+                        % (nmin, nmax),
             "zones": zones, "value": zones * steps / (ms_batch * 1e-3), "unit": UNIT,
             "ms_per_step": ms_batch / steps, "launches_per_step": info["launches_per_step"],
             "gpu_launches": info["launches"] - l0, "cuda_graph": bool(info["graph"]),
+            "autotuned": bool(info["tuned"]), "untuned_ms_per_step": ms_untuned / steps,
             "singles_value": zones * steps / (ms_single * 1e-3),
             "singles_ms_per_step": ms_single / steps,
             "speedup_vs_singles": ms_single / ms_batch, "steps": steps}
@@ -459,6 +464,8 @@ def main():
     if not args.no_extras:
         extras["mixed"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream)
         extras["batched"] = batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, stream)
+        extras["batched_small"] = batched_throughput(grmhd, args.steps, args.warmup, stream,
+                                                     nmin=32, nmax=48)
         if rank == 0:
             extras["mixed_accuracy"] = mixed_accuracy(grmhd, args.accuracy_steps, stream)
 

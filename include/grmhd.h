@@ -195,6 +195,18 @@ int grmhd_profile(grmhd_sim *sim, int enable);
  * the last reset; reset != 0 clears them afterwards. */
 int grmhd_get_profile(grmhd_sim *sim, grmhd_profile_data *out, int reset);
 
+/* Autotuner: pick, by timing on the simulation's stream, the threads per
+ * block (64, 128 or 256) of each heavy kernel of the step (reconstruction,
+ * face fluxes, update + fixup, in the simulation's precision).  Results do
+ * not depend on the choice: each thread computes the same zone or face
+ * whatever the block size.  The trial launches write only scratch (face
+ * values, fluxes, the interior of the half-step array) and the inversion
+ * and bound flags of the last stage; the state and the clock are left as
+ * they were.  Synchronises the device.  trials >= 1 timed passes per
+ * candidate; *ms_before / *ms_after (either may be NULL): one pass of the
+ * tuned kernels with the previous and the chosen settings. */
+int grmhd_autotune(grmhd_sim *sim, int trials, double *ms_before, double *ms_after);
+
 /* Measured double-precision FMA throughput of the current device: runs a
  * dependency-free DFMA kernel for about `iters` FMAs per thread on every SM
  * and returns FLOP/s (2 per FMA) in *flops.  Used as the roofline peak of
@@ -250,6 +262,7 @@ typedef struct {
   int launches_per_step;  /* kernels launched per batched step (0 before the first) */
   long long launches;     /* kernels launched by grmhd_batch_step so far */
   int graph;              /* 1 once a CUDA graph of the step has been captured */
+  int tuned;              /* 1 after grmhd_batch_autotune */
 } grmhd_batch_info;
 
 /* Group nsims simulations (created by grmhd_create on the current device;
@@ -270,6 +283,25 @@ int grmhd_batch_destroy(grmhd_batch *batch);
  * a CUDA graph and every step replays it.  Per-grid statistics and the
  * unrecoverable-zone check: grmhd_get_stats / grmhd_step(sim, 0, &stats). */
 int grmhd_batch_step(grmhd_batch *batch, int nsteps, int use_graph);
+
+/* The autotuner of grmhd_autotune over the batch's launches: per heavy
+ * kernel, the threads per block (64, 128, 256) and the order in which the
+ * grids' blocks are issued (plan order; largest grid first; round robin
+ * over the grids).  Results do not depend on either choice.  A captured
+ * graph is dropped and captured again at the next graph step. */
+int grmhd_batch_autotune(grmhd_batch *batch, int trials, double *ms_before, double *ms_after);
+
+/* Block orders for grmhd_batch_set_launch. */
+#define GRMHD_ORDER_GRID 0 /* grids in batch order, each grid's blocks together */
+#define GRMHD_ORDER_LPT 1  /* grids by decreasing block count (largest first) */
+#define GRMHD_ORDER_RR 2   /* round robin: one block of each grid in turn */
+
+/* Set by hand what grmhd_batch_autotune picks, for the kernels of class
+ * kclass (GRMHD_K_RECON, GRMHD_K_FLUX or GRMHD_K_UPDATE; the update's
+ * class also sets the fixup): threads per block (64..256, a multiple of 32)
+ * and block order (GRMHD_ORDER_*).  Results do not depend on either.
+ * Synchronises the device; a captured graph is dropped. */
+int grmhd_batch_set_launch(grmhd_batch *batch, int kclass, int threads, int order);
 
 /* Size and launch counts of the batch. */
 int grmhd_batch_get_info(grmhd_batch *batch, grmhd_batch_info *out);

@@ -501,6 +501,11 @@ extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
   return GRMHD_OK;
 }
 
+extern "C" int grmhd_autotune(grmhd_sim *s, int trials, double *ms_before, double *ms_after) {
+  if (!s || trials < 1) return GRMHD_ERR_INVALID;
+  return plan_autotune(s->plan, trials, s->st, ms_before, ms_after);
+}
+
 extern "C" int grmhd_profile(grmhd_sim *s, int enable) {
   if (!s) return GRMHD_ERR_INVALID;
   s->prof_on = enable ? 1 : 0;

@@ -132,6 +132,55 @@ extern "C" int grmhd_batch_step(grmhd_batch *b, int nsteps, int use_graph) {
   return GRMHD_OK;
 }
 
+static void drop_graph(grmhd_batch *b) {
+  if (b->exec) {  // the graph holds the old launch shapes
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+}
+
+extern "C" int grmhd_batch_set_launch(grmhd_batch *b, int kclass, int threads, int order) {
+  if (!b) return GRMHD_ERR_INVALID;
+  static const int recon[] = {PC_RECON01, PC_RECON2, PC_RECON01F, PC_RECON2F};
+  static const int flux[] = {PC_FACE0, PC_FACE1, PC_FACE2, PC_FACE0F, PC_FACE1F, PC_FACE2F};
+  static const int zone[] = {PC_ZONE};
+  const int *cls = nullptr;
+  int ncls = 0;
+  if (kclass == GRMHD_K_RECON) {
+    cls = recon;
+    ncls = 4;
+  } else if (kclass == GRMHD_K_FLUX) {
+    cls = flux;
+    ncls = 6;
+  } else if (kclass == GRMHD_K_UPDATE) {
+    cls = zone;
+    ncls = 1;
+  } else {
+    return GRMHD_ERR_INVALID;
+  }
+  if (threads < 64 || threads > 256 || threads % 32 || order < 0 || order >= SCHED_N)
+    return GRMHD_ERR_INVALID;
+  drop_graph(b);
+  for (int q = 0; q < ncls; q++) {
+    const int rc = plan_set_class(b->plan, cls[q], threads, order);
+    if (rc != GRMHD_OK) return rc;
+  }
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_batch_autotune(grmhd_batch *b, int trials, double *ms_before,
+                                    double *ms_after) {
+  if (!b || trials < 1) return GRMHD_ERR_INVALID;
+  // the members' pending work first (the trials read their current state)
+  for (cudaStream_t q : b->member_streams)
+    if (cudaStreamSynchronize(q) != cudaSuccess) return GRMHD_ERR_CUDA;
+  const int rc = plan_autotune(b->plan, trials, b->st, ms_before, ms_after);
+  drop_graph(b);
+  return rc;
+}
+
 extern "C" int grmhd_batch_get_info(grmhd_batch *b, grmhd_batch_info *out) {
   if (!b || !out) return GRMHD_ERR_INVALID;
   out->ngrid = b->ngrid;
@@ -139,6 +188,7 @@ extern "C" int grmhd_batch_get_info(grmhd_batch *b, grmhd_batch_info *out) {
   out->launches_per_step = b->launches_per_step;
   out->launches = b->launches;
   out->graph = b->exec ? 1 : 0;
+  out->tuned = b->plan.tuned;
   return GRMHD_OK;
 }
 

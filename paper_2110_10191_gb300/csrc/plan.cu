@@ -1,7 +1,9 @@
 // plan.cu -- the plan kernels of the predictor-corrector step and their
 // enqueue functions (plan.h).  Each kernel maps its block to a grid through
 // the class's block table and runs the per-thread body of that grid.
+#include <algorithm>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "../../include/grmhd.h"
@@ -17,12 +19,12 @@ namespace {
 struct BView {
   const StageItem *__restrict__ items;
   const int *__restrict__ map;  // grid of each block of this class
-  const int *__restrict__ off;  // first block of each grid in this class
+  const int *__restrict__ loc;  // index of each block within its grid
 };
 
 __device__ __forceinline__ int block_grid(const BView &V) { return __ldg(V.map + blockIdx.x); }
-__device__ __forceinline__ long long block_tid(const BView &V, int g) {
-  return (long long)((int)blockIdx.x - __ldg(V.off + g)) * BS + threadIdx.x;
+__device__ __forceinline__ long long block_tid(const BView &V, int) {
+  return (long long)__ldg(V.loc + blockIdx.x) * blockDim.x + threadIdx.x;
 }
 // the stage arrays: 0 = P, 1 = Ph
 __device__ __forceinline__ double *arr(const StageItem &it, int which) { return which ? it.Ph : it.P; }
@@ -39,7 +41,7 @@ __global__ void kp_bounds(BView V, int which) {
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(BS) kp_recon(BView V, int in) {
+__global__ void __launch_bounds__(BS_MAX) kp_recon(BView V, int in) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(BS) kp_recon(BView V, int in) {
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(BS) kp_face(BView V, int in) {
+__global__ void __launch_bounds__(BS_MAX) kp_face(BView V, int in) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
@@ -67,7 +69,7 @@ __global__ void kp_to_f32(BView V, int in) {
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(BS) kp_recon_f32(BView V) {
+__global__ void __launch_bounds__(BS_MAX) kp_recon_f32(BView V) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(BS) kp_recon_f32(BView V) {
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(BS) kp_face_f32(BView V) {
+__global__ void __launch_bounds__(BS_MAX) kp_face_f32(BView V) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
@@ -112,7 +114,8 @@ __global__ void kp_ct(BView V) {
   ct_body(it.A, it.F[0], it.F[1], it.F[2], it.emf, block_tid(V, g));
 }
 
-__global__ void __launch_bounds__(BS) kp_update(BView V, int in, double dtfac, int ucache_mode) {
+// at most 168 registers: 3 blocks of 128 threads per SM (172 would allow 2)
+__global__ void __maxnreg__(168) kp_update(BView V, int in, double dtfac, int ucache_mode) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   update_body(it.A, it.P, arr(it, in), arr(it, 1 - in), it.F[0], it.F[1], it.F[2], it.pflag,
@@ -135,13 +138,13 @@ __global__ void kp_clock(const StageItem *__restrict__ items, int ngrid, int op)
   if (op == 2) advance_body(it.A);
 }
 
-long long nblk(long long n) { return (n + BS - 1) / BS; }
+long long nblk(long long n, int bs) { return (n + bs - 1) / bs; }
 
 BView view(const Plan &p, int cls) {
   BView V;
   V.items = p.items;
-  V.off = p.tab + p.off_base[cls];
   V.map = p.tab + p.map_base[cls];
+  V.loc = p.tab + p.loc_base[cls];
   return V;
 }
 
@@ -151,9 +154,56 @@ template <typename L>
 int launch(const Plan &p, int cls, int kclass, PlanHook *h, L &&body) {
   if (p.nblocks[cls] <= 0) return 0;
   if (h) h->begin(kclass, 1);
-  body((unsigned)p.nblocks[cls], view(p, cls));
+  body((unsigned)p.nblocks[cls], (unsigned)p.bs[cls], view(p, cls));
   if (h) h->end(kclass);
   return 1;
+}
+
+// Block tables of every class, laid out for p.bs / p.sched and uploaded.
+int upload_tables(Plan &p) {
+  std::vector<int> host;
+  host.reserve((size_t)p.tab_cap);
+  const int n = p.ngrid;
+  for (int q = 0; q < PC_N; q++) {
+    std::vector<long long> nb(n);
+    long long tot = 0;
+    for (int g = 0; g < n; g++) {
+      nb[g] = nblk(p.count[(size_t)q * n + g], p.bs[q]);
+      tot += nb[g];
+    }
+    if (tot >= (1ll << 31) - 1) return GRMHD_ERR_INVALID;
+    p.nblocks[q] = (int)tot;
+    std::vector<int> map, loc;
+    map.reserve((size_t)tot);
+    loc.reserve((size_t)tot);
+    if (p.sched[q] == SCHED_RR) {
+      for (long long r = 0; (long long)map.size() < tot; r++)
+        for (int g = 0; g < n; g++)
+          if (r < nb[g]) {
+            map.push_back(g);
+            loc.push_back((int)r);
+          }
+    } else {
+      std::vector<int> order(n);
+      for (int g = 0; g < n; g++) order[g] = g;
+      if (p.sched[q] == SCHED_LPT)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[a] > nb[b]; });
+      for (int g : order)
+        for (long long r = 0; r < nb[g]; r++) {
+          map.push_back(g);
+          loc.push_back((int)r);
+        }
+    }
+    p.map_base[q] = (int)host.size();
+    host.insert(host.end(), map.begin(), map.end());
+    p.loc_base[q] = (int)host.size();
+    host.insert(host.end(), loc.begin(), loc.end());
+  }
+  if ((long long)host.size() > p.tab_cap) return GRMHD_ERR_INVALID;
+  if (!host.empty() &&
+      cudaMemcpy(p.tab, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  return GRMHD_OK;
 }
 
 }  // namespace
@@ -161,9 +211,15 @@ int launch(const Plan &p, int cls, int kclass, PlanHook *h, L &&body) {
 int plan_build(Plan &p, const StageItem *items, int n) {
   memset(&p, 0, sizeof(p));
   if (!items || n < 1) return GRMHD_ERR_INVALID;
-  long long tot[PC_N] = {0};
-  std::vector<std::vector<int>> nb(PC_N, std::vector<int>(n));
-  long long zones = 0;
+  p.ngrid = n;
+  p.count = new (std::nothrow) long long[(size_t)PC_N * n];
+  p.host_items = new (std::nothrow) StageItem[n];
+  if (!p.count || !p.host_items) {
+    plan_free(p);
+    return GRMHD_ERR_NOMEM;
+  }
+  memcpy(p.host_items, items, sizeof(StageItem) * n);
+  long long zones = 0, cap = 0;
   for (int g = 0; g < n; g++) {
     const Dims &D = items[g].A.D;
     const int fl = items[g].A.flat3, mx = items[g].mixed;
@@ -185,54 +241,65 @@ int plan_build(Plan &p, const StageItem *items, int n) {
     c[PC_EDGE] = n_edge(D);
     c[PC_ZONE] = n_zone(D);
     for (int q = 0; q < PC_N; q++) {
-      nb[q][g] = (int)nblk(c[q]);
-      tot[q] += nb[q][g];
-      if (tot[q] >= (1ll << 31) - 1) return GRMHD_ERR_INVALID;
+      p.count[(size_t)q * n + g] = c[q];
+      cap += 2 * nblk(c[q], 64);  // the smallest block the tuner tries
     }
     zones += n_zone(D);
   }
-  std::vector<int> host;
   for (int q = 0; q < PC_N; q++) {
-    p.nblocks[q] = (int)tot[q];
-    p.off_base[q] = (int)host.size();
-    int acc = 0;
-    for (int g = 0; g < n; g++) {
-      host.push_back(acc);
-      acc += nb[q][g];
-    }
-    host.push_back(acc);
-    p.map_base[q] = (int)host.size();
-    for (int g = 0; g < n; g++) host.insert(host.end(), (size_t)nb[q][g], g);
+    p.bs[q] = BS;
+    p.sched[q] = SCHED_GRID;
   }
+  p.zones = zones;
+  p.tab_cap = cap;
   if (cudaMalloc(&p.items, sizeof(StageItem) * n) != cudaSuccess ||
-      cudaMalloc(&p.tab, sizeof(int) * host.size()) != cudaSuccess) {
+      cudaMalloc(&p.tab, sizeof(int) * (size_t)(cap > 0 ? cap : 1)) != cudaSuccess) {
     cudaGetLastError();
     plan_free(p);
     return GRMHD_ERR_NOMEM;
   }
-  if (cudaMemcpy(p.items, items, sizeof(StageItem) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(p.tab, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+  if (cudaMemcpy(p.items, items, sizeof(StageItem) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
     plan_free(p);
     return GRMHD_ERR_CUDA;
   }
-  p.ngrid = n;
-  p.zones = zones;
-  return GRMHD_OK;
+  const int rc = upload_tables(p);
+  if (rc != GRMHD_OK) plan_free(p);
+  return rc;
 }
 
 void plan_free(Plan &p) {
   if (p.items) cudaFree(p.items);
   if (p.tab) cudaFree(p.tab);
+  delete[] p.count;
+  delete[] p.host_items;
   p.items = nullptr;
   p.tab = nullptr;
+  p.count = nullptr;
+  p.host_items = nullptr;
   p.ngrid = 0;
+}
+
+int plan_set_class(Plan &p, int cls, int bs, int sched) {
+  if (cls < 0 || cls >= PC_N || bs < 64 || bs > BS_MAX || bs % 32 || sched < 0 || sched >= SCHED_N)
+    return GRMHD_ERR_INVALID;
+  // kernels still in flight may read the tables
+  if (cudaDeviceSynchronize() != cudaSuccess) return GRMHD_ERR_CUDA;
+  const int obs = p.bs[cls], osc = p.sched[cls];
+  p.bs[cls] = bs;
+  p.sched[cls] = sched;
+  const int rc = upload_tables(p);
+  if (rc != GRMHD_OK) {
+    p.bs[cls] = obs;
+    p.sched[cls] = osc;
+    upload_tables(p);
+  }
+  return rc;
 }
 
 int plan_clock(const Plan &p, int op, cudaStream_t st, PlanHook *h) {
   const int kc = (op == 1) ? GRMHD_K_DT : GRMHD_K_OTHER;
   if (h) h->begin(kc, 1);
-  kp_clock<<<(unsigned)nblk(p.ngrid), BS, 0, st>>>(p.items, p.ngrid, op);
+  kp_clock<<<(unsigned)nblk(p.ngrid, BS), BS, 0, st>>>(p.items, p.ngrid, op);
   if (h) h->end(kc);
   return 1;
 }
@@ -241,48 +308,48 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   int nl = plan_clock(p, 0, st, h);
   const int R = GRMHD_K_RECON, F = GRMHD_K_FLUX;
   // FP64 grids
-  nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, BView V) { kp_recon<0><<<nb, BS, 0, st>>>(V, in); });
-  nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, BView V) { kp_face<0><<<nb, BS, 0, st>>>(V, in); });
-  nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, BView V) { kp_recon<1><<<nb, BS, 0, st>>>(V, in); });
-  nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, BView V) { kp_face<1><<<nb, BS, 0, st>>>(V, in); });
-  nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, BView V) { kp_recon<2><<<nb, BS, 0, st>>>(V, in); });
-  nl += launch(p, PC_FACE2, F, h, [&](unsigned nb, BView V) { kp_face<2><<<nb, BS, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_FACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, in); });
   // mixed-precision grids
-  nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, BView V) { kp_to_f32<<<nb, BS, 0, st>>>(V, in); });
-  nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, BView V) { kp_recon_f32<0><<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_FACE0F, F, h, [&](unsigned nb, BView V) { kp_face_f32<0><<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, BView V) { kp_recon_f32<1><<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_FACE1F, F, h, [&](unsigned nb, BView V) { kp_face_f32<1><<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_RECON2F, R, h, [&](unsigned nb, BView V) { kp_recon_f32<2><<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_FACE2F, F, h, [&](unsigned nb, BView V) { kp_face_f32<2><<<nb, BS, 0, st>>>(V); });
+  nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_f32<<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE0F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<0><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<1><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE1F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<1><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_RECON2F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<2><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE2F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<2><<<nb, bs, 0, st>>>(V); });
   // flat-X3 grids
   nl += launch(p, PC_REPL, GRMHD_K_OTHER, h,
-               [&](unsigned nb, BView V) { kp_replicate<<<nb, BS, 0, st>>>(V); });
+               [&](unsigned nb, unsigned bs, BView V) { kp_replicate<<<nb, bs, 0, st>>>(V); });
   return nl;
 }
 
 int plan_fix_ct(const Plan &p, cudaStream_t st, PlanHook *h) {
   const int C = GRMHD_K_CT;
-  int nl = launch(p, PC_FIX, C, h, [&](unsigned nb, BView V) { kp_fix<<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_EDGE, C, h, [&](unsigned nb, BView V) { kp_emf<<<nb, BS, 0, st>>>(V); });
-  nl += launch(p, PC_EDGE, C, h, [&](unsigned nb, BView V) { kp_ct<<<nb, BS, 0, st>>>(V); });
+  int nl = launch(p, PC_FIX, C, h, [&](unsigned nb, unsigned bs, BView V) { kp_fix<<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_EDGE, C, h, [&](unsigned nb, unsigned bs, BView V) { kp_emf<<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_EDGE, C, h, [&](unsigned nb, unsigned bs, BView V) { kp_ct<<<nb, bs, 0, st>>>(V); });
   return nl;
 }
 
 int plan_update(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st, PlanHook *h) {
-  int nl = launch(p, PC_ZONE, GRMHD_K_UPDATE, h, [&](unsigned nb, BView V) {
-    kp_update<<<nb, BS, 0, st>>>(V, in, dtfac, ucache_mode);
+  int nl = launch(p, PC_ZONE, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
+    kp_update<<<nb, bs, 0, st>>>(V, in, dtfac, ucache_mode);
   });
   nl += launch(p, PC_ZONE, GRMHD_K_FIXUP, h,
-               [&](unsigned nb, BView V) { kp_fixup<<<nb, BS, 0, st>>>(V, 1 - in); });
+               [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, 1 - in); });
   return nl;
 }
 
 int plan_bounds(const Plan &p, int which, cudaStream_t st, PlanHook *h) {
   const int B = GRMHD_K_BOUNDS;
-  int nl = launch(p, PC_BX1, B, h, [&](unsigned nb, BView V) { kp_bounds<0><<<nb, BS, 0, st>>>(V, which); });
-  nl += launch(p, PC_BX2, B, h, [&](unsigned nb, BView V) { kp_bounds<1><<<nb, BS, 0, st>>>(V, which); });
-  nl += launch(p, PC_BX3, B, h, [&](unsigned nb, BView V) { kp_bounds<2><<<nb, BS, 0, st>>>(V, which); });
+  int nl = launch(p, PC_BX1, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<0><<<nb, bs, 0, st>>>(V, which); });
+  nl += launch(p, PC_BX2, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<1><<<nb, bs, 0, st>>>(V, which); });
+  nl += launch(p, PC_BX3, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<2><<<nb, bs, 0, st>>>(V, which); });
   return nl;
 }
 
@@ -303,6 +370,127 @@ int plan_steps(const Plan &p, int nsteps, cudaStream_t st, PlanHook *h) {
     nl += plan_clock(p, 2, st, h);
   }
   return nl;
+}
+
+namespace {
+
+// Device time (ms) of `trials` passes of run() on st, after one warm-up pass.
+template <typename R>
+double time_passes(cudaStream_t st, int trials, R &&run) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  run();
+  cudaEventRecord(e0, st);
+  for (int q = 0; q < trials; q++) run();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (double)ms / trials;
+}
+
+}  // namespace
+
+int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, double *ms_after) {
+  if (p.ngrid < 1 || trials < 1) return GRMHD_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GRMHD_ERR_CUDA;
+  const int n = p.ngrid;
+  std::vector<Clock> saved(n);
+  for (int g = 0; g < n; g++)
+    if (cudaMemcpy(&saved[g], p.host_items[g].A.clk, sizeof(Clock), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return GRMHD_ERR_CUDA;
+  // representative scratch: face values, CT fluxes and a CFL dt of the current state
+  plan_fluxes(p, 0, st, nullptr);
+  plan_clock(p, 1, st, nullptr);
+  plan_fix_ct(p, st, nullptr);
+  struct Group {
+    int cls;
+    int which;  // what one pass launches
+  };
+  const Group groups[] = {{PC_RECON01, 0}, {PC_RECON2, 1},   {PC_FACE0, 2},    {PC_FACE1, 3},
+                          {PC_FACE2, 4},   {PC_ZONE, 5},     {PC_RECON01F, 6}, {PC_RECON2F, 7},
+                          {PC_FACE0F, 8},  {PC_FACE1F, 9},   {PC_FACE2F, 10}};
+  auto pass = [&](int which) {
+    auto L = [&](int cls, auto &&body) { launch(p, cls, 0, nullptr, body); };
+    switch (which) {
+      case 0:
+        L(PC_RECON01, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, 0); });
+        L(PC_RECON01, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, 0); });
+        break;
+      case 1:
+        L(PC_RECON2, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, 0); });
+        break;
+      case 2:
+        L(PC_FACE0, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, 0); });
+        break;
+      case 3:
+        L(PC_FACE1, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, 0); });
+        break;
+      case 4:
+        L(PC_FACE2, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, 0); });
+        break;
+      case 5:  // predictor-like update without keeping U(P^n), then the fixup
+        L(PC_ZONE, [&](unsigned nb, unsigned bs, BView V) { kp_update<<<nb, bs, 0, st>>>(V, 0, 0.5, 0); });
+        L(PC_ZONE, [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, 1); });
+        break;
+      case 6:
+        L(PC_RECON01F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });
+        L(PC_RECON01F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<1><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 7:
+        L(PC_RECON2F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<2><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 8:
+        L(PC_FACE0F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<0><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 9:
+        L(PC_FACE1F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<1><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 10:
+        L(PC_FACE2F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<2><<<nb, bs, 0, st>>>(V); });
+        break;
+    }
+  };
+  const int sizes[] = {64, 128, 256};
+  double before = 0.0, after = 0.0;
+  int rc = GRMHD_OK;
+  for (const Group &gr : groups) {
+    if (p.nblocks[gr.cls] <= 0) continue;
+    const int bs0 = p.bs[gr.cls], sc0 = p.sched[gr.cls];
+    double best = time_passes(st, trials, [&] { pass(gr.which); });
+    before += best;
+    int best_bs = bs0, best_sc = sc0;
+    for (int bs : sizes)
+      for (int sc = 0; sc < (n > 1 ? SCHED_N : 1); sc++) {
+        if (bs == bs0 && sc == sc0) continue;
+        rc = plan_set_class(p, gr.cls, bs, sc);
+        if (rc != GRMHD_OK) break;
+        const double t = time_passes(st, trials, [&] { pass(gr.which); });
+        if (t < 0.99 * best) {  // a change must gain more than the timing noise
+          best = t;
+          best_bs = bs;
+          best_sc = sc;
+        }
+      }
+    if (rc != GRMHD_OK) break;
+    rc = plan_set_class(p, gr.cls, best_bs, best_sc);
+    if (rc != GRMHD_OK) break;
+    after += best;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess && rc == GRMHD_OK) rc = GRMHD_ERR_CUDA;
+  for (int g = 0; g < n; g++)
+    if (cudaMemcpy(p.host_items[g].A.clk, &saved[g], sizeof(Clock), cudaMemcpyHostToDevice) !=
+            cudaSuccess &&
+        rc == GRMHD_OK)
+      rc = GRMHD_ERR_CUDA;
+  if (rc == GRMHD_OK) p.tuned = 1;
+  if (ms_before) *ms_before = before;
+  if (ms_after) *ms_after = after;
+  return rc;
 }
 
 }  // namespace grmhd

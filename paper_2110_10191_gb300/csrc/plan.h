@@ -49,12 +49,26 @@ enum {
   PC_N
 };
 
+// block order of a launch class
+enum {
+  SCHED_GRID = 0,  // grids in plan order, each grid's blocks contiguous
+  SCHED_LPT = 1,   // grids by decreasing block count (largest first), contiguous
+  SCHED_RR = 2,    // round robin: one block of each grid that has blocks left, in turn
+  SCHED_N
+};
+
 struct Plan {
   int ngrid;
   StageItem *items;  // device
-  int *tab;          // device: per class, ngrid + 1 first blocks, then the block -> grid map
-  int off_base[PC_N], map_base[PC_N], nblocks[PC_N];
+  StageItem *host_items;  // host copy of items
+  int *tab;          // device: per class, the grid of each block, then its index within that grid
+  long long tab_cap; // ints allocated for tab (enough for 64-thread blocks in every class)
+  long long *count;  // host: threads of each grid per class, [PC_N][ngrid]
+  int bs[PC_N];      // threads per block of each class (multiple of 32, <= 256)
+  int sched[PC_N];   // block order of each class (SCHED_*)
+  int map_base[PC_N], loc_base[PC_N], nblocks[PC_N];
   long long zones;  // interior zones over all grids
+  int tuned;        // 1 after plan_autotune
 };
 
 // Observer of the launches, per kernel class GRMHD_K_* (profiling).
@@ -69,6 +83,18 @@ struct PlanHook {
 // GRMHD_ERR_NOMEM or GRMHD_ERR_CUDA.
 int plan_build(Plan &p, const StageItem *items, int n);
 void plan_free(Plan &p);
+// Re-lay the block tables of class cls for bs threads per block and block
+// order sched (the results of every grid do not depend on either).
+int plan_set_class(Plan &p, int cls, int bs, int sched);
+// Pick, by timing on st, the block size and block order of each heavy
+// launch class (reconstruction, face fluxes, update + fixup, in both
+// precisions) among 64/128/256 threads and the SCHED_* orders.  Leaves
+// every grid's state and clock as it found them: the trial launches write
+// only scratch (face values, fluxes, the interior of the half-step array)
+// and the failure/bound flags of the last stage, and the clocks are saved
+// and restored.  Waits for the device before and after.  ms_before / ms_after (may be NULL): one
+// pass of the tuned kernels with the previous and the chosen settings.
+int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, double *ms_after);
 
 // The functions below enqueue on st and return the number of kernels
 // launched; launch errors are left for cudaGetLastError().

@@ -7,11 +7,11 @@
 //   section) -> fixup of failed zones.
 //
 // Each body takes the step arguments of one grid and the linear index t of
-// its thread within that grid's launch range, so the same code runs in the
-// single-grid kernels (step.cu, t from blockIdx) and in the batched kernels
-// (batch.cu, t from the block's offset within its grid).  A block never
-// spans two grids: the block reductions (signal speed maxima, warp counts)
-// see the threads of one grid only.
+// its thread within that grid's launch range.  The plan kernels (plan.cu)
+// run them for one grid or many (t from the block's index within its grid);
+// the allocation-free flux entry point's kernels (step.cu) for one.  A block
+// never spans two grids: the block reductions (signal speed maxima, warp
+// counts) see the threads of one grid only.
 //
 // Every thread owns one face, edge or zone; fields are SoA float64 in HBM
 // with i fastest, so warps read and write 256-byte contiguous runs.
@@ -29,7 +29,8 @@
 
 namespace grmhd {
 
-constexpr int BS = 128;  // threads per block of every stage kernel
+constexpr int BS = 128;      // default threads per block of the stage kernels
+constexpr int BS_MAX = 256;  // largest block the plan kernels are compiled for
 
 __device__ __forceinline__ int wrap(int g, int n) {  // periodic image of ghost index g
   int q = (g - NG) % n;
@@ -160,6 +161,8 @@ __device__ __forceinline__ void bounds_x3_body(const StepArgs &A, double *P, lon
 // ---------------------------------------------------------------------------
 // Face fluxes
 // ---------------------------------------------------------------------------
+// Block maximum of v >= 0 (any block size that is a multiple of 32, up to
+// 1024), one atomicMax per block; every thread of the block must call it.
 __device__ __forceinline__ void warp_block_max(double v, unsigned long long *dst) {
   // v >= 0: its bit pattern orders like the value
   unsigned long long b = __double_as_longlong(v);
@@ -168,13 +171,14 @@ __device__ __forceinline__ void warp_block_max(double v, unsigned long long *dst
     unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
     b = (x > b) ? x : b;
   }
-  __shared__ unsigned long long sm[BS / 32];
+  __shared__ unsigned long long sm[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sm[w] = b;
   __syncthreads();
   if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
     unsigned long long m = sm[0];
-    for (int q = 1; q < BS / 32; q++) m = (sm[q] > m) ? sm[q] : m;
+    for (int q = 1; q < nw; q++) m = (sm[q] > m) ? sm[q] : m;
     if (m) atomicMax(dst, m);
   }
 }

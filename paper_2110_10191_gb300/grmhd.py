@@ -71,7 +71,7 @@ class grmhd_stats(ctypes.Structure):
 class grmhd_batch_info(ctypes.Structure):
     _fields_ = [("ngrid", ctypes.c_int), ("zones", ctypes.c_longlong),
                 ("launches_per_step", ctypes.c_int), ("launches", ctypes.c_longlong),
-                ("graph", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("tuned", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -82,7 +82,8 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_predictor", "grmhd_get_fluxes", "grmhd_next_dt", "grmhd_get_flags",
            "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_profile", "grmhd_get_profile",
            "grmhd_fp64_peak", "grmhd_fluxes_noalloc", "grmhd_batch_create", "grmhd_batch_destroy",
-           "grmhd_batch_step", "grmhd_batch_get_info", "grmhd_batch_sync", "grmhd_strerror"]
+           "grmhd_batch_step", "grmhd_batch_get_info", "grmhd_batch_sync", "grmhd_autotune",
+           "grmhd_batch_autotune", "grmhd_batch_set_launch", "grmhd_strerror"]
 
 
 def lib_path() -> str:
@@ -126,6 +127,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_batch_step.argtypes = [vp, i, i]
         L.grmhd_batch_get_info.argtypes = [vp, P(grmhd_batch_info)]
         L.grmhd_batch_sync.argtypes = [vp]
+        L.grmhd_autotune.argtypes = [vp, i, P(d), P(d)]
+        L.grmhd_batch_autotune.argtypes = [vp, i, P(d), P(d)]
+        L.grmhd_batch_set_launch.argtypes = [vp, i, i, i]
         L.grmhd_strerror.argtypes = [i]
         L.grmhd_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -306,6 +310,14 @@ class Sim:
         _check(self.L.grmhd_get_profile(self.h, ctypes.byref(pd), int(reset)), "grmhd_get_profile")
         return {c: (pd.ms[q], pd.launches[q]) for q, c in enumerate(KCLASSES)}
 
+    def autotune(self, trials: int = 3):
+        """Pick the block sizes of the step's heavy kernels by timing;
+        returns (ms before, ms after) for one pass of them."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(self.L.grmhd_autotune(self.h, int(trials), ctypes.byref(a), ctypes.byref(b)),
+               "grmhd_autotune")
+        return a.value, b.value
+
     def geom(self, loc: int) -> np.ndarray:
         nc = 64 if loc == 3 else 34
         out = np.zeros((nc, self.s[1], self.s[0]))
@@ -350,6 +362,20 @@ class Batch:
 
     def sync(self) -> None:
         _check(self.L.grmhd_batch_sync(self.h), "grmhd_batch_sync")
+
+    def autotune(self, trials: int = 3):
+        """Pick block sizes and block orders of the heavy kernels by timing;
+        returns (ms before, ms after) for one pass of them."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(self.L.grmhd_batch_autotune(self.h, int(trials), ctypes.byref(a), ctypes.byref(b)),
+               "grmhd_batch_autotune")
+        return a.value, b.value
+
+    def set_launch(self, kclass: str, threads: int, order: int) -> None:
+        """Fix threads per block and block order (0 batch order, 1 largest
+        grid first, 2 round robin) of the "recon", "flux" or "update" kernels."""
+        _check(self.L.grmhd_batch_set_launch(self.h, KCLASSES.index(kclass), int(threads), int(order)),
+               "grmhd_batch_set_launch")
 
     def info(self):
         out = grmhd_batch_info()

@@ -235,3 +235,73 @@ def test_flat_x3_mixed_precision_matches_full_extent(grmhd):
     full, _ = _alone(grmhd, ext, 2)
     for k in range(2):
         assert np.array_equal(full[:, 3 + k, 3:-3, 3:-3], flat[:, 3, 3:-3, 3:-3]), k
+
+
+def _fresh(grmhd, probs):
+    sims = []
+    for pr in probs:
+        s = grmhd.Sim(pr)
+        s.set_prims(pr.P)
+        sims.append(s)
+    return sims
+
+
+def test_launch_settings_do_not_change_bits(grmhd):
+    """Every block size and block order of the heavy kernels gives the same
+    bits (each thread computes the same zone or face whatever the launch
+    shape)."""
+    probs = pb.batch_2d(ngrid=5, nmin=12, nmax=36, seed=8)
+    probs.append(pb.fm_torus(20, 16, 4))
+    probs[1].precision = 1
+    ref = [_alone(grmhd, pr, 2)[0] for pr in probs]
+    for threads, order in ((64, 2), (256, 1), (96, 0), (160, 2), (256, 2)):
+        sims = _fresh(grmhd, probs)
+        b = grmhd.Batch(sims)
+        for kc in ("recon", "flux", "update"):
+            b.set_launch(kc, threads, order)
+        b.step(2, sync=True)
+        for s, P, pr in zip(sims, ref, probs):
+            assert np.array_equal(s.get_prims(with_ghosts=True), P), (threads, order, pr.name)
+        b.close()
+
+
+def test_set_launch_rejects_bad_values(grmhd):
+    s = grmhd.Sim(pb.linear_mode(8))
+    b = grmhd.Batch([s])
+    for kc, th, od in (("recon", 32, 0), ("recon", 100, 0), ("flux", 512, 0), ("update", 128, 3),
+                       ("bounds", 128, 0)):
+        with pytest.raises(grmhd.GrmhdError):
+            b.set_launch(kc, th, od)
+    b.close()
+
+
+def test_batch_autotune_keeps_state_and_bits(grmhd):
+    probs = _mixture()
+    ref = [_alone(grmhd, pr, 2) for pr in probs]
+    sims = _fresh(grmhd, probs)
+    b = grmhd.Batch(sims)
+    b.step(1, sync=True)
+    before = [(s.get_prims(with_ghosts=True), s.stats()) for s in sims]
+    ms0, ms1 = b.autotune(trials=2)
+    assert ms0 > 0 and 0 < ms1 <= ms0 * 1.05
+    assert b.info()["tuned"] == 1 and b.info()["graph"] == 0
+    for s, (P, st) in zip(sims, before):
+        assert np.array_equal(s.get_prims(with_ghosts=True), P)
+        assert s.stats() == st
+    b.step(1, sync=True)
+    for s, (P, st), pr in zip(sims, ref, probs):
+        assert np.array_equal(s.get_prims(with_ghosts=True), P), pr.name
+        assert s.stats()["t"] == st["t"]
+    b.close()
+
+
+def test_sim_autotune_keeps_bits(grmhd):
+    pr = pb.fm_torus(24, 20, 8)
+    ref, st = _alone(grmhd, pr, 2)
+    s = grmhd.Sim(pr)
+    s.set_prims(pr.P)
+    ms0, ms1 = s.autotune(trials=2)
+    assert ms0 > 0 and ms1 > 0
+    got = s.step(2)
+    assert np.array_equal(s.get_prims(with_ghosts=True), ref)
+    assert got["t"] == st["t"] and got["floor_hits"] == st["floor_hits"]
