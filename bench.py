@@ -15,7 +15,9 @@ prints one JSON line.  Besides the headline it carries the same workload in
 the mixed-precision mode ("mixed"), 64 uneven flat 2D grids stepped as one
 batch against the same grids stepped one by one ("batched"), and the
 mixed-precision error of 100 cycles of the 288x128x128 torus against the
-FP64 path ("mixed_accuracy"); --no-extras skips them.
+FP64 path ("mixed_accuracy"), and a prefix of the serving workload's
+request stream through the serving loop ("served": p50/p99 time-to-result,
+aggregate zone-cycles/s, offered vs served load); --no-extras skips them.
 """
 import argparse
 import json
@@ -293,6 +295,59 @@ def batched_throughput(grmhd, steps, warmup, stream, nmin=32, nmax=256):
             "speedup_vs_singles": ms_single / ms_batch, "steps": steps}
 
 
+def serving_run(grmhd, nreq, zone_cap, quantum, policy=0):
+    """The serving workload: the first `nreq` requests of the 200-request
+    Poisson stream (4/s; 60% tori a ~ U[0, 0.98], N ~ U{64..192}; 40% 2D
+    Bondi, N ~ U{96..160}; 20..200 cycles; FP64 / mixed 50/50) submitted to
+    the serving loop at their arrival times.  Time-to-result runs from the
+    scheduled arrival to the result in host memory."""
+    import numpy as np
+    from paper_2110_10191_gb300 import problems as pb
+    stream = pb.serving_stream(nreq=200, rate=4.0, seed=0)[:nreq]
+    srv = grmhd.Server(max_active_zones=zone_cap, quantum=quantum, policy=policy)
+    t0 = srv.now()
+    results = []
+
+    def collect(wait_ms):
+        for r in srv.poll(64, wait_ms=wait_ms):
+            r.pop("P", None)
+            results.append(r)
+
+    work = 0.0
+    late = 0.0
+    for r in stream:
+        while srv.now() - t0 < r["t_arrival"]:
+            collect(int(max(1, min(50, 1e3 * (r["t_arrival"] - (srv.now() - t0))))))
+        pr = pb.serving_problem(r)
+        late = max(late, srv.now() - t0 - r["t_arrival"])
+        srv.submit(r["id"], pr, r["steps"], t_arrival=t0 + r["t_arrival"])
+        work += float(pr.zones) * r["steps"]
+        del pr
+    while len(results) < len(stream):
+        collect(200)
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["t_done"] - r["t_arrival"] for r in results])
+    end = max(r["t_done"] for r in results) - t0
+    span = stream[-1]["t_arrival"]
+    ok = sum(1 for r in results if r["status"] in (0, -4))
+    return {"workload": "first %d of 200 Poisson requests at 4/s (seed 0): 60%% FM tori (a ~ U[0, 0.98], "
+                        "N^3, N ~ U{64..192}), 40%% 2D Bondi (N ~ U{96..160}), 20..200 cycles, "
+                        "FP64/mixed 50/50" % nreq,
+            "requests": len(stream), "completed": ok,
+            "failed_zones_reported": sum(1 for r in results if r["status"] == -4),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "max_s": float(lat.max()),
+            "aggregate_value": st["zone_cycles"] / end, "unit": UNIT,
+            "offered_load": work / span, "served_load": work / end,
+            "zone_cycles": st["zone_cycles"], "seconds": end, "gpu_busy_fraction": st["busy_seconds"] / end,
+            "max_submission_lag_s": late, "peak_active": st["peak_active"],
+            "peak_hbm_bytes": st["peak_bytes"], "rounds": st["rounds"], "gpu_launches": st["launches"],
+            "policy": "%s admission by HBM footprint, at most %d zones in flight (one request always "
+                      "admitted), rounds of <= %d cycles as one batch step (CUDA graph)"
+                      % ("smallest-work-first" if policy else "FIFO", zone_cap, quantum)}
+
+
 def corner_divb(P, gdet, dx, n):
     """max |div(sqrt(-g) B)| at interior zone corners, the discrete
     divergence flux-CT keeps at round-off, and the scale max|sqrt(-g) B|/dx."""
@@ -386,6 +441,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision, batched and accuracy legs")
     ap.add_argument("--accuracy-steps", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the 200-request serving stream to run (0: skip)")
+    ap.add_argument("--serve-zone-cap", type=int, default=1 << 22)
+    ap.add_argument("--serve-quantum", type=int, default=8)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -468,6 +527,11 @@ def main():
                                                      nmin=32, nmax=48)
         if rank == 0:
             extras["mixed_accuracy"] = mixed_accuracy(grmhd, args.accuracy_steps, stream)
+        if args.serve_requests > 0:
+            extras["served"] = serving_run(grmhd, args.serve_requests, args.serve_zone_cap,
+                                           args.serve_quantum, policy=0)
+            extras["served_swf"] = serving_run(grmhd, args.serve_requests, args.serve_zone_cap,
+                                               args.serve_quantum, policy=1)
 
     if rank != 0:
         if world > 1:

@@ -35,6 +35,8 @@
 #ifndef GRMHD_H
 #define GRMHD_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -308,6 +310,100 @@ int grmhd_batch_get_info(grmhd_batch *batch, grmhd_batch_info *out);
 
 /* Wait for the batch's stream. */
 int grmhd_batch_sync(grmhd_batch *batch);
+
+/* Device bytes grmhd_create would allocate for this grid (state, stage
+ * scratch, fluxes, geometry, flags, clock, the FP32 copies of the mixed
+ * mode and the launch plan); GRMHD_ERR_INVALID as grmhd_create. */
+int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metric,
+                    const grmhd_params *params, size_t *bytes);
+
+/* ---- Serving: a request loop over simulations that arrive over time ----
+ *
+ * No counterpart in the paper (it runs one simulation per job).  A server
+ * owns a thread that takes submitted simulations in arrival order, admits
+ * each when its device footprint fits the server's HBM budget (and, if
+ * set, when the zones in flight stay under a cap), in arrival order or
+ * smallest work first, keeps the admitted
+ * states resident, and advances all of them together: each round is one
+ * batch step (grmhd_batch_*) of up to `quantum` cycles, so simulations of
+ * different grids, problems and precisions share every launch, and a
+ * simulation joins or leaves at round boundaries.  When a simulation has
+ * taken its requested cycles its primitives are copied to the caller's
+ * host buffer and its device memory is freed.  A result is bitwise the
+ * result of grmhd_step on the same simulation alone. */
+typedef struct grmhd_server grmhd_server; /* opaque, library-owned */
+
+typedef struct {
+  size_t hbm_budget;           /* bytes of simulation state the server may hold; 0: 90% of
+                                  the free device memory at creation */
+  long long max_active_zones;  /* admit no request that would take the zones in flight
+                                  above this (one is always admitted); 0: no cap */
+  int quantum;                 /* cycles per round at most (>= 1) */
+  int use_graph;               /* 1: each round replays a CUDA graph of one cycle */
+  int policy;                  /* GRMHD_SERVE_FIFO or GRMHD_SERVE_SWF */
+} grmhd_server_config;
+
+/* Admission order of waiting requests. */
+#define GRMHD_SERVE_FIFO 0 /* arrival order; the oldest waits for room (no overtaking) */
+#define GRMHD_SERVE_SWF 1  /* smallest work (zones x cycles) first among those that fit */
+
+typedef struct {
+  long long id;                 /* the caller's request id */
+  int status;                   /* GRMHD_OK; GRMHD_ERR_INVERSION: the result is there but a
+                                  failed zone had no valid neighbour (as grmhd_step reports);
+                                  any other code ended the request without a result */
+  long long zones, steps;       /* interior zones, cycles taken */
+  double t_arrival, t_admit, t_done; /* server clock (seconds): arrival as submitted,
+                                  admission (state on the device), result in host memory */
+  grmhd_stats stats;            /* the simulation's final statistics */
+} grmhd_server_result;
+
+typedef struct {
+  double now;                   /* server clock (seconds since creation) */
+  long long submitted, completed, failed, rounds; /* completed: with a result */
+  double zone_cycles;           /* interior zone-cycles advanced */
+  double busy_seconds;          /* wall time with rounds in flight */
+  size_t bytes_in_use, peak_bytes, budget;
+  int active, pending, peak_active;
+  long long launches;           /* kernels launched by the rounds */
+} grmhd_server_stats;
+
+/* Start a server on the current device (its thread makes that device
+ * current).  cfg == NULL: defaults (budget 90% of free memory, no zone
+ * cap, quantum 8, graphs on, FIFO). */
+int grmhd_server_create(const grmhd_server_config *cfg, grmhd_server **out);
+
+/* Submit one simulation: grid, metric and parameters as grmhd_create;
+ * P_in: host primitives, interior ([8][n3][n2][n1]) or with ghosts
+ * (in_ghosts = 1; needed for FIXED boundaries); P_out: host buffer for the
+ * result, interior or with ghosts (out_ghosts).  The caller keeps both
+ * buffers alive and untouched until the request's result has been polled.
+ * t_arrival: the request's arrival on the server clock (a negative value:
+ * now); time-to-result is counted from it.  Returns at once; a request
+ * whose footprint exceeds the whole budget is refused (GRMHD_ERR_NOMEM),
+ * invalid arguments give GRMHD_ERR_INVALID. */
+int grmhd_server_submit(grmhd_server *srv, long long id, const grmhd_grid *grid,
+                        const grmhd_metric *metric, const grmhd_params *params,
+                        const double *P_in, int in_ghosts, double *P_out, int out_ghosts,
+                        long long nsteps, double t_arrival);
+
+/* Move up to max finished requests into res (oldest first), waiting up to
+ * wait_ms milliseconds for the first; returns how many (>= 0) or an
+ * error code. */
+int grmhd_server_poll(grmhd_server *srv, grmhd_server_result *res, int max, int wait_ms);
+
+/* Wait until every submitted request has finished (results stay to be
+ * polled), at most timeout_ms (< 0: no limit); GRMHD_ERR_CUDA on timeout. */
+int grmhd_server_drain(grmhd_server *srv, int timeout_ms);
+
+int grmhd_server_get_stats(grmhd_server *srv, grmhd_server_stats *out);
+
+/* Seconds on the server clock. */
+double grmhd_server_now(grmhd_server *srv);
+
+/* Stop the thread (requests not finished are dropped) and free everything.
+ * NULL is accepted. */
+int grmhd_server_destroy(grmhd_server *srv);
 
 /* Name of an error code. */
 const char *grmhd_strerror(int code);

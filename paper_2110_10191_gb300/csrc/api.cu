@@ -90,20 +90,25 @@ static void free_all(grmhd_sim *s) {
   if (s->clk) cudaFree(s->clk);
 }
 
-extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
-                            const grmhd_params *params, void *stream, grmhd_sim **out) {
-  if (!grid || !metric || !params || !out) return GRMHD_ERR_INVALID;
-  *out = nullptr;
+// Arguments of grmhd_create: GRMHD_OK and the dimensions, or GRMHD_ERR_INVALID.
+static int validate(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_params *params,
+                    Dims *Dout) {
+  if (!grid || !metric || !params) return GRMHD_ERR_INVALID;
   const int n[3] = {grid->n1, grid->n2, grid->n3};
   const double xmin[3] = {grid->x1min, grid->x2min, grid->x3min};
   const double xmax[3] = {grid->x1max, grid->x2max, grid->x3max};
   long long tot = 1;
+  Dims D;
   for (int d = 0; d < 3; d++) {
     if (n[d] < 1 || n[d] > (1 << 20)) return GRMHD_ERR_INVALID;
     if (!(xmax[d] > xmin[d])) return GRMHD_ERR_INVALID;
+    D.n[d] = n[d];
+    D.s[d] = n[d] + 2 * NG;
     tot *= (long long)(n[d] + 2 * NG);
   }
   if (tot >= (1ll << 31)) return GRMHD_ERR_INVALID;
+  D.ntot = tot;
+  D.n2d = (long long)D.s[0] * D.s[1];
   if (metric->kind != GRMHD_METRIC_MINKOWSKI && metric->kind != GRMHD_METRIC_MKS_KERR)
     return GRMHD_ERR_INVALID;
   if (metric->kind == GRMHD_METRIC_MKS_KERR && !(fabs(metric->a) < 1.0)) return GRMHD_ERR_INVALID;
@@ -121,6 +126,45 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
       if ((b == GRMHD_BC_PERIODIC) != (params->bc[d][1 - sd] == GRMHD_BC_PERIODIC))
         return GRMHD_ERR_INVALID;
     }
+  if (Dout) *Dout = D;
+  return GRMHD_OK;
+}
+
+static int flat3_of(const Dims &D, const grmhd_params *params) {
+  return (D.n[2] == 1 && params->bc[2][0] == GRMHD_BC_PERIODIC) ? 1 : 0;
+}
+
+extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metric,
+                               const grmhd_params *params, size_t *bytes) {
+  Dims D;
+  if (!bytes) return GRMHD_ERR_INVALID;
+  const int rc = validate(grid, metric, params, &D);
+  if (rc != GRMHD_OK) return rc;
+  const size_t tot = (size_t)D.ntot, n2d = (size_t)D.n2d;
+  const int mixed = params->precision == GRMHD_PREC_MIXED;
+  size_t b = sizeof(double) * NV * tot * 8                 // P, Ph, F1..3, Lf, Rf, Uc
+             + sizeof(double) * 3 * tot                    // EMFs
+             + sizeof(double) * (NLOC * G_NCOMP + C_NCOMP + 2) * n2d  // geometry, connection, bounds
+             + sizeof(int) * 2 * tot + sizeof(Clock);     // flags, clock
+  if (mixed) b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
+  b += (size_t)plan_bytes(D, flat3_of(D, params), mixed);
+  *bytes = b;
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
+                            const grmhd_params *params, void *stream, grmhd_sim **out) {
+  if (!out) return GRMHD_ERR_INVALID;
+  *out = nullptr;
+  {
+    const int rc = validate(grid, metric, params, nullptr);
+    if (rc != GRMHD_OK) return rc;
+  }
+  const int n[3] = {grid->n1, grid->n2, grid->n3};
+  const double xmin[3] = {grid->x1min, grid->x2min, grid->x3min};
+  const double xmax[3] = {grid->x1max, grid->x2max, grid->x3max};
+  long long tot = 1;
+  for (int d = 0; d < 3; d++) tot *= (long long)(n[d] + 2 * NG);
 
   grmhd_sim *s = new (std::nothrow) grmhd_sim();
   if (!s) return GRMHD_ERR_NOMEM;
@@ -217,7 +261,7 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   A.floors_on = params->floors_on;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
-  A.flat3 = (n[2] == 1 && params->bc[2][0] == GRMHD_BC_PERIODIC) ? 1 : 0;
+  A.flat3 = flat3_of(D, params);
   A.geom = s->geom;
   A.conn = s->conn;
   A.floors = s->floors;

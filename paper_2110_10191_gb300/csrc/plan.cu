@@ -208,6 +208,33 @@ int upload_tables(Plan &p) {
 
 }  // namespace
 
+void plan_counts(const Dims &D, int flat3, int mixed, long long c[PC_N]) {
+  const int fl = flat3, mx = mixed;
+  c[PC_BX1] = n_bounds_x1(D);
+  c[PC_BX2] = n_bounds_x2(D);
+  c[PC_BX3] = n_bounds_x3(D);
+  c[PC_RECON01] = mx ? 0 : n_recon(D, fl);
+  c[PC_RECON2] = (mx || fl) ? 0 : n_recon(D, 0);
+  for (int d = 0; d < 3; d++) {
+    c[PC_FACE0 + d] = mx ? 0 : n_face(D, d, fl);
+    c[PC_FACE0F + d] = mx ? n_face(D, d, fl) : 0;
+  }
+  c[PC_TOF32] = mx ? (long long)NV * D.ntot : 0;
+  c[PC_RECON01F] = mx ? n_recon(D, fl) : 0;
+  c[PC_RECON2F] = (mx && !fl) ? n_recon(D, 0) : 0;
+  c[PC_REPL] = fl ? n_replicate(D) : 0;
+  c[PC_FIX] = n_fix(D);
+  c[PC_EDGE] = n_edge(D);
+  c[PC_ZONE] = n_zone(D);
+}
+
+long long plan_bytes(const Dims &D, int flat3, int mixed) {
+  long long c[PC_N], ints = 0;
+  plan_counts(D, flat3, mixed, c);
+  for (int q = 0; q < PC_N; q++) ints += 2 * nblk(c[q], 64);
+  return (long long)sizeof(StageItem) + 4 * ints;
+}
+
 int plan_build(Plan &p, const StageItem *items, int n) {
   memset(&p, 0, sizeof(p));
   if (!items || n < 1) return GRMHD_ERR_INVALID;
@@ -221,30 +248,13 @@ int plan_build(Plan &p, const StageItem *items, int n) {
   memcpy(p.host_items, items, sizeof(StageItem) * n);
   long long zones = 0, cap = 0;
   for (int g = 0; g < n; g++) {
-    const Dims &D = items[g].A.D;
-    const int fl = items[g].A.flat3, mx = items[g].mixed;
     long long c[PC_N];
-    c[PC_BX1] = n_bounds_x1(D);
-    c[PC_BX2] = n_bounds_x2(D);
-    c[PC_BX3] = n_bounds_x3(D);
-    c[PC_RECON01] = mx ? 0 : n_recon(D, fl);
-    c[PC_RECON2] = (mx || fl) ? 0 : n_recon(D, 0);
-    for (int d = 0; d < 3; d++) {
-      c[PC_FACE0 + d] = mx ? 0 : n_face(D, d, fl);
-      c[PC_FACE0F + d] = mx ? n_face(D, d, fl) : 0;
-    }
-    c[PC_TOF32] = mx ? (long long)NV * D.ntot : 0;
-    c[PC_RECON01F] = mx ? n_recon(D, fl) : 0;
-    c[PC_RECON2F] = (mx && !fl) ? n_recon(D, 0) : 0;
-    c[PC_REPL] = fl ? n_replicate(D) : 0;
-    c[PC_FIX] = n_fix(D);
-    c[PC_EDGE] = n_edge(D);
-    c[PC_ZONE] = n_zone(D);
+    plan_counts(items[g].A.D, items[g].A.flat3, items[g].mixed, c);
     for (int q = 0; q < PC_N; q++) {
       p.count[(size_t)q * n + g] = c[q];
       cap += 2 * nblk(c[q], 64);  // the smallest block the tuner tries
     }
-    zones += n_zone(D);
+    zones += n_zone(items[g].A.D);
   }
   for (int q = 0; q < PC_N; q++) {
     p.bs[q] = BS;

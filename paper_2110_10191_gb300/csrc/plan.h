@@ -82,6 +82,10 @@ struct PlanHook {
 // GRMHD_OK, GRMHD_ERR_INVALID (more than 2^31 - 1 blocks in a launch),
 // GRMHD_ERR_NOMEM or GRMHD_ERR_CUDA.
 int plan_build(Plan &p, const StageItem *items, int n);
+// threads per launch class of one grid (dimensions, flat X3, mixed precision)
+void plan_counts(const Dims &D, int flat3, int mixed, long long c[PC_N]);
+// device bytes a one-grid plan of such a grid holds (item + block tables)
+long long plan_bytes(const Dims &D, int flat3, int mixed);
 void plan_free(Plan &p);
 // Re-lay the block tables of class cls for bs threads per block and block
 // order sched (the results of every grid do not depend on either).

@@ -77,13 +77,39 @@ class grmhd_batch_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class grmhd_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active_zones", ctypes.c_longlong),
+                ("quantum", ctypes.c_int), ("use_graph", ctypes.c_int), ("policy", ctypes.c_int)]
+
+
+class grmhd_server_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("zones", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("stats", grmhd_stats)]
+
+
+class grmhd_server_stats(ctypes.Structure):
+    _fields_ = [("now", ctypes.c_double), ("submitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("rounds", ctypes.c_longlong), ("zone_cycles", ctypes.c_double),
+                ("busy_seconds", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("active", ctypes.c_int), ("pending", ctypes.c_int), ("peak_active", ctypes.c_int),
+                ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_ghost",
            "grmhd_get_prims", "grmhd_step", "grmhd_get_stats", "grmhd_set_time",
            "grmhd_predictor", "grmhd_get_fluxes", "grmhd_next_dt", "grmhd_get_flags",
            "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_profile", "grmhd_get_profile",
            "grmhd_fp64_peak", "grmhd_fluxes_noalloc", "grmhd_batch_create", "grmhd_batch_destroy",
            "grmhd_batch_step", "grmhd_batch_get_info", "grmhd_batch_sync", "grmhd_autotune",
-           "grmhd_batch_autotune", "grmhd_batch_set_launch", "grmhd_strerror"]
+           "grmhd_batch_autotune", "grmhd_batch_set_launch", "grmhd_footprint", "grmhd_server_create",
+           "grmhd_server_submit", "grmhd_server_poll", "grmhd_server_drain", "grmhd_server_get_stats",
+           "grmhd_server_now", "grmhd_server_destroy", "grmhd_strerror"]
 
 
 def lib_path() -> str:
@@ -130,11 +156,22 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_autotune.argtypes = [vp, i, P(d), P(d)]
         L.grmhd_batch_autotune.argtypes = [vp, i, P(d), P(d)]
         L.grmhd_batch_set_launch.argtypes = [vp, i, i, i]
+        L.grmhd_footprint.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params),
+                                      P(ctypes.c_size_t)]
+        L.grmhd_server_create.argtypes = [P(grmhd_server_config), P(vp)]
+        L.grmhd_server_submit.argtypes = [vp, ctypes.c_longlong, P(grmhd_grid), P(grmhd_metric),
+                                          P(grmhd_params), vp, i, vp, i, ctypes.c_longlong, d]
+        L.grmhd_server_poll.argtypes = [vp, P(grmhd_server_result), i, i]
+        L.grmhd_server_drain.argtypes = [vp, i]
+        L.grmhd_server_get_stats.argtypes = [vp, P(grmhd_server_stats)]
+        L.grmhd_server_now.argtypes = [vp]
+        L.grmhd_server_destroy.argtypes = [vp]
         L.grmhd_strerror.argtypes = [i]
         L.grmhd_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name != "grmhd_strerror":
+            if name not in ("grmhd_strerror", "grmhd_server_now"):
                 getattr(L, name).restype = i
+        L.grmhd_server_now.restype = d
         _lib = L
         return L
 
@@ -380,4 +417,93 @@ class Batch:
     def info(self):
         out = grmhd_batch_info()
         _check(self.L.grmhd_batch_get_info(self.h, ctypes.byref(out)), "grmhd_batch_get_info")
+        return out.as_dict()
+
+
+def footprint(problem) -> int:
+    """Device bytes a simulation of this problem holds."""
+    g, m, p = _structs(problem)
+    out = ctypes.c_size_t()
+    _check(load().grmhd_footprint(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p), ctypes.byref(out)),
+           "grmhd_footprint")
+    return out.value
+
+
+class Server:
+    """The serving request loop (``grmhd_server_*``): submit simulations as
+    they arrive, poll finished results.  Input and output arrays are kept
+    referenced here until their result has been polled."""
+
+    FIFO, SWF = 0, 1  # admission: arrival order / smallest work first
+
+    def __init__(self, hbm_budget: int = 0, max_active_zones: int = 0, quantum: int = 8,
+                 use_graph: bool = True, policy: int = 0):
+        self.L = load()
+        cfg = grmhd_server_config(int(hbm_budget), int(max_active_zones), int(quantum), int(use_graph),
+                                  int(policy))
+        self.h = ctypes.c_void_p()
+        _check(self.L.grmhd_server_create(ctypes.byref(cfg), ctypes.byref(self.h)), "grmhd_server_create")
+        self._held = {}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.grmhd_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+            self._held = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def now(self) -> float:
+        return self.L.grmhd_server_now(self.h)
+
+    def submit(self, rid: int, problem, nsteps: int, t_arrival: float = -1.0,
+               out_ghosts: bool = False) -> np.ndarray:
+        """Queue a simulation of ``problem`` for ``nsteps`` cycles; returns the
+        host array its result will be written to.  A problem with fixed
+        boundary ghosts (``info['P_ghost']``) is submitted with its ghosts."""
+        g, m, p = _structs(problem)
+        Pg = problem.info.get("P_ghost") if problem.info else None
+        P_in = np.ascontiguousarray(Pg if Pg is not None else problem.P, dtype=np.float64)
+        n1, n2, n3 = (int(x) for x in problem.n)
+        shape = (NPRIM, n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG) if out_ghosts else (NPRIM, n3, n2, n1)
+        out = np.empty(shape, dtype=np.float64)
+        _check(self.L.grmhd_server_submit(self.h, int(rid), ctypes.byref(g), ctypes.byref(m),
+                                          ctypes.byref(p), P_in.ctypes.data, int(Pg is not None),
+                                          out.ctypes.data, int(out_ghosts), int(nsteps),
+                                          float(t_arrival)), "grmhd_server_submit")
+        self._held[int(rid)] = (P_in, out)
+        return out
+
+    def poll(self, max_results: int = 64, wait_ms: int = 0):
+        """Finished requests as dicts (id, status, zones, steps, t_arrival,
+        t_admit, t_done, stats, P)."""
+        buf = (grmhd_server_result * max(int(max_results), 1))()
+        n = self.L.grmhd_server_poll(self.h, buf, int(max_results), int(wait_ms))
+        if n < 0:
+            raise GrmhdError(n, "grmhd_server_poll")
+        out = []
+        for q in range(n):
+            r = buf[q]
+            held = self._held.pop(int(r.id), (None, None))
+            out.append({"id": r.id, "status": r.status, "zones": r.zones, "steps": r.steps,
+                        "t_arrival": r.t_arrival, "t_admit": r.t_admit, "t_done": r.t_done,
+                        "stats": r.stats.as_dict(), "P": held[1]})
+        return out
+
+    def drain(self, timeout_ms: int = -1) -> None:
+        _check(self.L.grmhd_server_drain(self.h, int(timeout_ms)), "grmhd_server_drain")
+
+    def stats(self):
+        out = grmhd_server_stats()
+        _check(self.L.grmhd_server_get_stats(self.h, ctypes.byref(out)), "grmhd_server_get_stats")
         return out.as_dict()

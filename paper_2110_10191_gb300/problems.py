@@ -21,6 +21,8 @@ Problems (all with GM = c = 1, the paper's units, "Implementation Notes"):
 * ``orszag_tang``  -- flat periodic Orszag-Tang vortex (batched workloads).
 * ``batch_2d``     -- many uneven flat 2D grids of modes and vortices (batched
   workload).
+* ``serving_stream`` -- Poisson arrivals of tori and Bondi inflows of random
+  size, length and precision (serving workload).
 
 Random numbers come from a counter-based generator (splitmix64 of
 seed and zone index), so a zone's value does not depend on the grid split.
@@ -255,6 +257,48 @@ def batch_2d(ngrid: int = 64, nmin: int = 32, nmax: int = 256, seed: int = 0,
         pr.info["kind"] = kinds[g]
         out.append(pr)
     return out
+
+
+# --------------------------------------------------------------------------
+# Arrival stream of the serving workload
+# --------------------------------------------------------------------------
+
+def serving_stream(nreq: int = 200, rate: float = 4.0, seed: int = 0) -> list:
+    """``nreq`` requests arriving as a Poisson process of ``rate`` per second:
+    60% Fishbone-Moncrief tori (spin a uniform in [0, 0.98], cubic N uniform
+    in {64..192}), 40% 2D Bondi inflows (N x N, N uniform in {96..160}); each
+    asks for a number of cycles uniform in {20..200} and runs in FP64 or in
+    the mixed mode with probability 1/2.  Returns dicts (id, t_arrival,
+    kind, n, a, steps, precision); ``serving_problem`` builds a request's
+    input.  Draws: splitmix_uniform(seed, 8 r + field) for request r."""
+    idx = np.arange(8 * nreq, dtype=np.uint64)
+    u = splitmix_uniform(seed, idx).reshape(nreq, 8)
+    t = 0.0
+    out = []
+    for r in range(nreq):
+        t += -math.log(1.0 - u[r, 0]) / rate
+        torus = u[r, 1] < 0.6
+        if torus:
+            n = 64 + min(int(u[r, 2] * 129), 128)
+            a = 0.98 * u[r, 3]
+        else:
+            n = 96 + min(int(u[r, 2] * 65), 64)
+            a = 0.0
+        out.append({"id": r, "t_arrival": t, "kind": "torus" if torus else "bondi", "n": n, "a": a,
+                    "steps": 20 + min(int(u[r, 4] * 181), 180), "precision": int(u[r, 5] < 0.5)})
+    return out
+
+
+def serving_problem(req: dict) -> "Problem":
+    """The input of one serving request (see serving_stream)."""
+    if req["kind"] == "torus":
+        n = req["n"]
+        pr = fm_torus(n, n, n, a=req["a"], seed=req["id"])
+    else:
+        pr = bondi(req["n"], req["n"])
+    pr.precision = req["precision"]
+    pr.name = "req%03d_%s" % (req["id"], pr.name)
+    return pr
 
 
 # --------------------------------------------------------------------------

@@ -136,3 +136,26 @@ def test_batch_2d_recipe():
     # the kind shares depend on ngrid; sizes, reconstruction and draws do not
     assert [p.n for p in few] == [p.n for p in probs[:8]]
     assert [p.recon for p in few] == [p.recon for p in probs[:8]]
+
+
+def test_serving_stream_recipe():
+    """200 Poisson arrivals at 4/s: 60/40 tori/Bondi, sizes, spins, cycle
+    counts and precisions in their ranges, deterministic."""
+    st = pb.serving_stream()
+    assert len(st) == 200 and st == pb.serving_stream()
+    t = np.array([r["t_arrival"] for r in st])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert 0.2 < gaps.mean() < 0.3                      # 1/rate = 0.25 s
+    tori = [r for r in st if r["kind"] == "torus"]
+    assert 0.5 < len(tori) / 200 < 0.7
+    for r in st:
+        assert 20 <= r["steps"] <= 200 and r["precision"] in (0, 1)
+        if r["kind"] == "torus":
+            assert 64 <= r["n"] <= 192 and 0.0 <= r["a"] <= 0.98
+        else:
+            assert 96 <= r["n"] <= 160
+    assert 0.35 < np.mean([r["precision"] for r in st]) < 0.65
+    small = pb.serving_problem({"id": 3, "kind": "bondi", "n": 96, "a": 0.0, "steps": 20,
+                                "precision": 1, "t_arrival": 0.0})
+    assert small.n == (96, 96, 1) and small.precision == 1
