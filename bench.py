@@ -12,7 +12,8 @@ zone-cycles/s (zones advanced by one full cycle per second).
 N > 1 runs under torchrun, one process per GPU; every rank advances its own
 replica (the single-grid path is not decomposed), scaling "weak".  Rank 0
 prints one JSON line.  Besides the headline it carries the same workload in
-the mixed-precision mode ("mixed"), 64 uneven flat 2D grids stepped as one
+the mixed-precision and float-float modes ("mixed", "float_float"), 64
+uneven flat 2D grids stepped as one
 batch against the same grids stepped one by one ("batched"), and the
 mixed-precision error of 100 cycles of the 288x128x128 torus against the
 FP64 path ("mixed_accuracy"), and a prefix of the serving workload's
@@ -244,20 +245,32 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1)
 
 
-def mixed_throughput(grmhd, pr, steps, warmup, stream):
-    """The same workload in the mixed-precision mode."""
+PREC_DTYPE = {
+    1: "mixed: FP32 reconstruction, fluid states, signal speeds, LLF fluxes; "
+       "FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
+    2: "float-float: reconstruction, fluid states, signal speeds, LLF fluxes in pairs of FP32 "
+       "words (~48 significant bits); FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
+}
+
+
+def mixed_throughput(grmhd, pr, steps, warmup, stream, precision=1):
+    """The same workload in the mixed-precision (1) or float-float (2) mode,
+    with the device time of each kernel class."""
     import dataclasses
-    pm = dataclasses.replace(pr, precision=1)
+    pm = dataclasses.replace(pr, precision=precision)
     s = grmhd.Sim(pm, stream=stream)
     s.set_prims(pm.P)
     s.step(warmup)
     ms = _timed(stream, lambda: s.step(steps, sync=False))
+    s.profile(True)
+    s.get_profile(reset=True)
+    s.step(2, sync=False)
+    prof = s.get_profile(reset=True)
     s.close()
     z = pr.n[0] * pr.n[1] * pr.n[2]
     return {"value": z * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
-            "dtype": "mixed: FP32 reconstruction, fluid states, signal speeds, LLF fluxes; "
-                     "FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
-            "steps": steps}
+            "dtype": PREC_DTYPE[precision], "steps": steps,
+            "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()}}
 
 
 def batched_throughput(grmhd, steps, warmup, stream, nmin=32, nmax=256):
@@ -521,7 +534,10 @@ def main():
 
     extras = {}
     if not args.no_extras:
-        extras["mixed"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream)
+        extras["mixed"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream, 1)
+        extras["float_float"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream, 2)
+        extras["float_float"]["parity"] = ("one step against the FP64 oracle within 3e-11 of each "
+                                           "primitive group's scale (tests/test_gpu_ff.py)")
         extras["batched"] = batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, stream)
         extras["batched_small"] = batched_throughput(grmhd, args.steps, args.warmup, stream,
                                                      nmin=32, nmax=48)

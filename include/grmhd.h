@@ -62,6 +62,8 @@ extern "C" {
 #define GRMHD_PREC_FP64 0  /* every step in FP64 */
 #define GRMHD_PREC_MIXED 1 /* reconstruction, fluid states, signal speeds and LLF fluxes
                               in FP32; geometry, flux-CT, update, inversion, bounds FP64 */
+#define GRMHD_PREC_FF 2    /* the same split with the flux stage in float-float arithmetic
+                              (pairs of FP32 words, ~48 significant bits) on the FP32 pipe */
 
 typedef struct grmhd_sim grmhd_sim; /* opaque, library-owned */
 

@@ -85,6 +85,8 @@ static void free_all(grmhd_sim *s) {
     if (p) cudaFree(p);
   if (s->Pf) cudaFree(s->Pf);
   if (s->geomf) cudaFree(s->geomf);
+  if (s->Pff) cudaFree(s->Pff);
+  if (s->geomff) cudaFree(s->geomff);
   if (s->pflag) cudaFree(s->pflag);
   if (s->fflag) cudaFree(s->fflag);
   if (s->clk) cudaFree(s->clk);
@@ -114,7 +116,8 @@ static int validate(const grmhd_grid *grid, const grmhd_metric *metric, const gr
   if (metric->kind == GRMHD_METRIC_MKS_KERR && !(fabs(metric->a) < 1.0)) return GRMHD_ERR_INVALID;
   if (!(params->gamma > 1.0) || !(params->cfl > 0.0)) return GRMHD_ERR_INVALID;
   if (params->recon != GRMHD_RECON_MC && params->recon != GRMHD_RECON_WENO5) return GRMHD_ERR_INVALID;
-  if (params->precision != GRMHD_PREC_FP64 && params->precision != GRMHD_PREC_MIXED)
+  if (params->precision != GRMHD_PREC_FP64 && params->precision != GRMHD_PREC_MIXED &&
+      params->precision != GRMHD_PREC_FF)
     return GRMHD_ERR_INVALID;
   if (params->floors_on && metric->kind != GRMHD_METRIC_MKS_KERR) return GRMHD_ERR_INVALID;
   for (int d = 0; d < 3; d++)
@@ -141,13 +144,15 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
   const int rc = validate(grid, metric, params, &D);
   if (rc != GRMHD_OK) return rc;
   const size_t tot = (size_t)D.ntot, n2d = (size_t)D.n2d;
-  const int mixed = params->precision == GRMHD_PREC_MIXED;
   size_t b = sizeof(double) * NV * tot * 8                 // P, Ph, F1..3, Lf, Rf, Uc
              + sizeof(double) * 3 * tot                    // EMFs
              + sizeof(double) * (NLOC * G_NCOMP + C_NCOMP + 2) * n2d  // geometry, connection, bounds
              + sizeof(int) * 2 * tot + sizeof(Clock);     // flags, clock
-  if (mixed) b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
-  b += (size_t)plan_bytes(D, flat3_of(D, params), mixed);
+  if (params->precision == GRMHD_PREC_MIXED)
+    b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
+  if (params->precision == GRMHD_PREC_FF)
+    b += 2 * sizeof(float) * NV * tot + 2 * sizeof(float) * NLOC * G_NCOMP * n2d;
+  b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision);
   *bytes = b;
   return GRMHD_OK;
 }
@@ -203,6 +208,9 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   if (ok && params->precision == GRMHD_PREC_MIXED)
     ok = cudaMalloc(&s->Pf, sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
          cudaMalloc(&s->geomf, sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess;
+  if (ok && params->precision == GRMHD_PREC_FF)
+    ok = cudaMalloc(&s->Pff, 2 * sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
+         cudaMalloc(&s->geomff, 2 * sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -240,6 +248,7 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   if (rc == GRMHD_OK) {
     launch_geometry(G, st);
     if (s->geomf) launch_to_f32((long long)NLOC * G_NCOMP * D.n2d, s->geom, s->geomf, st);
+    if (s->geomff) launch_to_ff((long long)NLOC * G_NCOMP * D.n2d, s->geom, s->geomff, st);
     rc = launched();
   }
   if (rc == GRMHD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
@@ -280,7 +289,9 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   it.fflag = s->fflag;
   it.Pf = s->Pf;
   it.geomf = s->geomf;
-  it.mixed = (params->precision == GRMHD_PREC_MIXED) ? 1 : 0;
+  it.Pff = s->Pff;
+  it.geomff = s->geomff;
+  it.prec = params->precision;
   rc = plan_build(s->plan, &it, 1);
   if (rc != GRMHD_OK) {
     free_all(s);
@@ -540,6 +551,8 @@ extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
   if (s->geomf)
     launch_to_f32((long long)G_NCOMP * n2d, s->geom + (long long)loc * G_NCOMP * n2d,
                   s->geomf + (long long)loc * G_NCOMP * n2d, s->st);
+  if (s->geomff)  // the whole split copy (its low words follow all locations' high words)
+    launch_to_ff((long long)NLOC * G_NCOMP * n2d, s->geom, s->geomff, s->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s->st));
   return GRMHD_OK;

@@ -1,0 +1,323 @@
+// ff_bodies.cuh -- per-thread bodies of the flux stage of the float-float
+// mode (GRMHD_PREC_FF): the reconstruction, the fluid states, the signal
+// speeds and the local Lax-Friedrichs flux in float-float arithmetic
+// (ff.cuh, about 48 significant bits) on the FP32 pipe; the fluxes are
+// stored in FP64, and the flux-CT, the update, the 1D_W inversion and the
+// bounds run in FP64 as in the FP64 mode.  Same formulas as the FP64 bodies
+// (grmhd_dev.cuh), with the energy flux formed without the rest-mass
+// cancellation as in the FP32 bodies (grmhd_f32.cuh), since the 5 bits the
+// float pair lacks would otherwise be lost 1e3-fold at rho >> u.
+//
+// Data: the stage input split once per stage into high and low float words
+// ([2][8][ntot]: all high words, then all low words), the face values in the
+// same split layout, and a split copy of the geometry ([2][NLOC][G_NCOMP][n2d]).
+#pragma once
+
+#include "ff.cuh"
+#include "grmhd_dev.cuh"
+#include "step_bodies.cuh"
+
+namespace grmhd {
+
+__device__ __forceinline__ ff ff_load(const float *__restrict__ hi, long long lo_off, long long i) {
+  ff r;
+  r.hi = __ldg(hi + i);
+  r.lo = __ldg(hi + lo_off + i);
+  return r;
+}
+
+__device__ __forceinline__ void ff_store(float *hi, long long lo_off, long long i, ff v) {
+  hi[i] = v.hi;
+  hi[lo_off + i] = v.lo;
+}
+
+// one value split into its two words ([2][n]); values beyond the float
+// range (inverse-metric components on the polar axis, which no flux reads)
+// are clamped to +-FLT_MAX
+__device__ __forceinline__ void to_ff_body(const double *__restrict__ src, float *__restrict__ dst,
+                                           long long n, long long t) {
+  if (t >= n) return;
+  const double x = src[t];
+  ff v;
+  if (fabs(x) > 3.4028234663852886e38) {
+    v.hi = (x > 0.0) ? 3.4028234663852886e38f : -3.4028234663852886e38f;
+    v.lo = 0.0f;
+  } else {
+    v = ff_from(x);
+  }
+  dst[t] = v.hi;
+  dst[n + t] = v.lo;
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction
+// ---------------------------------------------------------------------------
+// MC limited slope of x1 with neighbours x0, x2 (the FP64 body's decisions
+// taken on the float-float differences)
+__device__ __forceinline__ ff mc_slope_ff(ff x0, ff x1, ff x2) {
+  const ff dm = ff_sub(x1, x0), dp = ff_sub(x2, x1);
+  if (!((dm.hi > 0.0f && dp.hi > 0.0f) || (dm.hi < 0.0f && dp.hi < 0.0f))) return ff_f(0.0f);
+  const ff dc = ff_ldexp(ff_add(dm, dp), 0.5f);
+  const ff m = ff_min(ff_min(ff_abs(ff_ldexp(dm, 2.0f)), ff_abs(dc)), ff_abs(ff_ldexp(dp, 2.0f)));
+  return (dc.hi > 0.0f) ? m : ff_neg(m);
+}
+
+// Both WENO5 face values of the middle zone of a..e: the FP64 body's
+// first/second-difference form, with the weights d_k/(eps + beta_k)^2
+// normalised by the smallest (eps + beta): r_k = min_j e_j / e_k <= 1, so
+// no product leaves the float exponent range (eps = 1e-26 makes e_k^2 as
+// small as 1e-50); a weight that underflows is negligible next to the
+// dominant one, which is 1.
+__device__ __forceinline__ void weno5_pair_ff(ff a, ff b, ff c, ff d, ff e, ff &lo, ff &hi) {
+  const ff dm2 = ff_sub(b, a), dm1 = ff_sub(c, b), dp1 = ff_sub(d, c), dp2 = ff_sub(e, d);
+  const ff D0 = ff_sub(dm1, dm2), D1 = ff_sub(dp1, dm1), D2 = ff_sub(dp2, dp1);
+  const ff s0 = ff_add(D0, ff_ldexp(dm1, 2.0f));
+  const ff s1 = ff_add(dm1, dp1);
+  const ff s2 = ff_sub(D2, ff_ldexp(dp1, 2.0f));
+  // 12 (eps + beta_k) = 12 eps + 13 D_k^2 + 3 s_k^2; 12 eps = 1.2e-25 split
+  // into its float words (high 0x16148d85, low 0x89c7ce7b: the double
+  // constant to 2e-41)
+  ff eps12;
+  eps12.hi = __int_as_float(0x16148d85);
+  eps12.lo = __int_as_float((int)0x89c7ce7bu);
+  const ff e0 = ff_add(ff_add(ff_mul_f(ff_sqr(D0), 13.0f), ff_mul_f(ff_sqr(s0), 3.0f)), eps12);
+  const ff e1 = ff_add(ff_add(ff_mul_f(ff_sqr(D1), 13.0f), ff_mul_f(ff_sqr(s1), 3.0f)), eps12);
+  const ff e2 = ff_add(ff_add(ff_mul_f(ff_sqr(D2), 13.0f), ff_mul_f(ff_sqr(s2), 3.0f)), eps12);
+  const ff emin = ff_min(ff_min(e0, e1), e2);
+  const ff r0 = ff_mul(emin, ff_rcp(e0)), r1 = ff_mul(emin, ff_rcp(e1)), r2 = ff_mul(emin, ff_rcp(e2));
+  const ff w0 = ff_sqr(r0), w1 = ff_mul_f(ff_sqr(r1), 6.0f), w2 = ff_sqr(r2);
+  const ff w2x3 = ff_mul_f(w2, 3.0f), w0x3 = ff_mul_f(w0, 3.0f);
+  const ff m3 = ff_mul_f(dm1, 3.0f), p3 = ff_mul_f(dp1, 3.0f);
+  // high face: linear weights 1 : 6 : 3 on stencils 0, 1, 2
+  const ff nh = ff_add(ff_add(ff_mul(w0, ff_add(ff_ldexp(D0, 2.0f), m3)),
+                              ff_mul(w1, ff_add(dm1, ff_ldexp(dp1, 2.0f)))),
+                       ff_mul(w2x3, ff_sub(p3, D2)));
+  const ff H = ff_mul_f(ff_add(ff_add(w0, w1), w2x3), 6.0f);
+  // low face: the mirrored stencils (2, 1, 0) with the same linear weights
+  const ff nl = ff_sub(ff_sub(ff_mul(w2, ff_sub(ff_ldexp(D2, 2.0f), p3)),
+                              ff_mul(w1, ff_add(dp1, ff_ldexp(dm1, 2.0f)))),
+                       ff_mul(w0x3, ff_add(m3, D0)));
+  const ff L = ff_mul_f(ff_add(ff_add(w2, w1), w0x3), 6.0f);
+  hi = ff_add(c, ff_div(nh, H));
+  lo = ff_add(c, ff_div(nl, L));
+}
+
+// Zone-centric reconstruction along DIR in float-float: Pff is the split
+// stage input ([2][8][ntot]), Lf/Rf the split low/high face values.
+template <int DIR, int RECON>
+__device__ __forceinline__ void recon_ff_body(const StepArgs &A, const float *__restrict__ Pff,
+                                              float *__restrict__ Lf, float *__restrict__ Rf,
+                                              long long t) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2;
+  if (t >= n_recon(D, A.flat3)) return;
+  const int i = NG - 1 + (int)(t % e0);
+  const int j = NG - 1 + (int)((t / e0) % e1);
+  const int k = (A.flat3 ? NG : NG - 1) + (int)(t / ((long long)e0 * e1));
+  const long long c = zid(D, i, j, k);
+  const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+  const long long half = (long long)NV * D.ntot;
+#pragma unroll 1
+  for (int v = 0; v < NV; v++) {
+    const long long o = v * D.ntot + c;
+    ff lo, hi;
+    if (RECON == 1) {
+      weno5_pair_ff(ff_load(Pff, half, o - 2 * st), ff_load(Pff, half, o - st), ff_load(Pff, half, o),
+                    ff_load(Pff, half, o + st), ff_load(Pff, half, o + 2 * st), lo, hi);
+    } else {
+      const ff x1 = ff_load(Pff, half, o);
+      const ff h = ff_ldexp(mc_slope_ff(ff_load(Pff, half, o - st), x1, ff_load(Pff, half, o + st)), 0.5f);
+      lo = ff_sub(x1, h);
+      hi = ff_add(x1, h);
+    }
+    ff_store(Lf, half, o, lo);
+    ff_store(Rf, half, o, hi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Face fluxes
+// ---------------------------------------------------------------------------
+struct GeoFF {
+  ff gcov[10], gcon[10], gdet, alpha, ialpha, omalpha;
+};
+
+// geometry of one location from the split copy ([2][NLOC][G_NCOMP][n2d];
+// g points at this location's components, lo_off = NLOC G_NCOMP n2d)
+__device__ __forceinline__ void load_geo_ff(const float *__restrict__ g, long long lo_off, long long n2d,
+                                            long long ij, GeoFF &G) {
+#pragma unroll
+  for (int q = 0; q < 10; q++) G.gcov[q] = ff_load(g, lo_off, (G_GCOV + q) * n2d + ij);
+#pragma unroll
+  for (int q = 0; q < 10; q++) G.gcon[q] = ff_load(g, lo_off, (G_GCON + q) * n2d + ij);
+  G.gdet = ff_load(g, lo_off, G_GDET * n2d + ij);
+  G.alpha = ff_load(g, lo_off, G_ALPHA * n2d + ij);
+  G.ialpha = ff_load(g, lo_off, G_IALPHA * n2d + ij);
+  G.omalpha = ff_load(g, lo_off, G_OMALPHA * n2d + ij);
+}
+
+// Fluid state as fluid_state (grmhd_dev.cuh), plus opu_t = 1 + u_t formed
+// as (1 - alpha) - alpha (gamma - 1) + g_tj utilde^j, gamma - 1 = q^2/(1 + gamma).
+struct FStateFF {
+  ff ucon[4], ucov[4], bcon[4], bcov[4], bsq, opu_t;
+};
+
+__device__ __forceinline__ ff dot3(ff a0, ff b0, ff a1, ff b1, ff a2, ff b2) {
+  return ff_add(ff_add(ff_mul(a0, b0), ff_mul(a1, b1)), ff_mul(a2, b2));
+}
+
+__device__ __forceinline__ void fluid_state_ff(const ff P[NV], const GeoFF &G, FStateFF &s) {
+  const ff v1 = P[U1], v2 = P[U2], v3 = P[U3];
+  const ff l1 = dot3(G.gcov[SY(1, 1)], v1, G.gcov[SY(1, 2)], v2, G.gcov[SY(1, 3)], v3);
+  const ff l2 = dot3(G.gcov[SY(1, 2)], v1, G.gcov[SY(2, 2)], v2, G.gcov[SY(2, 3)], v3);
+  const ff l3 = dot3(G.gcov[SY(1, 3)], v1, G.gcov[SY(2, 3)], v2, G.gcov[SY(3, 3)], v3);
+  const ff qsq = dot3(l1, v1, l2, v2, l3, v3);
+  const ff g2 = ff_add_f(qsq, 1.0f);
+  const ff rg = ff_rsqrt(g2);
+  const ff gam = ff_mul(g2, rg);
+  const ff ga = ff_mul(gam, G.alpha);
+  const ff sh = dot3(G.gcov[SY(0, 1)], v1, G.gcov[SY(0, 2)], v2, G.gcov[SY(0, 3)], v3);
+  s.opu_t = ff_add(ff_sub(G.omalpha, ff_mul(ff_mul(G.alpha, qsq), ff_rcp(ff_add_f(gam, 1.0f)))), sh);
+  s.ucon[0] = ff_mul(gam, G.ialpha);
+  s.ucon[1] = ff_sub(v1, ff_mul(ga, G.gcon[SY(0, 1)]));
+  s.ucon[2] = ff_sub(v2, ff_mul(ga, G.gcon[SY(0, 2)]));
+  s.ucon[3] = ff_sub(v3, ff_mul(ga, G.gcon[SY(0, 3)]));
+  s.ucov[0] = ff_sub(sh, ga);
+  s.ucov[1] = l1;
+  s.ucov[2] = l2;
+  s.ucov[3] = l3;
+  const ff bt = dot3(P[B1], l1, P[B2], l2, P[B3], l3);
+  const ff iut = ff_mul(G.alpha, rg);  // 1/u^t
+  s.bcon[0] = bt;
+  s.bcon[1] = ff_mul(ff_add(P[B1], ff_mul(bt, s.ucon[1])), iut);
+  s.bcon[2] = ff_mul(ff_add(P[B2], ff_mul(bt, s.ucon[2])), iut);
+  s.bcon[3] = ff_mul(ff_add(P[B3], ff_mul(bt, s.ucon[3])), iut);
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    ff a = ff_f(0.0f);
+#pragma unroll
+    for (int n = 0; n < 4; n++) a = ff_add(a, ff_mul(G.gcov[SY(m, n)], s.bcon[n]));
+    s.bcov[m] = a;
+  }
+  s.bsq = ff_add(ff_add(ff_mul(s.bcon[0], s.bcov[0]), ff_mul(s.bcon[1], s.bcov[1])),
+                 ff_add(ff_mul(s.bcon[2], s.bcov[2]), ff_mul(s.bcon[3], s.bcov[3])));
+}
+
+// acc += F^dir + coef U without the sqrt(-g) factor (flux_cons_acc), the
+// energy row as rho uc (1 + u_t) + (w - rho) uc u_t - bc b_t + coef pt
+__device__ __forceinline__ void flux_cons_acc_ff(const ff P[NV], const FStateFF &s, ff gm1,
+                                                 int dir, ff coef, ff acc[NV]) {
+  const ff pg = ff_mul(P[UU], gm1);
+  const ff w = ff_add(ff_add(P[RHO], P[UU]), ff_add(pg, s.bsq));
+  const ff pt = ff_add(pg, ff_ldexp(s.bsq, 0.5f));
+  const ff uc = ff_add(s.ucon[dir], ff_mul(coef, s.ucon[0]));
+  const ff bc = ff_add(s.bcon[dir], ff_mul(coef, s.bcon[0]));
+  const ff wuc = ff_mul(w, uc);
+  ff T[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; nu++) T[nu] = ff_sub(ff_mul(wuc, s.ucov[nu]), ff_mul(bc, s.bcov[nu]));
+  T[dir] = ff_add(T[dir], pt);
+  const ff mf = ff_mul(P[RHO], uc);
+  acc[RHO] = ff_add(acc[RHO], mf);
+  const ff en = ff_add(ff_mul(mf, s.opu_t),
+                       ff_sub(ff_mul(ff_mul(ff_sub(w, P[RHO]), uc), s.ucov[0]), ff_mul(bc, s.bcov[0])));
+  acc[UU] = ff_add(acc[UU], ff_add(en, ff_mul(coef, pt)));
+  acc[U1] = ff_add(acc[U1], T[1]);
+  acc[U2] = ff_add(acc[U2], T[2]);
+  acc[U3] = ff_add(acc[U3], T[3]);
+  acc[B1] = ff_add(acc[B1], ff_sub(ff_mul(s.bcon[1], uc), ff_mul(bc, s.ucon[1])));
+  acc[B2] = ff_add(acc[B2], ff_sub(ff_mul(s.bcon[2], uc), ff_mul(bc, s.ucon[2])));
+  acc[B3] = ff_add(acc[B3], ff_sub(ff_mul(s.bcon[3], uc), ff_mul(bc, s.ucon[3])));
+}
+
+// fast magnetosonic speeds along dir (mhd_vchar)
+// gam: the adiabatic index, ggm1 = gam (gam - 1), both float-float
+__device__ __forceinline__ void mhd_vchar_ff(const ff P[NV], const FStateFF &s, const GeoFF &G,
+                                             ff gam, ff ggm1, int dir, ff &vmax, ff &vmin) {
+  const ff ef = ff_add(P[RHO], ff_mul(P[UU], gam));
+  const ff ee = ff_add(s.bsq, ef);
+  const ff iee = ff_rcp(ff_mul(ef, ee));
+  const ff va2 = ff_mul(ff_mul(s.bsq, ef), iee);
+  const ff cs2 = ff_mul(ff_mul(ff_mul(P[UU], ggm1), ee), iee);
+  const ff cms2 = ff_sub(ff_add(cs2, va2), ff_mul(cs2, va2));
+  const ff Asq = G.gcon[SY(dir, dir)];
+  const ff Bsq = G.gcon[SY(0, 0)];
+  const ff AB = G.gcon[SY(0, dir)];
+  const ff Au = s.ucon[dir];
+  const ff Bu = s.ucon[0];
+  const ff AuBu = ff_mul(Au, Bu);
+  const ff qa = ff_sub(ff_sqr(Bu), ff_mul(ff_add(Bsq, ff_sqr(Bu)), cms2));
+  const ff qb = ff_mul_f(ff_sub(AuBu, ff_mul(ff_add(AB, AuBu), cms2)), -2.0f);
+  const ff qc = ff_sub(ff_sqr(Au), ff_mul(ff_add(Asq, ff_sqr(Au)), cms2));
+  ff disc = ff_sub(ff_sqr(qb), ff_mul_f(ff_mul(qa, qc), 4.0f));
+  disc = (disc.hi > 0.0f) ? ff_sqrt(disc) : ff_f(0.0f);
+  const ff i2a = ff_ldexp(ff_rcp(qa), 0.5f);
+  const ff v1 = ff_mul(ff_add(ff_neg(qb), disc), i2a);
+  const ff v2 = ff_mul(ff_sub(ff_neg(qb), disc), i2a);
+  vmax = ff_max(v1, v2);
+  vmin = ff_min(v1, v2);
+}
+
+// One thread per face: split states Rf(c - st) (left) and Lf(c) (right),
+// split geometry; the LLF flux stored in FP64.  Every thread of the block
+// must call it (signal-speed block maximum).
+template <int DIR>
+__device__ __forceinline__ void face_ff_body(const StepArgs &A, const float *__restrict__ geomff,
+                                             const float *__restrict__ Lf,
+                                             const float *__restrict__ Rf, double *__restrict__ F,
+                                             long long t) {
+  const Dims &D = A.D;
+  int lo[3], ext[3];
+  face_box(D, DIR, A.flat3, lo, ext);
+  const long long nface = (long long)ext[0] * ext[1] * ext[2];
+  const bool active = t < nface;
+  double ctop = 0.0;
+  if (active) {
+    const int i = lo[0] + (int)(t % ext[0]);
+    const int j = lo[1] + (int)((t / ext[0]) % ext[1]);
+    const int k = lo[2] + (int)(t / ((long long)ext[0] * ext[1]));
+    const long long c = zid(D, i, j, k);
+    const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+    const long long half = (long long)NV * D.ntot;
+    ff PL[NV], PR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      PL[v] = ff_load(Rf, half, v * D.ntot + c - st);
+      PR[v] = ff_load(Lf, half, v * D.ntot + c);
+    }
+    const int loc = (DIR == 0) ? LOC_FACE1 : (DIR == 1) ? LOC_FACE2 : LOC_CENT;
+    GeoFF G;
+    load_geo_ff(geomff + (long long)loc * G_NCOMP * D.n2d, (long long)NLOC * G_NCOMP * D.n2d, D.n2d,
+                (long long)j * D.s[0] + i, G);
+    const ff gam = ff_from(A.gam), gm1 = ff_from(A.gam - 1.0), ggm1 = ff_from(A.gam * (A.gam - 1.0));
+    FStateFF sL, sR;
+    fluid_state_ff(PL, G, sL);
+    fluid_state_ff(PR, G, sR);
+    ff vmaxL, vminL, vmaxR, vminR;
+    mhd_vchar_ff(PL, sL, G, gam, ggm1, DIR + 1, vmaxL, vminL);
+    mhd_vchar_ff(PR, sR, G, gam, ggm1, DIR + 1, vmaxR, vminR);
+    const ff z = ff_f(0.0f);
+    const ff cmax = ff_max(ff_max(z, vmaxL), vmaxR);
+    const ff cmin = ff_max(ff_max(z, ff_neg(vminL)), ff_neg(vminR));
+    const ff ct = ff_max(cmax, cmin);
+    ff acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) acc[v] = z;
+    flux_cons_acc_ff(PL, sL, gm1, DIR + 1, ct, acc);
+    flux_cons_acc_ff(PR, sR, gm1, DIR + 1, ff_neg(ct), acc);
+    const ff hg = ff_ldexp(G.gdet, 0.5f);
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v * D.ntot + c] = ff_to(ff_mul(hg, acc[v]));
+    bool interior = true;
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      if (e == DIR) continue;
+      const int q = (e == 0) ? i : (e == 1) ? j : k;
+      interior = interior && (q >= NG) && (q < D.n[e] + NG);
+    }
+    if (interior) ctop = ff_to(ct);
+  }
+  warp_block_max(ctop, &A.clk->ctop_bits[DIR]);
+}
+
+}  // namespace grmhd

@@ -54,6 +54,8 @@ void launch_fix_ct(const StepArgs &A, double *F[3], double *emf, cudaStream_t st
 
 // FP32 copy of n doubles (clamped to the float range)
 void launch_to_f32(long long n, const double *src, float *dst, cudaStream_t st);
+// float-float split of n doubles: dst[0..n) high words, dst[n..2n) low words
+void launch_to_ff(long long n, const double *src, float *dst, cudaStream_t st);
 // pack interior <-> ghost layout
 void launch_pack(const Dims &D, const double *src, double *dst, int to_ghost, cudaStream_t st);
 

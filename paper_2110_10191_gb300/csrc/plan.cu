@@ -8,6 +8,7 @@
 
 #include "../../include/grmhd.h"
 #include "grmhd_impl.h"
+#include "ff_bodies.cuh"
 #include "mixed_bodies.cuh"
 #include "plan.h"
 #include "step_bodies.cuh"
@@ -88,6 +89,34 @@ __global__ void __launch_bounds__(BS_MAX) kp_face_f32(BView V) {
   const float *Lf = (const float *)it.Lf, *Rf = (const float *)it.Rf;
   if (DIR == 2 && it.A.flat3) Lf = Rf = it.Pf;
   face_f32_body<DIR>(it.A, it.geomf, Lf, Rf, it.F[DIR], t);
+}
+
+__global__ void kp_to_ff(BView V, int in) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  to_ff_body(arr(it, in), it.Pff, (long long)NV * it.A.D.ntot, block_tid(V, g));
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(BS_MAX) kp_recon_ff(BView V) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  const long long t = block_tid(V, g);
+  float *Lf = (float *)it.Lf, *Rf = (float *)it.Rf;
+  if (it.A.recon == 1)
+    recon_ff_body<DIR, 1>(it.A, it.Pff, Lf, Rf, t);
+  else
+    recon_ff_body<DIR, 0>(it.A, it.Pff, Lf, Rf, t);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(BS_MAX) kp_face_ff(BView V) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  const long long t = block_tid(V, g);
+  const float *Lf = (const float *)it.Lf, *Rf = (const float *)it.Rf;
+  if (DIR == 2 && it.A.flat3) Lf = Rf = it.Pff;
+  face_ff_body<DIR>(it.A, it.geomff, Lf, Rf, it.F[DIR], t);
 }
 
 __global__ void kp_replicate(BView V) {
@@ -208,29 +237,34 @@ int upload_tables(Plan &p) {
 
 }  // namespace
 
-void plan_counts(const Dims &D, int flat3, int mixed, long long c[PC_N]) {
-  const int fl = flat3, mx = mixed;
+void plan_counts(const Dims &D, int flat3, int prec, long long c[PC_N]) {
+  const int fl = flat3;
+  const bool f64 = prec == GRMHD_PREC_FP64, mx = prec == GRMHD_PREC_MIXED, fx = prec == GRMHD_PREC_FF;
   c[PC_BX1] = n_bounds_x1(D);
   c[PC_BX2] = n_bounds_x2(D);
   c[PC_BX3] = n_bounds_x3(D);
-  c[PC_RECON01] = mx ? 0 : n_recon(D, fl);
-  c[PC_RECON2] = (mx || fl) ? 0 : n_recon(D, 0);
+  c[PC_RECON01] = f64 ? n_recon(D, fl) : 0;
+  c[PC_RECON2] = (f64 && !fl) ? n_recon(D, 0) : 0;
   for (int d = 0; d < 3; d++) {
-    c[PC_FACE0 + d] = mx ? 0 : n_face(D, d, fl);
+    c[PC_FACE0 + d] = f64 ? n_face(D, d, fl) : 0;
     c[PC_FACE0F + d] = mx ? n_face(D, d, fl) : 0;
+    c[PC_FACE0X + d] = fx ? n_face(D, d, fl) : 0;
   }
   c[PC_TOF32] = mx ? (long long)NV * D.ntot : 0;
   c[PC_RECON01F] = mx ? n_recon(D, fl) : 0;
   c[PC_RECON2F] = (mx && !fl) ? n_recon(D, 0) : 0;
+  c[PC_TOFF] = fx ? (long long)NV * D.ntot : 0;
+  c[PC_RECON01X] = fx ? n_recon(D, fl) : 0;
+  c[PC_RECON2X] = (fx && !fl) ? n_recon(D, 0) : 0;
   c[PC_REPL] = fl ? n_replicate(D) : 0;
   c[PC_FIX] = n_fix(D);
   c[PC_EDGE] = n_edge(D);
   c[PC_ZONE] = n_zone(D);
 }
 
-long long plan_bytes(const Dims &D, int flat3, int mixed) {
+long long plan_bytes(const Dims &D, int flat3, int prec) {
   long long c[PC_N], ints = 0;
-  plan_counts(D, flat3, mixed, c);
+  plan_counts(D, flat3, prec, c);
   for (int q = 0; q < PC_N; q++) ints += 2 * nblk(c[q], 64);
   return (long long)sizeof(StageItem) + 4 * ints;
 }
@@ -249,7 +283,7 @@ int plan_build(Plan &p, const StageItem *items, int n) {
   long long zones = 0, cap = 0;
   for (int g = 0; g < n; g++) {
     long long c[PC_N];
-    plan_counts(items[g].A.D, items[g].A.flat3, items[g].mixed, c);
+    plan_counts(items[g].A.D, items[g].A.flat3, items[g].prec, c);
     for (int q = 0; q < PC_N; q++) {
       p.count[(size_t)q * n + g] = c[q];
       cap += 2 * nblk(c[q], 64);  // the smallest block the tuner tries
@@ -332,6 +366,14 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   nl += launch(p, PC_FACE1F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<1><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_RECON2F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<2><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_FACE2F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<2><<<nb, bs, 0, st>>>(V); });
+  // float-float grids
+  nl += launch(p, PC_TOFF, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_ff<<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON01X, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<0><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE0X, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<0><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_RECON01X, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<1><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE1X, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<1><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_RECON2X, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<2><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE2X, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<2><<<nb, bs, 0, st>>>(V); });
   // flat-X3 grids
   nl += launch(p, PC_REPL, GRMHD_K_OTHER, h,
                [&](unsigned nb, unsigned bs, BView V) { kp_replicate<<<nb, bs, 0, st>>>(V); });
@@ -421,9 +463,10 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     int cls;
     int which;  // what one pass launches
   };
-  const Group groups[] = {{PC_RECON01, 0}, {PC_RECON2, 1},   {PC_FACE0, 2},    {PC_FACE1, 3},
-                          {PC_FACE2, 4},   {PC_ZONE, 5},     {PC_RECON01F, 6}, {PC_RECON2F, 7},
-                          {PC_FACE0F, 8},  {PC_FACE1F, 9},   {PC_FACE2F, 10}};
+  const Group groups[] = {{PC_RECON01, 0},  {PC_RECON2, 1},   {PC_FACE0, 2},    {PC_FACE1, 3},
+                          {PC_FACE2, 4},    {PC_ZONE, 5},     {PC_RECON01F, 6}, {PC_RECON2F, 7},
+                          {PC_FACE0F, 8},   {PC_FACE1F, 9},   {PC_FACE2F, 10},  {PC_RECON01X, 11},
+                          {PC_RECON2X, 12}, {PC_FACE0X, 13},  {PC_FACE1X, 14},  {PC_FACE2X, 15}};
   auto pass = [&](int which) {
     auto L = [&](int cls, auto &&body) { launch(p, cls, 0, nullptr, body); };
     switch (which) {
@@ -462,6 +505,22 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
         break;
       case 10:
         L(PC_FACE2F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<2><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 11:
+        L(PC_RECON01X, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<0><<<nb, bs, 0, st>>>(V); });
+        L(PC_RECON01X, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<1><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 12:
+        L(PC_RECON2X, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<2><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 13:
+        L(PC_FACE0X, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<0><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 14:
+        L(PC_FACE1X, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<1><<<nb, bs, 0, st>>>(V); });
+        break;
+      case 15:
+        L(PC_FACE2X, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<2><<<nb, bs, 0, st>>>(V); });
         break;
     }
   };

@@ -23,7 +23,9 @@ struct StageItem {
   int *pflag, *fflag;
   float *Pf;           // mixed precision: FP32 primitives (8 x ntot)
   const float *geomf;  // mixed precision: FP32 geometry
-  int mixed;           // 1: FP32 flux stage
+  float *Pff;          // float-float: split primitives ([2][8][ntot])
+  const float *geomff; // float-float: split geometry ([2][NLOC][G_NCOMP][n2d])
+  int prec;            // GRMHD_PREC_*: the flux stage's arithmetic
 };
 
 // launch classes, each with its own block table
@@ -42,6 +44,12 @@ enum {
   PC_FACE0F,
   PC_FACE1F,
   PC_FACE2F,
+  PC_TOFF,  // float-float: split copy of the stage input
+  PC_RECON01X,
+  PC_RECON2X,
+  PC_FACE0X,
+  PC_FACE1X,
+  PC_FACE2X,
   PC_REPL,  // flat-X3 flux copies
   PC_FIX,
   PC_EDGE,  // EMFs and CT
@@ -82,10 +90,10 @@ struct PlanHook {
 // GRMHD_OK, GRMHD_ERR_INVALID (more than 2^31 - 1 blocks in a launch),
 // GRMHD_ERR_NOMEM or GRMHD_ERR_CUDA.
 int plan_build(Plan &p, const StageItem *items, int n);
-// threads per launch class of one grid (dimensions, flat X3, mixed precision)
-void plan_counts(const Dims &D, int flat3, int mixed, long long c[PC_N]);
+// threads per launch class of one grid (dimensions, flat X3, GRMHD_PREC_*)
+void plan_counts(const Dims &D, int flat3, int prec, long long c[PC_N]);
 // device bytes a one-grid plan of such a grid holds (item + block tables)
-long long plan_bytes(const Dims &D, int flat3, int mixed);
+long long plan_bytes(const Dims &D, int flat3, int prec);
 void plan_free(Plan &p);
 // Re-lay the block tables of class cls for bs threads per block and block
 // order sched (the results of every grid do not depend on either).
@@ -103,7 +111,7 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
 // The functions below enqueue on st and return the number of kernels
 // launched; launch errors are left for cudaGetLastError().
 // stage input: 0 = P, 1 = Ph.  Signal-speed reset, reconstruction + face
-// fluxes (FP64 or FP32 per grid), flat-X3 copies.
+// fluxes (FP64, FP32 or float-float per grid), flat-X3 copies.
 int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h);
 // per-grid clock: 0 reset the signal-speed maxima, 1 CFL time step, 2 advance
 int plan_clock(const Plan &p, int op, cudaStream_t st, PlanHook *h);

@@ -17,7 +17,8 @@ struct grmhd_sim {
   cudaStream_t st;
   double *P, *Ph, *F[3], *emf, *Lf, *Rf, *Uc;
   double *geom, *conn, *floors;
-  float *Pf, *geomf;  // FP32 copies (mixed precision only)
+  float *Pf, *geomf;    // FP32 copies (mixed precision only)
+  float *Pff, *geomff;  // split float-float copies (float-float mode only)
   int *pflag, *fflag;
   grmhd::Clock *clk;
   unsigned long long unrec_seen, dterr_seen;
