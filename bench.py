@@ -248,8 +248,9 @@ def _timed(stream, fn):
 PREC_DTYPE = {
     1: "mixed: FP32 reconstruction, fluid states, signal speeds, LLF fluxes; "
        "FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
-    2: "float-float: reconstruction, fluid states, signal speeds, LLF fluxes in pairs of FP32 "
-       "words (~48 significant bits); FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
+    2: "float-float: reconstruction, fluid states, signal speeds, LLF fluxes, U(P), geometric "
+       "source and 1D_W inversion in pairs of FP32 words (~48 significant bits); FP64 state, "
+       "geometry, flux divergence, flux-CT, bounds",
 }
 
 
@@ -449,6 +450,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="torus128", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff"],
+                    help="arithmetic of the flux stage of the timed workload (fp64: the headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
@@ -482,6 +485,7 @@ def main():
             dist.barrier()
 
     pr = make_problem(args.config)
+    pr.precision = {"fp64": 0, "mixed": 1, "ff": 2}[args.precision]
     zones = pr.n[0] * pr.n[1] * pr.n[2]
     stream = torch.cuda.current_stream()
     sim = grmhd.Sim(pr, stream=stream)
@@ -561,7 +565,7 @@ def main():
     launches = sum(v[1] for v in prof.values())
     roofline = None
     kernels = {}
-    if cpu is not None:
+    if cpu is not None and pr.precision == 0:  # the FP64 kernels' algorithmic count
         faces = faces_per_launch(pr.n)
         hbm = 6791e9
         try:
@@ -617,7 +621,8 @@ def main():
                                           "launch, profiles/%s_fm_torus_128.md" % kd["kernel"].split()[0]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if pr.precision == 0 else PREC_DTYPE[pr.precision],
             "data": "synthetic", "config": workload_config(args.config),
             "e2e": None if e2e_s is None else {
                 "value": job_value(zones, args.steps, world, e2e_s), "unit": UNIT,

@@ -62,8 +62,10 @@ extern "C" {
 #define GRMHD_PREC_FP64 0  /* every step in FP64 */
 #define GRMHD_PREC_MIXED 1 /* reconstruction, fluid states, signal speeds and LLF fluxes
                               in FP32; geometry, flux-CT, update, inversion, bounds FP64 */
-#define GRMHD_PREC_FF 2    /* the same split with the flux stage in float-float arithmetic
-                              (pairs of FP32 words, ~48 significant bits) on the FP32 pipe */
+#define GRMHD_PREC_FF 2    /* float-float: reconstruction, fluxes, U(P), geometric source
+                              and the 1D_W inversion in pairs of FP32 words (~48
+                              significant bits) on the FP32 pipe, in per-zone scaled
+                              units; flux divergence, flux-CT, bounds and the state FP64 */
 
 typedef struct grmhd_sim grmhd_sim; /* opaque, library-owned */
 

@@ -87,6 +87,7 @@ static void free_all(grmhd_sim *s) {
   if (s->geomf) cudaFree(s->geomf);
   if (s->Pff) cudaFree(s->Pff);
   if (s->geomff) cudaFree(s->geomff);
+  if (s->connff) cudaFree(s->connff);
   if (s->pflag) cudaFree(s->pflag);
   if (s->fflag) cudaFree(s->fflag);
   if (s->clk) cudaFree(s->clk);
@@ -151,7 +152,7 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
   if (params->precision == GRMHD_PREC_MIXED)
     b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
   if (params->precision == GRMHD_PREC_FF)
-    b += 2 * sizeof(float) * NV * tot + 2 * sizeof(float) * NLOC * G_NCOMP * n2d;
+    b += 2 * sizeof(float) * (NV * tot + (NLOC * G_NCOMP + C_NCOMP) * n2d);
   b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision);
   *bytes = b;
   return GRMHD_OK;
@@ -210,7 +211,8 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
          cudaMalloc(&s->geomf, sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess;
   if (ok && params->precision == GRMHD_PREC_FF)
     ok = cudaMalloc(&s->Pff, 2 * sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
-         cudaMalloc(&s->geomff, 2 * sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess;
+         cudaMalloc(&s->geomff, 2 * sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
+         cudaMalloc(&s->connff, 2 * sizeof(float) * C_NCOMP * (size_t)D.n2d) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -249,6 +251,7 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
     launch_geometry(G, st);
     if (s->geomf) launch_to_f32((long long)NLOC * G_NCOMP * D.n2d, s->geom, s->geomf, st);
     if (s->geomff) launch_to_ff((long long)NLOC * G_NCOMP * D.n2d, s->geom, s->geomff, st);
+    if (s->connff) launch_to_ff((long long)C_NCOMP * D.n2d, s->conn, s->connff, st);
     rc = launched();
   }
   if (rc == GRMHD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
@@ -271,6 +274,9 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
   A.flat3 = flat3_of(D, params);
+  set_ff_constants(A);
+  A.geomff = s->geomff;
+  A.connff = s->connff;
   A.geom = s->geom;
   A.conn = s->conn;
   A.floors = s->floors;
@@ -528,6 +534,8 @@ extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
           memcpy(c.data() + (l * 10 + SY(m, n)) * n2d, in + ((l * 4 + m) * 4 + n) * n2d,
                  sizeof(double) * (size_t)n2d);
     CK(cudaMemcpyAsync(s->conn, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, s->st));
+    if (s->connff) launch_to_ff((long long)C_NCOMP * n2d, s->conn, s->connff, s->st);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->st));
     return GRMHD_OK;
   }

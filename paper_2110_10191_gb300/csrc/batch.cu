@@ -146,7 +146,7 @@ extern "C" int grmhd_batch_set_launch(grmhd_batch *b, int kclass, int threads, i
   static const int recon[] = {PC_RECON01, PC_RECON2, PC_RECON01F, PC_RECON2F, PC_RECON01X, PC_RECON2X};
   static const int flux[] = {PC_FACE0, PC_FACE1, PC_FACE2, PC_FACE0F, PC_FACE1F,
                              PC_FACE2F, PC_FACE0X, PC_FACE1X, PC_FACE2X};
-  static const int zone[] = {PC_ZONE};
+  static const int zone[] = {PC_ZONE, PC_UPD64, PC_UPDX};
   const int *cls = nullptr;
   int ncls = 0;
   if (kclass == GRMHD_K_RECON) {
@@ -157,7 +157,7 @@ extern "C" int grmhd_batch_set_launch(grmhd_batch *b, int kclass, int threads, i
     ncls = 9;
   } else if (kclass == GRMHD_K_UPDATE) {
     cls = zone;
-    ncls = 1;
+    ncls = 3;
   } else {
     return GRMHD_ERR_INVALID;
   }

@@ -1,12 +1,13 @@
-// ff_bodies.cuh -- per-thread bodies of the flux stage of the float-float
-// mode (GRMHD_PREC_FF): the reconstruction, the fluid states, the signal
-// speeds and the local Lax-Friedrichs flux in float-float arithmetic
-// (ff.cuh, about 48 significant bits) on the FP32 pipe; the fluxes are
-// stored in FP64, and the flux-CT, the update, the 1D_W inversion and the
-// bounds run in FP64 as in the FP64 mode.  Same formulas as the FP64 bodies
-// (grmhd_dev.cuh), with the energy flux formed without the rest-mass
+// ff_bodies.cuh -- per-thread bodies of the float-float mode
+// (GRMHD_PREC_FF): the reconstruction, the fluid states, the signal speeds,
+// the local Lax-Friedrichs flux, U(P), the geometric source and the 1D_W
+// inversion in float-float arithmetic (ff.cuh, about 48 significant bits) on
+// the FP32 pipe; the state, the fluxes, the flux divergence, the flux-CT and
+// the bounds stay FP64.  Same formulas as the FP64 bodies (grmhd_dev.cuh),
+// with the energy flux and energy density formed without the rest-mass
 // cancellation as in the FP32 bodies (grmhd_f32.cuh), since the 5 bits the
-// float pair lacks would otherwise be lost 1e3-fold at rho >> u.
+// float pair lacks would otherwise be lost 1e3-fold at rho >> u, and with
+// every zone or face computed in units scaled by its density (FFScale).
 //
 // Data: the stage input split once per stage into high and low float words
 // ([2][8][ntot]: all high words, then all low words), the face values in the
@@ -29,6 +30,42 @@ __device__ __forceinline__ ff ff_load(const float *__restrict__ hi, long long lo
 __device__ __forceinline__ void ff_store(float *hi, long long lo_off, long long i, ff v) {
   hi[i] = v.hi;
   hi[lo_off + i] = v.lo;
+}
+
+// Per-zone (per-face) scale.  Ideal MHD is invariant under rho, u, p, b^2 ->
+// s (rho, u, p, b^2) with B -> sqrt(s) B and the velocities unchanged, so the
+// float-float bodies work in units where the density is about 1: s = 4^m
+// (an exact power of two whose square root 2^m is exact too) from the
+// density; the hydrodynamic densities, fluxes and sources scale by s, the
+// field and its fluxes by 2^m.  Without it the float exponent range
+// (1e-38..3e38) cuts into floor-density atmospheres, where products such as
+// (Q.B)^2 fall below 1e-38.
+struct FFScale {
+  float is, irs;   // 1/s, 1/sqrt(s): into the scaled units
+  double s, rs;    // s, sqrt(s): back, applied in FP64
+};
+
+__device__ __forceinline__ FFScale ff_scale_for(float rho) {
+  int m = 0;
+  if (rho > 0.0f) {
+    m = ilogbf(rho) >> 1;  // floor of half the binary exponent
+    m = max(-60, min(60, m));
+  }
+  FFScale c;
+  c.is = ldexpf(1.0f, -2 * m);
+  c.irs = ldexpf(1.0f, -m);
+  c.s = ldexp(1.0, 2 * m);
+  c.rs = ldexp(1.0, m);
+  return c;
+}
+
+// a primitive vector into the scaled units (exact)
+__device__ __forceinline__ void ff_scale_prims(ff P[NV], const FFScale &c) {
+  P[RHO] = ff_ldexp(P[RHO], c.is);
+  P[UU] = ff_ldexp(P[UU], c.is);
+  P[B1] = ff_ldexp(P[B1], c.irs);
+  P[B2] = ff_ldexp(P[B2], c.irs);
+  P[B3] = ff_ldexp(P[B3], c.irs);
 }
 
 // one value split into its two words ([2][n]); values beyond the float
@@ -139,7 +176,7 @@ __device__ __forceinline__ void recon_ff_body(const StepArgs &A, const float *__
 // Face fluxes
 // ---------------------------------------------------------------------------
 struct GeoFF {
-  ff gcov[10], gcon[10], gdet, alpha, ialpha, omalpha;
+  ff gcov[10], gcon[10], gdet, alpha, ialpha, omalpha, igdet;
 };
 
 // geometry of one location from the split copy ([2][NLOC][G_NCOMP][n2d];
@@ -154,6 +191,7 @@ __device__ __forceinline__ void load_geo_ff(const float *__restrict__ g, long lo
   G.alpha = ff_load(g, lo_off, G_ALPHA * n2d + ij);
   G.ialpha = ff_load(g, lo_off, G_IALPHA * n2d + ij);
   G.omalpha = ff_load(g, lo_off, G_OMALPHA * n2d + ij);
+  G.igdet = ff_load(g, lo_off, G_IGDET * n2d + ij);
 }
 
 // Fluid state as fluid_state (grmhd_dev.cuh), plus opu_t = 1 + u_t formed
@@ -289,8 +327,12 @@ __device__ __forceinline__ void face_ff_body(const StepArgs &A, const float *__r
     GeoFF G;
     load_geo_ff(geomff + (long long)loc * G_NCOMP * D.n2d, (long long)NLOC * G_NCOMP * D.n2d, D.n2d,
                 (long long)j * D.s[0] + i, G);
-    const ff gam = ff_from(A.gam), gm1 = ff_from(A.gam - 1.0), ggm1 = ff_from(A.gam * (A.gam - 1.0));
+    const ff gam = {A.gam_ff[0], A.gam_ff[1]}, gm1 = {A.gm1_ff[0], A.gm1_ff[1]};
+    const ff ggm1 = {A.ggm1_ff[0], A.ggm1_ff[1]};
     FStateFF sL, sR;
+    const FFScale sc = ff_scale_for(PL[RHO].hi);
+    ff_scale_prims(PL, sc);
+    ff_scale_prims(PR, sc);
     fluid_state_ff(PL, G, sL);
     fluid_state_ff(PR, G, sR);
     ff vmaxL, vminL, vmaxR, vminR;
@@ -307,7 +349,8 @@ __device__ __forceinline__ void face_ff_body(const StepArgs &A, const float *__r
     flux_cons_acc_ff(PR, sR, gm1, DIR + 1, ff_neg(ct), acc);
     const ff hg = ff_ldexp(G.gdet, 0.5f);
 #pragma unroll
-    for (int v = 0; v < NV; v++) F[v * D.ntot + c] = ff_to(ff_mul(hg, acc[v]));
+    for (int v = 0; v < NV; v++)
+      F[v * D.ntot + c] = ff_to(ff_mul(hg, acc[v])) * (v < B1 ? sc.s : sc.rs);
     bool interior = true;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
@@ -318,6 +361,291 @@ __device__ __forceinline__ void face_ff_body(const StepArgs &A, const float *__r
     if (interior) ctop = ff_to(ct);
   }
   warp_block_max(ctop, &A.clk->ctop_bits[DIR]);
+}
+
+// ---------------------------------------------------------------------------
+// Update: U(P), the geometric source and the 1D_W inversion in float-float
+// ---------------------------------------------------------------------------
+// sqrt(-g)-weighted conserved densities of a state (prim_flux with dir 0),
+// the energy density without the rest-mass cancellation:
+// T^t_t + rho u^t = rho u^t (1 + u_t) + (w - rho) u^t u_t - b^t b_t + p_t
+__device__ __forceinline__ void prim_cons_ff(const ff P[NV], const FStateFF &s, const GeoFF &G, ff gm1,
+                                             ff U[NV]) {
+  const ff pg = ff_mul(P[UU], gm1);
+  const ff w = ff_add(ff_add(P[RHO], P[UU]), ff_add(pg, s.bsq));
+  const ff pt = ff_add(pg, ff_ldexp(s.bsq, 0.5f));
+  const ff ut = s.ucon[0], bt = s.bcon[0];
+  const ff wu = ff_mul(w, ut);
+  const ff mf = ff_mul(P[RHO], ut);
+  U[RHO] = ff_mul(G.gdet, mf);
+  const ff en = ff_add(ff_add(ff_mul(mf, s.opu_t), ff_mul(ff_mul(ff_sub(w, P[RHO]), ut), s.ucov[0])),
+                       ff_sub(pt, ff_mul(bt, s.bcov[0])));
+  U[UU] = ff_mul(G.gdet, en);
+#pragma unroll
+  for (int i = 1; i < 4; i++) U[UU + i] = ff_mul(G.gdet, ff_sub(ff_mul(wu, s.ucov[i]), ff_mul(bt, s.bcov[i])));
+#pragma unroll
+  for (int i = 1; i < 4; i++)
+    U[B1 + i - 1] = ff_mul(G.gdet, ff_sub(ff_mul(s.bcon[i], ut), ff_mul(bt, s.ucon[i])));
+}
+
+// S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} (geo_source) from the split connection
+__device__ __forceinline__ void geo_source_ff(const ff P[NV], const FStateFF &s, const GeoFF &G,
+                                              const float *__restrict__ connff, long long lo_off,
+                                              long long n2d, long long ij, ff gm1, ff S[4]) {
+  const ff pg = ff_mul(P[UU], gm1);
+  const ff w = ff_add(ff_add(P[RHO], P[UU]), ff_add(pg, s.bsq));
+  const ff pt = ff_add(pg, ff_ldexp(s.bsq, 0.5f));
+  ff T[4][4];
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    const ff wu = ff_mul(w, s.ucon[m]);
+#pragma unroll
+    for (int n = 0; n < 4; n++) T[m][n] = ff_sub(ff_mul(wu, s.ucov[n]), ff_mul(s.bcon[m], s.bcov[n]));
+    T[m][m] = ff_add(T[m][m], pt);
+  }
+#pragma unroll
+  for (int nu = 0; nu < 4; nu++) {
+    ff acc = ff_f(0.0f);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int l = 0; l < 4; l++)
+        acc = ff_add(acc, ff_mul(T[k][l], ff_load(connff, lo_off, (l * 10 + SY(nu, k)) * n2d + ij)));
+    S[nu] = ff_mul(acc, G.gdet);
+  }
+}
+
+// 1D_W inversion (invert_1dw) in float-float: the same iteration rule, the
+// same cancellation-free Q'.n and spatial inverse metric; the decisions are
+// taken on float-float values against the same constants (split into float
+// words: 1 - 1e-10 = 0x3f800000 + 0xaedbe700, 1e-8 = 0x322bcc77 + 0x248c230e).
+__device__ __forceinline__ int invert_1dw_ff(const ff U[NV], const GeoFF &G, ff gam, ff igam, ff gf,
+                                             const ff Pg[NV], ff P[NV], ff &bsq_out, ff &lorentz_out) {
+  const ff vsq_max = {__int_as_float(0x3f800000), __int_as_float((int)0xaedbe700u)};
+  const ff tol = {__int_as_float(0x322bcc77), __int_as_float(0x248c230e)};
+  const ff z = ff_f(0.0f);
+#pragma unroll
+  for (int v = 0; v < NV; v++) P[v] = Pg[v];
+  const ff igd = G.igdet, al = G.alpha;
+  P[B1] = ff_mul(U[B1], igd);
+  P[B2] = ff_mul(U[B2], igd);
+  P[B3] = ff_mul(U[B3], igd);
+  const ff aig = ff_mul(al, igd);
+  const ff D = ff_mul(U[RHO], aig);
+  if (!(D.hi > 0.0f)) return PF_D;
+  const ff n1 = ff_mul(al, P[B1]), n2 = ff_mul(al, P[B2]), n3 = ff_mul(al, P[B3]);
+  const ff Q1 = ff_mul(aig, U[U1]), Q2 = ff_mul(aig, U[U2]), Q3 = ff_mul(aig, U[U3]);
+  const ff c1 = G.gcon[SY(0, 1)], c2 = G.gcon[SY(0, 2)], c3 = G.gcon[SY(0, 3)];
+  const ff Qpn = ff_sub(ff_mul(ff_sub(U[UU], ff_mul(G.omalpha, U[RHO])), igd),
+                        ff_mul(al, dot3(Q1, c1, Q2, c2, Q3, c3)));
+  const ff mig00 = ff_sqr(al);  // -1/g^tt
+  const ff h11 = ff_add(G.gcon[SY(1, 1)], ff_mul(ff_sqr(c1), mig00));
+  const ff h12 = ff_add(G.gcon[SY(1, 2)], ff_mul(ff_mul(c1, c2), mig00));
+  const ff h13 = ff_add(G.gcon[SY(1, 3)], ff_mul(ff_mul(c1, c3), mig00));
+  const ff h22 = ff_add(G.gcon[SY(2, 2)], ff_mul(ff_sqr(c2), mig00));
+  const ff h23 = ff_add(G.gcon[SY(2, 3)], ff_mul(ff_mul(c2, c3), mig00));
+  const ff h33 = ff_add(G.gcon[SY(3, 3)], ff_mul(ff_sqr(c3), mig00));
+  const ff Qt1 = dot3(h11, Q1, h12, Q2, h13, Q3);
+  const ff Qt2 = dot3(h12, Q1, h22, Q2, h23, Q3);
+  const ff Qt3 = dot3(h13, Q1, h23, Q2, h33, Q3);
+  const ff Qtsq = dot3(Qt1, Q1, Qt2, Q2, Qt3, Q3);
+  const ff QdB = dot3(Q1, n1, Q2, n2, Q3, n3);
+  const ff Bsq = dot3(n1, dot3(G.gcov[SY(1, 1)], n1, G.gcov[SY(1, 2)], n2, G.gcov[SY(1, 3)], n3), n2,
+                      dot3(G.gcov[SY(1, 2)], n1, G.gcov[SY(2, 2)], n2, G.gcov[SY(2, 3)], n3), n3,
+                      dot3(G.gcov[SY(1, 3)], n1, G.gcov[SY(2, 3)], n2, G.gcov[SY(3, 3)], n3));
+  // guess
+  const ff g1 = Pg[U1], g2 = Pg[U2], g3 = Pg[U3];
+  const ff qsq = dot3(g1, dot3(G.gcov[SY(1, 1)], g1, G.gcov[SY(1, 2)], g2, G.gcov[SY(1, 3)], g3), g2,
+                      dot3(G.gcov[SY(1, 2)], g1, G.gcov[SY(2, 2)], g2, G.gcov[SY(2, 3)], g3), g3,
+                      dot3(G.gcov[SY(1, 3)], g1, G.gcov[SY(2, 3)], g2, G.gcov[SY(3, 3)], g3));
+  ff Wp = ff_sub(ff_mul(ff_add(Pg[RHO], ff_mul(gam, Pg[UU])), ff_add_f(qsq, 1.0f)), D);
+  if (Wp.hi < 0.0f) Wp = z;
+  int converged = 0, extra = 0, invalid = 0, have_hi = 0;
+  ff lo = z, hi = z;
+  for (int it = 0; it < INV_MAXIT + INV_EXTRA; it++) {
+    const ff W = ff_add(Wp, D);
+    const ff W2 = ff_sqr(W);
+    const ff BW = ff_add(Bsq, W);
+    const ff ix = ff_rcp(ff_mul(BW, W));  // 1/W = BW ix, 1/(B^2+W) = W ix
+    const ff a = ff_mul(W, ix);           // 1/(B^2 + W)
+    const ff qx = ff_mul(QdB, ix);        // Q.B / (W (B^2 + W))
+    // v^2 = Qt^2/(B^2+W)^2 + (Q.B)^2 (B^2 + 2W)/(W^2 (B^2+W)^2), each factor in range
+    ff vsq = ff_add(ff_mul(Qtsq, ff_sqr(a)), ff_mul(ff_mul(qx, ff_add(Bsq, ff_ldexp(W, 2.0f))), qx));
+    invalid = 0;
+    if (ff_gt(vsq, vsq_max)) {
+      lo = ff_max(lo, Wp);
+      Wp = have_hi ? ff_ldexp(ff_add(lo, hi), 0.5f) : ff_add(Wp, W);
+      invalid = 1;
+      if (converged || it + 1 >= INV_MAXIT) break;
+      continue;
+    }
+    if (vsq.hi < 0.0f) vsq = z;
+    const ff omv = ff_add_f(ff_neg(vsq), 1.0f);
+    const ff rsq = ff_rsqrt(omv);  // 1/sqrt(1 - v^2)
+    const ff sq = ff_mul(omv, rsq);
+    const ff wmr = ff_sub(ff_mul(Wp, omv), ff_mul(ff_mul(ff_mul(D, vsq), sq), ff_rcp(ff_add_f(sq, 1.0f))));
+    const ff iW = ff_mul(BW, ix);
+    const ff qw0 = ff_mul(QdB, iW);
+    const ff f = ff_sub(ff_add(ff_add(Qpn, Wp), ff_mul(ff_ldexp(ff_add_f(vsq, 1.0f), 0.5f), Bsq)),
+                        ff_add(ff_mul(gf, wmr), ff_ldexp(ff_sqr(qw0), 0.5f)));
+    if (f.hi > 0.0f) {
+      hi = have_hi ? ff_min(hi, Wp) : Wp;
+      have_hi = 1;
+    } else {
+      lo = ff_max(lo, Wp);
+    }
+    const ff poly = ff_add(ff_mul_f(ff_add(W2, ff_mul(W, Bsq)), 3.0f), ff_sqr(Bsq));
+    // dv^2/dW = -2 (Qt^2 W^3 + (Q.B)^2 poly) / (W (B^2+W))^3, as
+    // -2 [Qt^2 a^3 + qx^2 (poly ix)]
+    const ff dv = ff_mul_f(ff_add(ff_mul(ff_mul(Qtsq, a), ff_sqr(a)),
+                                  ff_mul(ff_sqr(qx), ff_mul(poly, ix))), -2.0f);
+    const ff dpdW = ff_mul(gf, ff_add(omv, ff_mul(dv, ff_sub(ff_mul(ff_ldexp(D, 0.5f), rsq), W))));
+    const ff qw = ff_mul(QdB, iW);  // Q.B / W
+    const ff df = ff_add(ff_add(ff_add_f(ff_neg(dpdW), 1.0f), ff_mul(ff_ldexp(Bsq, 0.5f), dv)),
+                         ff_mul(ff_sqr(qw), iW));
+    ff Wn = ff_sub(Wp, ff_div(f, df));
+    if (Wn.hi < 0.0f) Wn = ff_ldexp(Wp, 0.5f);
+    if (converged) {
+      Wp = Wn;
+      if (++extra >= INV_EXTRA) break;
+      continue;
+    }
+    if (!ff_gt(ff_abs(ff_sub(Wn, Wp)), ff_mul(tol, ff_abs(W)))) converged = 1;
+    Wp = Wn;
+    if (!converged && it + 1 >= INV_MAXIT) break;
+  }
+  const ff W = ff_add(Wp, D);
+  if (!converged) return PF_NOCONV;
+  if (!(W.hi > 0.0f) || !isfinite(W.hi)) return PF_W;
+  const ff BW = ff_add(Bsq, W);
+  const ff ix = ff_rcp(ff_mul(BW, W));
+  const ff a = ff_mul(W, ix), qx = ff_mul(QdB, ix);
+  ff vsq = ff_add(ff_mul(Qtsq, ff_sqr(a)), ff_mul(ff_mul(qx, ff_add(Bsq, ff_ldexp(W, 2.0f))), qx));
+  if (!(vsq.hi < 1.0f || (vsq.hi == 1.0f && vsq.lo < 0.0f)) || invalid) return PF_VSQ;
+  if (vsq.hi < 0.0f) vsq = z;
+  const ff omv = ff_add_f(ff_neg(vsq), 1.0f);
+  const ff rsq = ff_rsqrt(omv);  // Lorentz factor
+  const ff sq = ff_mul(omv, rsq);
+  const ff rho = ff_mul(D, sq);
+  const ff uu = ff_mul(ff_sub(ff_mul(Wp, omv), ff_mul(ff_mul(ff_mul(D, vsq), sq), ff_rcp(ff_add_f(sq, 1.0f)))),
+                       igam);
+  if (!(rho.hi > 0.0f)) return PF_RHO;
+  if (uu.hi < 0.0f) return PF_U;
+  const ff fac = ff_mul(rsq, ff_mul(W, ix));  // gamma / (W + B^2)
+  const ff qbw = ff_mul(QdB, ff_mul(BW, ix));  // Q.B / W
+  bsq_out = ff_add(ff_mul(Bsq, omv), ff_sqr(qbw));
+  lorentz_out = rsq;
+  P[RHO] = rho;
+  P[UU] = uu;
+  P[U1] = ff_mul(fac, ff_add(Qt1, ff_mul(qbw, n1)));
+  P[U2] = ff_mul(fac, ff_add(Qt2, ff_mul(qbw, n2)));
+  P[U3] = ff_mul(fac, ff_add(Qt3, ff_mul(qbw, n3)));
+  return PF_OK;
+}
+
+// One thread per interior zone (update_body): U(P^n) (or its cache), the
+// source of P_s, the inversion in float-float; the flux divergence, the
+// conserved sum, the bounds and all stored arrays in FP64.  Every thread
+// of the block must call it (warp counters).
+__device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *Pi,
+                                               const double *__restrict__ Ps, double *Pout,
+                                               const double *__restrict__ F1,
+                                               const double *__restrict__ F2,
+                                               const double *__restrict__ F3, int *pflag, int *fflag,
+                                               double dtfac, double *Ucache, int ucache_mode,
+                                               long long t) {
+  const Dims &D = A.D;
+  const double dt = A.clk->dt;
+  if (!(dt > 0.0)) return;  // uniform across the grid
+  const double dtp = dtfac * dt;
+  const long long nz = n_zone(D);
+  const bool active = t < nz;
+  int pf = 0, fl = 0;
+  if (active) {
+    const int i = NG + (int)(t % D.n[0]);
+    const int j = NG + (int)((t / D.n[0]) % D.n[1]);
+    const int k = NG + (int)(t / ((long long)D.n[0] * D.n[1]));
+    const long long c = zid(D, i, j, k), N = D.ntot;
+    const long long ij = (long long)j * D.s[0] + i;
+    GeoFF G;
+    load_geo_ff(A.geomff, (long long)NLOC * G_NCOMP * D.n2d, D.n2d, ij, G);
+    const ff gam = {A.gam_ff[0], A.gam_ff[1]}, gm1 = {A.gm1_ff[0], A.gm1_ff[1]};
+    const ff igam = {A.igam_ff[0], A.igam_ff[1]}, gf = {A.gf_ff[0], A.gf_ff[1]};
+    const long long clo = (long long)C_NCOMP * D.n2d;
+    ff pi[NV], Ui[NV], S[4];
+#pragma unroll
+    for (int v = 0; v < NV; v++) pi[v] = ff_from(Pi[v * N + c]);
+    // scaled units from P^n's density (the same in both stages, so that
+    // U(P^n) kept by the predictor is read back in the corrector's units)
+    const FFScale sc = ff_scale_for(pi[RHO].hi);
+    ff_scale_prims(pi, sc);
+    if (Ps == Pi) {
+      FStateFF si;
+      fluid_state_ff(pi, G, si);
+      prim_cons_ff(pi, si, G, gm1, Ui);
+      if (ucache_mode == 1) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) Ucache[v * N + c] = ff_to(Ui[v]) * (v < B1 ? sc.s : sc.rs);
+      }
+      geo_source_ff(pi, si, G, A.connff, clo, D.n2d, ij, gm1, S);
+    } else {
+      if (ucache_mode == 2) {
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+          Ui[v] = ff_from(Ucache[v * N + c] * (double)(v < B1 ? sc.is : sc.irs));
+      } else {
+        FStateFF si;
+        fluid_state_ff(pi, G, si);
+        prim_cons_ff(pi, si, G, gm1, Ui);
+      }
+      ff ps[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) ps[v] = ff_from(Ps[v * N + c]);
+      ff_scale_prims(ps, sc);
+      FStateFF ss;
+      fluid_state_ff(ps, G, ss);
+      geo_source_ff(ps, ss, G, A.connff, clo, D.n2d, ij, gm1, S);
+    }
+    const double idx1 = A.idx[0], idx2 = A.idx[1], idx3 = A.idx[2];
+    const ff dtpf = ff_from(dtp);
+    ff Un[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const long long o = v * N + c;
+      const double div = (F1[o + 1] - F1[o]) * idx1 + (F2[o + D.s[0]] - F2[o]) * idx2 +
+                         (F3[o + D.n2d] - F3[o]) * idx3;
+      ff rhs = ff_neg(ff_from(div * (double)(v < B1 ? sc.is : sc.irs)));
+      if (v >= UU && v <= U3) rhs = ff_add(rhs, S[v - UU]);
+      Un[v] = ff_add(Ui[v], ff_mul(dtpf, rhs));
+    }
+    ff pn[NV], bsq_n = ff_f(0.0f), lor_n = ff_f(1.0f);
+    pf = invert_1dw_ff(Un, G, gam, igam, gf, pi, pn, bsq_n, lor_n);
+    double pd[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      pd[v] = ff_to(pn[v]);
+      if (v == RHO || v == UU) pd[v] *= sc.s;
+      if (v >= B1) pd[v] *= sc.rs;
+    }
+    if (pf == PF_OK && A.floors_on) {
+      const double rho_fl = __ldg(A.floors + ij), u_fl = __ldg(A.floors + D.n2d + ij);
+      const double lor = ff_to(lor_n);
+      if (lor > FL_GAMMA) {  // the Lorentz-factor cap needs the FP64 fluid state
+        Geo Gd;
+        load_geo(A.geom, D.n2d, ij, Gd);
+        fl = apply_floors(pd, Gd, rho_fl, u_fl, A.gam);
+      } else {
+        Geo Gd;  // not read on this path
+        fl = apply_floors_known(pd, Gd, rho_fl, u_fl, A.gam, ff_to(bsq_n) * sc.s, lor);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) Pout[v * N + c] = pd[v];
+    pflag[c] = pf;
+    fflag[c] = fl;
+  }
+  count_warp(active && pf != 0, &A.clk->counters[0]);
+  count_warp(active && fl != 0, &A.clk->counters[1]);
 }
 
 }  // namespace grmhd

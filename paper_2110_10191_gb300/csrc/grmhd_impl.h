@@ -34,12 +34,26 @@ struct StepArgs {
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   int flat3;  // n3 = 1 with periodic X3: fluxes on the single k layer, copied
+  // gamma, gamma - 1 and gamma (gamma - 1) split into float words (high, low)
+  // for the float-float flux stage
+  float gam_ff[2], gm1_ff[2], ggm1_ff[2], igam_ff[2], gf_ff[2];  // gf = (gamma - 1)/gamma
+  const float *geomff, *connff;  // float-float mode: split geometry and connection
   int bc[3][2];
   const double *geom;
   const double *conn;
   const double *floors;
   Clock *clk;
 };
+
+// the float-float words of the adiabatic-index constants
+inline void set_ff_constants(StepArgs &A) {
+  const double v[5] = {A.gam, A.gam - 1.0, A.gam * (A.gam - 1.0), A.igam, (A.gam - 1.0) / A.gam};
+  float *o[5] = {A.gam_ff, A.gm1_ff, A.ggm1_ff, A.igam_ff, A.gf_ff};
+  for (int q = 0; q < 5; q++) {
+    o[q][0] = (float)v[q];
+    o[q][1] = (float)(v[q] - (double)o[q][0]);
+  }
+}
 
 void launch_geometry(const GeomArgs &A, cudaStream_t st);
 

@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(BS_MAX) kp_recon_ff(BView V) {
     recon_ff_body<DIR, 0>(it.A, it.Pff, Lf, Rf, t);
 }
 
+// at most 128 registers: 4 blocks of 128 threads per SM (a few bytes spill)
 template <int DIR>
-__global__ void __launch_bounds__(BS_MAX) kp_face_ff(BView V) {
+__global__ void __maxnreg__(128) kp_face_ff(BView V) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
@@ -149,6 +150,15 @@ __global__ void __maxnreg__(168) kp_update(BView V, int in, double dtfac, int uc
   const StageItem &it = V.items[g];
   update_body(it.A, it.P, arr(it, in), arr(it, 1 - in), it.F[0], it.F[1], it.F[2], it.pflag,
               it.fflag, dtfac, it.Uc, ucache_mode, block_tid(V, g));
+}
+
+// at most 128 registers: 4 blocks of 128 threads per SM; the spill it costs
+// is cheaper than the occupancy it buys for this latency-bound FP32 code
+__global__ void __maxnreg__(128) kp_update_ff(BView V, int in, double dtfac, int ucache_mode) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  update_ff_body(it.A, it.P, arr(it, in), arr(it, 1 - in), it.F[0], it.F[1], it.F[2], it.pflag,
+                 it.fflag, dtfac, it.Uc, ucache_mode, block_tid(V, g));
 }
 
 __global__ void kp_fixup(BView V, int out) {
@@ -260,6 +270,8 @@ void plan_counts(const Dims &D, int flat3, int prec, long long c[PC_N]) {
   c[PC_FIX] = n_fix(D);
   c[PC_EDGE] = n_edge(D);
   c[PC_ZONE] = n_zone(D);
+  c[PC_UPD64] = fx ? 0 : n_zone(D);
+  c[PC_UPDX] = fx ? n_zone(D) : 0;
 }
 
 long long plan_bytes(const Dims &D, int flat3, int prec) {
@@ -389,8 +401,11 @@ int plan_fix_ct(const Plan &p, cudaStream_t st, PlanHook *h) {
 }
 
 int plan_update(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st, PlanHook *h) {
-  int nl = launch(p, PC_ZONE, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
+  int nl = launch(p, PC_UPD64, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
     kp_update<<<nb, bs, 0, st>>>(V, in, dtfac, ucache_mode);
+  });
+  nl += launch(p, PC_UPDX, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
+    kp_update_ff<<<nb, bs, 0, st>>>(V, in, dtfac, ucache_mode);
   });
   nl += launch(p, PC_ZONE, GRMHD_K_FIXUP, h,
                [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, 1 - in); });
@@ -463,10 +478,11 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     int cls;
     int which;  // what one pass launches
   };
-  const Group groups[] = {{PC_RECON01, 0},  {PC_RECON2, 1},   {PC_FACE0, 2},    {PC_FACE1, 3},
-                          {PC_FACE2, 4},    {PC_ZONE, 5},     {PC_RECON01F, 6}, {PC_RECON2F, 7},
-                          {PC_FACE0F, 8},   {PC_FACE1F, 9},   {PC_FACE2F, 10},  {PC_RECON01X, 11},
-                          {PC_RECON2X, 12}, {PC_FACE0X, 13},  {PC_FACE1X, 14},  {PC_FACE2X, 15}};
+  const Group groups[] = {{PC_RECON01, 0},  {PC_RECON2, 1},  {PC_FACE0, 2},    {PC_FACE1, 3},
+                          {PC_FACE2, 4},    {PC_UPD64, 5},   {PC_RECON01F, 6}, {PC_RECON2F, 7},
+                          {PC_FACE0F, 8},   {PC_FACE1F, 9},  {PC_FACE2F, 10},  {PC_RECON01X, 11},
+                          {PC_RECON2X, 12}, {PC_FACE0X, 13}, {PC_FACE1X, 14},  {PC_FACE2X, 15},
+                          {PC_UPDX, 16}};
   auto pass = [&](int which) {
     auto L = [&](int cls, auto &&body) { launch(p, cls, 0, nullptr, body); };
     switch (which) {
@@ -486,9 +502,11 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
       case 4:
         L(PC_FACE2, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, 0); });
         break;
-      case 5:  // predictor-like update without keeping U(P^n), then the fixup
-        L(PC_ZONE, [&](unsigned nb, unsigned bs, BView V) { kp_update<<<nb, bs, 0, st>>>(V, 0, 0.5, 0); });
-        L(PC_ZONE, [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, 1); });
+      case 5:  // predictor-like update without keeping U(P^n)
+        L(PC_UPD64, [&](unsigned nb, unsigned bs, BView V) { kp_update<<<nb, bs, 0, st>>>(V, 0, 0.5, 0); });
+        break;
+      case 16:
+        L(PC_UPDX, [&](unsigned nb, unsigned bs, BView V) { kp_update_ff<<<nb, bs, 0, st>>>(V, 0, 0.5, 0); });
         break;
       case 6:
         L(PC_RECON01F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });

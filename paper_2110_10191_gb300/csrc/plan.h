@@ -52,8 +52,10 @@ enum {
   PC_FACE2X,
   PC_REPL,  // flat-X3 flux copies
   PC_FIX,
-  PC_EDGE,  // EMFs and CT
-  PC_ZONE,  // update and fixup
+  PC_EDGE,   // EMFs and CT
+  PC_ZONE,   // fixup (every grid)
+  PC_UPD64,  // FP64 update (FP64 and mixed-precision grids)
+  PC_UPDX,   // float-float update (float-float grids)
   PC_N
 };
 

@@ -18,7 +18,7 @@ struct grmhd_sim {
   double *P, *Ph, *F[3], *emf, *Lf, *Rf, *Uc;
   double *geom, *conn, *floors;
   float *Pf, *geomf;    // FP32 copies (mixed precision only)
-  float *Pff, *geomff;  // split float-float copies (float-float mode only)
+  float *Pff, *geomff, *connff;  // split float-float copies (float-float mode only)
   int *pflag, *fflag;
   grmhd::Clock *clk;
   unsigned long long unrec_seen, dterr_seen;
