@@ -201,6 +201,15 @@ int grmhd_profile(grmhd_sim *sim, int enable);
  * the last reset; reset != 0 clears them afterwards. */
 int grmhd_get_profile(grmhd_sim *sim, grmhd_profile_data *out, int reset);
 
+/* The flux-CT invariant of the current state: *divb_max = the largest
+ * |corner-centred divergence of sqrt(-g) B| over the corners between
+ * interior zones (sum over directions with more than one zone of the
+ * difference of sqrt(-g) B^d between the 4 zones on either side of the
+ * corner, over 4 dX_d), and *gb_max (may be NULL) = the largest
+ * |sqrt(-g) B^d| of those zones; flux-CT keeps their ratio, times the
+ * smallest dX, at round-off.  Synchronises the stream. */
+int grmhd_divb(grmhd_sim *sim, double *divb_max, double *gb_max);
+
 /* Autotuner: pick, by timing on the simulation's stream, the threads per
  * block (64, 128 or 256) of each heavy kernel of the step (reconstruction,
  * face fluxes, update + fixup, in the simulation's precision).  Results do
@@ -408,6 +417,46 @@ double grmhd_server_now(grmhd_server *srv);
 /* Stop the thread (requests not finished are dropped) and free everything.
  * NULL is accepted. */
 int grmhd_server_destroy(grmhd_server *srv);
+
+/* ---- Domain decomposition: one grid split into blocks ----
+ *
+ * The paper scales by splitting the grid into mesh blocks, one per node
+ * ("Scaling" section), and tests that the evolution does not depend on the
+ * split (end of its "Tests" section).  A decomposed grid here is a set of
+ * blocks of one global grid advanced together on the current device: each
+ * block fills the ghosts it shares with a neighbour from that neighbour's
+ * edge zones, in the order of the global ghost fill; the blocks share one
+ * CFL time step (the signal-speed maxima are combined before it is taken);
+ * and a failed zone at a block edge averages over the same neighbours as in
+ * the whole grid.  The result is bitwise that of grmhd_create/grmhd_step on
+ * the undecomposed grid.  The exchange step is the one a multi-GPU split
+ * would carry between devices. */
+typedef struct grmhd_decomp grmhd_decomp; /* opaque, library-owned */
+
+/* Split the global grid into nblocks[0] x nblocks[1] x nblocks[2] blocks of
+ * as equal sizes as possible (each split direction needs >= 3 zones per
+ * block); grid, metric and params as grmhd_create.  stream: as grmhd_create
+ * (every call of this object is ordered on it). */
+int grmhd_decomp_create(const grmhd_grid *grid, const grmhd_metric *metric,
+                        const grmhd_params *params, const int nblocks[3], void *stream,
+                        grmhd_decomp **out);
+
+int grmhd_decomp_destroy(grmhd_decomp *dc);
+
+/* Host primitives of the global grid, interior ([8][n3][n2][n1]) or with
+ * ghosts ([8][n3+6][n2+6][n1+6]; needed for FIXED boundaries); the ghosts
+ * are then filled as grmhd_set_prims fills them.  Synchronous. */
+int grmhd_decomp_set_prims(grmhd_decomp *dc, const double *P, int with_ghosts);
+
+/* The global primitives into host memory, interior or with ghosts. */
+int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghosts);
+
+/* Advance nsteps cycles, as grmhd_step (stats: the blocks' counters summed). */
+int grmhd_decomp_step(grmhd_decomp *dc, int nsteps, grmhd_stats *stats);
+
+/* Synchronise and read the statistics; check != 0 also reports, as
+ * grmhd_step does, GRMHD_ERR_INVERSION / GRMHD_ERR_DT since the last check. */
+int grmhd_decomp_get_stats(grmhd_decomp *dc, grmhd_stats *stats, int check);
 
 /* Name of an error code. */
 const char *grmhd_strerror(int code);

@@ -94,8 +94,8 @@ static void free_all(grmhd_sim *s) {
 }
 
 // Arguments of grmhd_create: GRMHD_OK and the dimensions, or GRMHD_ERR_INVALID.
-static int validate(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_params *params,
-                    Dims *Dout) {
+int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_params *params,
+                     Dims *Dout) {
   if (!grid || !metric || !params) return GRMHD_ERR_INVALID;
   const int n[3] = {grid->n1, grid->n2, grid->n3};
   const double xmin[3] = {grid->x1min, grid->x2min, grid->x3min};
@@ -142,7 +142,7 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
                                const grmhd_params *params, size_t *bytes) {
   Dims D;
   if (!bytes) return GRMHD_ERR_INVALID;
-  const int rc = validate(grid, metric, params, &D);
+  const int rc = validate_problem(grid, metric, params, &D);
   if (rc != GRMHD_OK) return rc;
   const size_t tot = (size_t)D.ntot, n2d = (size_t)D.n2d;
   size_t b = sizeof(double) * NV * tot * 8                 // P, Ph, F1..3, Lf, Rf, Uc
@@ -158,15 +158,17 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
   return GRMHD_OK;
 }
 
-extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
-                            const grmhd_params *params, void *stream, grmhd_sim **out) {
+int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_params *params,
+               void *stream, const BlockSpec *blk, grmhd_sim **out) {
   if (!out) return GRMHD_ERR_INVALID;
   *out = nullptr;
-  {
-    const int rc = validate(grid, metric, params, nullptr);
+  if (!blk) {
+    const int rc = validate_problem(grid, metric, params, nullptr);
     if (rc != GRMHD_OK) return rc;
   }
-  const int n[3] = {grid->n1, grid->n2, grid->n3};
+  // a block: its own size, the global grid's coordinates
+  const int gn[3] = {grid->n1, grid->n2, grid->n3};
+  const int n[3] = {blk ? blk->n[0] : gn[0], blk ? blk->n[1] : gn[1], blk ? blk->n[2] : gn[2]};
   const double xmin[3] = {grid->x1min, grid->x2min, grid->x3min};
   const double xmax[3] = {grid->x1max, grid->x2max, grid->x3max};
   long long tot = 1;
@@ -242,7 +244,8 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   G.gam = params->gamma;
   for (int d = 0; d < 3; d++) {
     G.xmin[d] = xmin[d];
-    G.dx[d] = (xmax[d] - xmin[d]) / n[d];
+    G.dx[d] = (xmax[d] - xmin[d]) / gn[d];
+    G.off[d] = blk ? blk->off[d] : 0;
   }
   G.geom = s->geom;
   G.conn = s->conn;
@@ -274,6 +277,10 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
   A.flat3 = flat3_of(D, params);
+  for (int d = 0; d < 3; d++) {
+    A.xlo[d] = blk ? blk->xlo[d] : 0;
+    A.xhi[d] = blk ? blk->xhi[d] : 0;
+  }
   set_ff_constants(A);
   A.geomff = s->geomff;
   A.connff = s->connff;
@@ -306,6 +313,11 @@ extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
   }
   *out = s;
   return GRMHD_OK;
+}
+
+extern "C" int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
+                            const grmhd_params *params, void *stream, grmhd_sim **out) {
+  return sim_create(grid, metric, params, stream, nullptr, out);
 }
 
 extern "C" int grmhd_destroy(grmhd_sim *s) {
@@ -563,6 +575,19 @@ extern "C" int grmhd_set_geometry(grmhd_sim *s, int loc, const double *in) {
     launch_to_ff((long long)NLOC * G_NCOMP * n2d, s->geom, s->geomff, s->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_divb(grmhd_sim *s, double *divb_max, double *gb_max) {
+  if (!s || !divb_max) return GRMHD_ERR_INVALID;
+  // the two result words live in the (between-step) EMF scratch
+  unsigned long long *dev = (unsigned long long *)s->emf, host[2];
+  launch_divb(s->A, s->P, dev, s->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  memcpy(divb_max, &host[0], sizeof(double));
+  if (gb_max) memcpy(gb_max, &host[1], sizeof(double));
   return GRMHD_OK;
 }
 

@@ -90,11 +90,13 @@ __global__ void k_geometry(GeomArgs A) {
   if (ij >= n2d) return;
   const int i = (int)(ij % A.D.s[0]);
   const int j = (int)(ij / A.D.s[0]);
-  const double X1c = A.xmin[0] + (i - NG + 0.5) * A.dx[0];
-  const double X2c = A.xmin[1] + (j - NG + 0.5) * A.dx[1];
+  // global zone indices (a block of a decomposed grid sits at A.off)
+  const int ig = i - NG + A.off[0], jg = j - NG + A.off[1];
+  const double X1c = A.xmin[0] + (ig + 0.5) * A.dx[0];
+  const double X2c = A.xmin[1] + (jg + 0.5) * A.dx[1];
   for (int loc = 0; loc < NLOC; loc++) {
-    const double X1 = (loc == LOC_FACE1) ? A.xmin[0] + (i - NG) * A.dx[0] : X1c;
-    const double X2 = (loc == LOC_FACE2) ? A.xmin[1] + (j - NG) * A.dx[1] : X2c;
+    const double X1 = (loc == LOC_FACE1) ? A.xmin[0] + ig * A.dx[0] : X1c;
+    const double X2 = (loc == LOC_FACE2) ? A.xmin[1] + jg * A.dx[1] : X2c;
     double g[4][4], gi[4][4];
     metric_at(A.kind, A.a, A.h, X1, X2, g);
     const double det = inverse4(g, gi);

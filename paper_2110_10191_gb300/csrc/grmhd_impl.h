@@ -14,6 +14,7 @@ struct GeomArgs {
   int kind;
   double a, h, gam;
   double xmin[3], dx[3];
+  int off[3];      // global index of the first interior zone (blocks of a decomposed grid; else 0)
   double *geom;    // [NLOC][G_NCOMP][n2d]
   double *conn;    // [C_NCOMP][n2d]
   double *floors;  // [2][n2d]
@@ -28,12 +29,20 @@ struct Clock {
   unsigned long long counters[4];   // inversion failures, floor hits, unrecoverable, spare
 };
 
+// boundary code of a side shared with another block of a decomposed grid:
+// the bounds leave its ghosts to the exchange between blocks
+constexpr int BC_EXCHANGE = 4;
+
 struct StepArgs {
   Dims D;
   double gam, igam, cfl;  // adiabatic index, its reciprocal, Courant number
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   int flat3;  // n3 = 1 with periodic X3: fluxes on the single k layer, copied
+  // sides that continue into a neighbouring block of a decomposed grid (1)
+  // rather than ending at a physical boundary (0): the fixup may average
+  // over the first ghost layer there, which holds the neighbour's zones
+  int xlo[3], xhi[3];
   // gamma, gamma - 1 and gamma (gamma - 1) split into float words (high, low)
   // for the float-float flux stage
   float gam_ff[2], gm1_ff[2], ggm1_ff[2], igam_ff[2], gf_ff[2];  // gf = (gamma - 1)/gamma
@@ -70,6 +79,9 @@ void launch_fix_ct(const StepArgs &A, double *F[3], double *emf, cudaStream_t st
 void launch_to_f32(long long n, const double *src, float *dst, cudaStream_t st);
 // float-float split of n doubles: dst[0..n) high words, dst[n..2n) low words
 void launch_to_ff(long long n, const double *src, float *dst, cudaStream_t st);
+// max |corner divergence of sqrt(-g) B| and max |sqrt(-g) B^d| over the
+// corners' zones, as double bit patterns into out[2] (device)
+void launch_divb(const StepArgs &A, const double *P, unsigned long long *out, cudaStream_t st);
 // pack interior <-> ghost layout
 void launch_pack(const Dims &D, const double *src, double *dst, int to_ghost, cudaStream_t st);
 

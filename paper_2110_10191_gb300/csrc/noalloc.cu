@@ -105,6 +105,7 @@ extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *
     G.xmin[d] = xmin[d];
     G.dx[d] = (xmax[d] - xmin[d]) / n[d];
   }
+  G.off[0] = G.off[1] = G.off[2] = 0;
   G.geom = (double *)(base + off_geom);
   G.conn = (double *)(base + off_conn);
   G.floors = (double *)(base + off_floors);

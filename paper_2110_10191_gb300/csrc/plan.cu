@@ -400,23 +400,38 @@ int plan_fix_ct(const Plan &p, cudaStream_t st, PlanHook *h) {
   return nl;
 }
 
-int plan_update(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st, PlanHook *h) {
+int plan_update_only(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st,
+                     PlanHook *h) {
   int nl = launch(p, PC_UPD64, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
     kp_update<<<nb, bs, 0, st>>>(V, in, dtfac, ucache_mode);
   });
   nl += launch(p, PC_UPDX, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
     kp_update_ff<<<nb, bs, 0, st>>>(V, in, dtfac, ucache_mode);
   });
-  nl += launch(p, PC_ZONE, GRMHD_K_FIXUP, h,
-               [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, 1 - in); });
   return nl;
 }
 
-int plan_bounds(const Plan &p, int which, cudaStream_t st, PlanHook *h) {
+int plan_fixup(const Plan &p, int out, cudaStream_t st, PlanHook *h) {
+  return launch(p, PC_ZONE, GRMHD_K_FIXUP, h,
+                [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, out); });
+}
+
+int plan_update(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st, PlanHook *h) {
+  return plan_update_only(p, in, dtfac, ucache_mode, st, h) + plan_fixup(p, 1 - in, st, h);
+}
+
+int plan_bounds_pass(const Plan &p, int which, int pass, cudaStream_t st, PlanHook *h) {
   const int B = GRMHD_K_BOUNDS;
-  int nl = launch(p, PC_BX1, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<0><<<nb, bs, 0, st>>>(V, which); });
-  nl += launch(p, PC_BX2, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<1><<<nb, bs, 0, st>>>(V, which); });
-  nl += launch(p, PC_BX3, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<2><<<nb, bs, 0, st>>>(V, which); });
+  if (pass == 0)
+    return launch(p, PC_BX1, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<0><<<nb, bs, 0, st>>>(V, which); });
+  if (pass == 1)
+    return launch(p, PC_BX2, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<1><<<nb, bs, 0, st>>>(V, which); });
+  return launch(p, PC_BX3, B, h, [&](unsigned nb, unsigned bs, BView V) { kp_bounds<2><<<nb, bs, 0, st>>>(V, which); });
+}
+
+int plan_bounds(const Plan &p, int which, cudaStream_t st, PlanHook *h) {
+  int nl = 0;
+  for (int pass = 0; pass < 3; pass++) nl += plan_bounds_pass(p, which, pass, st, h);
   return nl;
 }
 

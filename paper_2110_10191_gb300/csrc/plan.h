@@ -124,6 +124,13 @@ int plan_fix_ct(const Plan &p, cudaStream_t st, PlanHook *h);
 int plan_update(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st, PlanHook *h);
 // ghost fill of P (which 0) or Ph (which 1)
 int plan_bounds(const Plan &p, int which, cudaStream_t st, PlanHook *h);
+// the pieces of plan_update and plan_bounds, for a decomposed grid that
+// exchanges block edges between them: the update alone (into 1 - in), the
+// fixup of array out, one ghost-fill pass (0: X1, 1: X2, 2: X3)
+int plan_update_only(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st,
+                     PlanHook *h);
+int plan_fixup(const Plan &p, int out, cudaStream_t st, PlanHook *h);
+int plan_bounds_pass(const Plan &p, int which, int pass, cudaStream_t st, PlanHook *h);
 // one stage: stage 0 predictor (P -> Ph, dt/2, with the CFL step),
 // stage 1 corrector (Ph -> P, dt)
 int plan_stage(const Plan &p, int stage, int ucache_mode, cudaStream_t st, PlanHook *h);

@@ -32,3 +32,19 @@ struct grmhd_sim {
   double prof_ms[GRMHD_NKCLASS];
 };
 
+
+// A block of a decomposed grid: the global index of its first interior
+// zone, its size, and the sides that continue into a neighbouring block.
+struct BlockSpec {
+  int off[3], n[3], xlo[3], xhi[3];
+};
+
+// grmhd_create for a whole grid (blk == NULL) or for one block of a
+// decomposed grid (grid: the global grid; params->bc with GRMHD_BC_EXCHANGE
+// on the sides shared with other blocks; no validation: the caller
+// validated the global problem).
+int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_params *params,
+               void *stream, const BlockSpec *blk, grmhd_sim **out);
+// the argument checks of grmhd_create
+int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_params *params,
+                     grmhd::Dims *Dout);

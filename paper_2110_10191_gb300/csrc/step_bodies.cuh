@@ -544,8 +544,8 @@ __device__ __forceinline__ void fixup_body(const StepArgs &A, double *P, const i
           for (int di = -1; di <= 1; di++) {
             if (di == 0 && dj == 0 && dk == 0) continue;
             const int ii = i + di, jj = j + dj, kk = k + dk;
-            if (ii < NG || ii >= D.n[0] + NG || jj < NG || jj >= D.n[1] + NG || kk < NG ||
-                kk >= D.n[2] + NG)
+            if (ii < NG - A.xlo[0] || ii >= D.n[0] + NG + A.xhi[0] || jj < NG - A.xlo[1] ||
+                jj >= D.n[1] + NG + A.xhi[1] || kk < NG - A.xlo[2] || kk >= D.n[2] + NG + A.xhi[2])
               continue;
             const long long nb = zid(D, ii, jj, kk);
             if (pflag[nb] != 0) continue;

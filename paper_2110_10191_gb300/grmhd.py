@@ -104,12 +104,14 @@ class grmhd_server_stats(ctypes.Structure):
 EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_ghost",
            "grmhd_get_prims", "grmhd_step", "grmhd_get_stats", "grmhd_set_time",
            "grmhd_predictor", "grmhd_get_fluxes", "grmhd_next_dt", "grmhd_get_flags",
-           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_profile", "grmhd_get_profile",
+           "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_divb", "grmhd_profile", "grmhd_get_profile",
            "grmhd_fp64_peak", "grmhd_fluxes_noalloc", "grmhd_batch_create", "grmhd_batch_destroy",
            "grmhd_batch_step", "grmhd_batch_get_info", "grmhd_batch_sync", "grmhd_autotune",
            "grmhd_batch_autotune", "grmhd_batch_set_launch", "grmhd_footprint", "grmhd_server_create",
            "grmhd_server_submit", "grmhd_server_poll", "grmhd_server_drain", "grmhd_server_get_stats",
-           "grmhd_server_now", "grmhd_server_destroy", "grmhd_strerror"]
+           "grmhd_server_now", "grmhd_server_destroy", "grmhd_decomp_create", "grmhd_decomp_destroy",
+           "grmhd_decomp_set_prims", "grmhd_decomp_get_prims", "grmhd_decomp_step",
+           "grmhd_decomp_get_stats", "grmhd_strerror"]
 
 
 def lib_path() -> str:
@@ -154,6 +156,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_batch_get_info.argtypes = [vp, P(grmhd_batch_info)]
         L.grmhd_batch_sync.argtypes = [vp]
         L.grmhd_autotune.argtypes = [vp, i, P(d), P(d)]
+        L.grmhd_divb.argtypes = [vp, P(d), P(d)]
         L.grmhd_batch_autotune.argtypes = [vp, i, P(d), P(d)]
         L.grmhd_batch_set_launch.argtypes = [vp, i, i, i]
         L.grmhd_footprint.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params),
@@ -166,6 +169,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_server_get_stats.argtypes = [vp, P(grmhd_server_stats)]
         L.grmhd_server_now.argtypes = [vp]
         L.grmhd_server_destroy.argtypes = [vp]
+        L.grmhd_decomp_create.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params),
+                                          P(i), vp, P(vp)]
+        L.grmhd_decomp_destroy.argtypes = [vp]
+        L.grmhd_decomp_set_prims.argtypes = [vp, vp, i]
+        L.grmhd_decomp_get_prims.argtypes = [vp, vp, i]
+        L.grmhd_decomp_step.argtypes = [vp, i, P(grmhd_stats)]
+        L.grmhd_decomp_get_stats.argtypes = [vp, P(grmhd_stats), i]
         L.grmhd_strerror.argtypes = [i]
         L.grmhd_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -347,6 +357,12 @@ class Sim:
         _check(self.L.grmhd_get_profile(self.h, ctypes.byref(pd), int(reset)), "grmhd_get_profile")
         return {c: (pd.ms[q], pd.launches[q]) for q, c in enumerate(KCLASSES)}
 
+    def divb(self):
+        """(max |corner div sqrt(-g) B|, max |sqrt(-g) B^d|) of the state."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(self.L.grmhd_divb(self.h, ctypes.byref(a), ctypes.byref(b)), "grmhd_divb")
+        return a.value, b.value
+
     def autotune(self, trials: int = 3):
         """Pick the block sizes of the step's heavy kernels by timing;
         returns (ms before, ms after) for one pass of them."""
@@ -507,3 +523,60 @@ class Server:
         out = grmhd_server_stats()
         _check(self.L.grmhd_server_get_stats(self.h, ctypes.byref(out)), "grmhd_server_get_stats")
         return out.as_dict()
+
+
+class Decomp:
+    """One grid split into nblocks[0] x nblocks[1] x nblocks[2] blocks
+    (``grmhd_decomp_*``); bitwise the same evolution as ``Sim``."""
+
+    def __init__(self, problem, nblocks, stream=None):
+        self.L = load()
+        self.n = tuple(int(x) for x in problem.n)
+        self.s = tuple(x + 2 * NG for x in self.n)
+        g, m, p = _structs(problem)
+        nb = (ctypes.c_int * 3)(*[int(x) for x in nblocks])
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.h = ctypes.c_void_p()
+        _check(self.L.grmhd_decomp_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p), nb,
+                                          ctypes.c_void_p(stream or 0), ctypes.byref(self.h)),
+               "grmhd_decomp_create")
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.grmhd_decomp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_prims(self, P) -> None:
+        a = np.ascontiguousarray(P, dtype=np.float64)
+        n1, n2, n3 = self.n
+        if a.shape == (NPRIM, n3, n2, n1):
+            ghosts = 0
+        elif a.shape == (NPRIM,) + self.s[::-1]:
+            ghosts = 1
+        else:
+            raise ValueError("bad primitive shape %s" % (a.shape,))
+        _check(self.L.grmhd_decomp_set_prims(self.h, a.ctypes.data, ghosts), "grmhd_decomp_set_prims")
+
+    def get_prims(self, with_ghosts: bool = False) -> np.ndarray:
+        out = np.zeros((NPRIM,) + (self.s[::-1] if with_ghosts else self.n[::-1]))
+        _check(self.L.grmhd_decomp_get_prims(self.h, out.ctypes.data, int(with_ghosts)),
+               "grmhd_decomp_get_prims")
+        return out
+
+    def step(self, nsteps: int = 1):
+        st = grmhd_stats()
+        _check(self.L.grmhd_decomp_step(self.h, int(nsteps), ctypes.byref(st)), "grmhd_decomp_step")
+        return st.as_dict()
+
+    def stats(self, check: bool = False):
+        st = grmhd_stats()
+        _check(self.L.grmhd_decomp_get_stats(self.h, ctypes.byref(st), int(check)),
+               "grmhd_decomp_get_stats")
+        return st.as_dict()
