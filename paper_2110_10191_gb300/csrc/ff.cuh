@@ -11,9 +11,10 @@
 // and the double-word algorithms analysed by Joldes, Muller and Popescu
 // (ACM TOMS 2017): the "sloppy" sum (relative error bounded when both
 // operands have the same sign; absolute error about 2^-47 (|a| + |b|)
-// otherwise), the product with the cross terms folded into the FMA, and
-// Newton iterations for the reciprocal and the square root seeded by the
-// FP32 operation on the high word.
+// otherwise), the product with the cross terms folded into the FMA, and one
+// Newton step in float-float for the reciprocal, the inverse square root
+// (seeded by the hardware approximations on the high word) and the square
+// root (seeded by the FP32 square root).
 //
 // Every primitive uses the _rn intrinsics, which the compiler never fuses
 // into FMAs, so the error-free transformations stay exact.
@@ -120,9 +121,13 @@ __device__ __forceinline__ ff ff_sqr(ff a) {
 // a b + c
 __device__ __forceinline__ ff ff_fma(ff a, ff b, ff c) { return ff_add(ff_mul(a, b), c); }
 
-// 1/a: FP32 seed r0, then r0 + r0 (1 - a r0) with the residual in float-float
+// 1/a: FP32 seed r0 (the hardware approximation, within about an ulp of
+// 1/hi; a is never near the float underflow in these bodies, which work in
+// scaled units), then r0 + r0 (1 - a r0) with the residual in float-float,
+// which squares the seed's relative error
 __device__ __forceinline__ ff ff_rcp(ff a) {
-  const float r0 = __frcp_rn(a.hi);
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(a.hi));
   const ff res = ff_add_f(ff_neg(ff_mul_f(a, r0)), 1.0f);  // 1 - a r0, small
   return ff_add_f(ff_mul_f(res, r0), r0);
 }
@@ -140,9 +145,11 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
   return ff_add_f(ff_mul_f(d, __fdiv_rn(0.5f, s0)), s0);
 }
 
-// 1/sqrt(a), a > 0: y0 = 1/sqrtf(hi), then y0 + y0 (1 - a y0^2) / 2
+// 1/sqrt(a), a > 0: y0 from the hardware approximation of 1/sqrt(hi), then
+// y0 + y0 (1 - a y0^2) / 2
 __device__ __forceinline__ ff ff_rsqrt(ff a) {
-  const float y0 = __frcp_rn(__fsqrt_rn(a.hi));
+  float y0;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(a.hi));
   const ff ay = ff_mul_f(ff_mul_f(a, y0), y0);
   const ff res = ff_add_f(ff_neg(ay), 1.0f);
   return ff_add_f(ff_mul_f(res, __fmul_rn(0.5f, y0)), y0);
