@@ -29,6 +29,9 @@ _LIBS: dict = {}
 
 NPRIM = 8
 NG = 3
+# floor flag bits (as in grmhd_oracle.cpp)
+FF_GAMMA, FF_RHO_GEOM, FF_U_GEOM, FF_SIGMA, FF_BETA, FF_TEMP = 1, 2, 4, 8, 16, 32
+FF_DRIFT, FF_DRIFT_FAIL = 64, 128
 METRIC_MINKOWSKI, METRIC_MKS_KERR = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_POLAR, BC_FIXED = 0, 1, 2, 3
 RECON_MC, RECON_WENO5 = 0, 1
@@ -102,6 +105,9 @@ def lib(counting: bool = False) -> ctypes.CDLL:
         L.oracle_source_at.argtypes = [i, d, d, P(d), d, P(d), P(d)]
         L.oracle_floors_at.argtypes = [i, d, d, P(d), d, P(d)]
         L.oracle_floors_at.restype = i
+        L.oracle_floors_drift_at.argtypes = [i, d, d, P(d), d, P(d), P(d)]
+        L.oracle_floors_drift_at.restype = i
+        L.oracle_set_floor_frame.argtypes = [vp, i]
         L.oracle_recon.argtypes = [i, P(d), P(d)]
         L.oracle_op_counts.argtypes = [P(d), i]
         L.oracle_is_counting.restype = i
@@ -128,6 +134,7 @@ class Oracle:
         self.h = self.L.oracle_create(_ip(n), _dp(xmin), _dp(xmax), int(pr.metric), float(pr.a),
                                       float(pr.hslope), float(pr.gamma), float(pr.cfl),
                                       float(pr.t_final), int(pr.recon), int(pr.floors), _ip(bc))
+        self.L.oracle_set_floor_frame(self.h, int(getattr(pr, "floor_frame", 0)))
 
     def close(self):
         if self.h:
@@ -260,6 +267,16 @@ def floors_at(kind, a, h, X, gam, P):
     P = np.array(P, dtype=np.float64)
     fl = lib().oracle_floors_at(int(kind), float(a), float(h), _dp(_X(X)), float(gam), _dp(P))
     return int(fl), P
+
+
+def floors_drift_at(kind, a, h, X, gam, P):
+    """Drift-frame bounds at one point: (flags, bounded P, P before the
+    closing fluid-frame pass or None when no parcel was added)."""
+    P = np.array(P, dtype=np.float64)
+    pre = np.zeros(8)
+    fl = lib().oracle_floors_drift_at(int(kind), float(a), float(h), _dp(_X(X)), float(gam),
+                                      _dp(P), _dp(pre))
+    return int(fl), P, (pre if fl & FF_DRIFT else None)
 
 
 def recon(kind, x):

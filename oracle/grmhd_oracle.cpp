@@ -107,8 +107,11 @@ static const double GAMMA_MAX = 50.;         /* Lorentz factor < 50 */
 
 /* floor flag bits */
 enum {
-  FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32
+  FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32,
+  FF_DRIFT = 64,      /* drift-frame bounds: the parcel was added and the sum inverted */
+  FF_DRIFT_FAIL = 128 /* drift-frame bounds: that inversion failed, fluid-frame result kept */
 };
+enum { FLOOR_FLUID = 0, FLOOR_DRIFT = 1 };
 /* inversion failure codes (first failing check, fixed order) */
 enum {
   INV_OK = 0, INV_NOCONV = 1, INV_W_BAD = 2, INV_VSQ = 3, INV_RHO_NEG = 4, INV_U_NEG = 5, INV_D_NEG = 6
@@ -415,6 +418,7 @@ struct Sim {
   double a, hslope;
   double gam, cfl, t_final;
   int recon, floors_on;
+  int floor_frame; /* FLOOR_FLUID or FLOOR_DRIFT */
   int bc[3][2];
   std::vector<GeomPt> geom[NLOC];       /* [ij] */
   std::vector<real> conn;               /* [ij][4][4][4] */
@@ -906,6 +910,75 @@ static int apply_floors(real P[NPRIM], const GeomPt &g, real rho_fl, real u_fl, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* READING (drift-frame bounds; a variant the paper's bounds list leaves      */
+/* open).  The mass and internal energy that the fluid-frame bounds would     */
+/* add are added instead as a field-free parcel that moves with the zone's    */
+/* drift velocity: the part of the fluid 3-velocity seen by the normal        */
+/* observer that is perpendicular to B (the E x B drift of ideal MHD), so     */
+/* that floor material brings no momentum along the field.  With v = u~/gam  */
+/* (gam = sqrt(1 + u~.u~)) and B-hat = B/|B| in the spatial metric g_ij, the  */
+/* drift velocity is v_d = v - (v.B-hat) B-hat, its Lorentz factor is         */
+/* gam/sqrt(1 + (u~.B-hat)^2), hence u~_d = (u~ - (u~.B-hat) B-hat) /        */
+/* sqrt(1 + (u~.B-hat)^2); for B = 0 the parcel moves with the fluid.  The    */
+/* parcel's conserved variables are added to U(P) (P after the Lorentz-factor */
+/* cap) and the sum is inverted by 1D_W from the fluid-frame result; the      */
+/* fluid-frame bounds are then applied once more, so every bound holds on     */
+/* exit.  Where B = 0 or v is perpendicular to B the parcel moves with the    */
+/* fluid and the result is the fluid-frame one up to the inversion's          */
+/* round-off.  If the inversion fails, the fluid-frame result is kept.        */
+/* Ppre (may be NULL) receives the inverted state before that last pass.      */
+/* ------------------------------------------------------------------------ */
+static int apply_floors_drift(real P[NPRIM], const GeomPt &g, real rho_fl, real u_fl, real gam,
+                              real *Ppre) {
+  real Pf[NPRIM];
+  for (int v = 0; v < NPRIM; v++) Pf[v] = P[v];
+  int flags = apply_floors(Pf, g, rho_fl, u_fl, gam);
+  if (!(flags & ~FF_GAMMA)) {
+    for (int v = 0; v < NPRIM; v++) P[v] = Pf[v];
+    return flags;
+  }
+  /* the state the bounds act on: P's rho and u, the (capped) velocity */
+  real Pc[NPRIM];
+  for (int v = 0; v < NPRIM; v++) Pc[v] = P[v];
+  for (int i = 0; i < 3; i++) Pc[U1 + i] = Pf[U1 + i];
+  real Pp[NPRIM];
+  Pp[RHO] = Pf[RHO] - Pc[RHO];
+  Pp[UU] = Pf[UU] - Pc[UU];
+  real udB = 0.0, Bsq = 0.0;
+  for (int i = 1; i < 4; i++)
+    for (int j = 1; j < 4; j++) {
+      udB += g.gcov[i][j] * Pc[U1 + i - 1] * Pc[B1 + j - 1];
+      Bsq += g.gcov[i][j] * Pc[B1 + i - 1] * Pc[B1 + j - 1];
+    }
+  if (Bsq > 0.0) {
+    real upar2 = udB * udB / Bsq; /* (u~.B-hat)^2 */
+    real f = 1.0 / rsqrt_(1.0 + upar2);
+    for (int i = 0; i < 3; i++) Pp[U1 + i] = f * (Pc[U1 + i] - (udB / Bsq) * Pc[B1 + i]);
+  } else {
+    for (int i = 0; i < 3; i++) Pp[U1 + i] = Pc[U1 + i];
+  }
+  Pp[B1] = Pp[B2] = Pp[B3] = 0.0;
+  FluidState sc, sp;
+  get_state(Pc, g, sc);
+  get_state(Pp, g, sp);
+  real Uc[NPRIM], Up[NPRIM], Us[NPRIM];
+  prim_to_flux(Pc, sc, g, gam, 0, Uc);
+  prim_to_flux(Pp, sp, g, gam, 0, Up);
+  for (int v = 0; v < NPRIM; v++) Us[v] = Uc[v] + Up[v];
+  real Pn[NPRIM];
+  int pf = u_to_p(Us, g, gam, Pf, Pn);
+  if (pf != INV_OK) {
+    for (int v = 0; v < NPRIM; v++) P[v] = Pf[v];
+    return flags | FF_DRIFT_FAIL;
+  }
+  if (Ppre)
+    for (int v = 0; v < NPRIM; v++) Ppre[v] = Pn[v];
+  flags |= FF_DRIFT | apply_floors(Pn, g, rho_fl, u_fl, gam);
+  for (int v = 0; v < NPRIM; v++) P[v] = Pn[v];
+  return flags;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One stage: U(Pi) + dt'[-div F + S(Ps)] -> invert -> floors -> fixup.      */
 /* ------------------------------------------------------------------------ */
 static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<real> &Ps,
@@ -941,13 +1014,18 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
         }
         int pf = u_to_p(Unew, g, S->gam, pi, pn);
         int ff = 0;
-        if (pf == INV_OK && S->floors_on) ff = apply_floors(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam);
+        if (pf == INV_OK && S->floors_on)
+          ff = (S->floor_frame == FLOOR_DRIFT)
+                   ? apply_floors_drift(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam, nullptr)
+                   : apply_floors(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam);
         S->pflag[c] = pf;
         S->fflag[c] = ff;
         for (int v = 0; v < NPRIM; v++) Pout[v * N + c] = pn[v];
       }
   /* fixup of failed zones: mean of the non-failed interior zones of the
-   * 3x3x3 neighbourhood (rho, u, utilde); B is kept.  READING. */
+   * 3x3x3 neighbourhood (rho, u, utilde); B is kept.  READING.  The bounds
+   * of a fixed-up zone are the fluid-frame ones in either frame: the
+   * neighbour mean it takes conserves nothing to begin with. */
 #ifdef ORACLE_COUNT
   int saved_phase = g_phase;
   g_phase = 3;
@@ -1080,6 +1158,7 @@ void *oracle_create(const int n[3], const double xmin[3], const double xmax[3], 
   S->t_final = t_final;
   S->recon = recon;
   S->floors_on = floors_on;
+  S->floor_frame = FLOOR_FLUID;
   build_geometry(S);
   S->P.assign(NPRIM * S->ntot, real(0.0));
   S->Ph.assign(NPRIM * S->ntot, real(0.0));
@@ -1098,6 +1177,9 @@ void *oracle_create(const int n[3], const double xmin[3], const double xmax[3], 
 }
 
 void oracle_destroy(void *h) { delete (Sim *)h; }
+
+/* frame of the bounds: FLOOR_FLUID (default) or FLOOR_DRIFT */
+void oracle_set_floor_frame(void *h, int frame) { ((Sim *)h)->floor_frame = frame; }
 
 /* P: [8][n3][n2][n1] interior primitives; ghosts are filled by the BCs
  * (BC_FIXED ghosts are left as they are). */
@@ -1342,6 +1424,25 @@ int oracle_floors_at(int kind, double a, double h, const double X[4], double gam
   for (int v = 0; v < NPRIM; v++) p[v] = P[v];
   int fl = apply_floors(p, G, FLOOR_RHO_K * kk, FLOOR_U_K * std::pow(kk, gam), gam);
   for (int v = 0; v < NPRIM; v++) P[v] = val(p[v]);
+  return fl;
+}
+
+/* the drift-frame bounds at one point; Ppre (8 doubles, may be NULL): the
+ * inverted state before the closing fluid-frame pass (untouched unless
+ * FF_DRIFT is set) */
+int oracle_floors_drift_at(int kind, double a, double h, const double X[4], double gam, double *P,
+                           double *Ppre) {
+  GeomPt G;
+  geom_from_point(kind, a, h, X, G);
+  double r = std::exp(X[1]);
+  double kk = 1.0 / (r * r * (1.0 + r / 10.0));
+  real p[NPRIM], pre[NPRIM];
+  for (int v = 0; v < NPRIM; v++) p[v] = P[v];
+  for (int v = 0; v < NPRIM; v++) pre[v] = 0.0;
+  int fl = apply_floors_drift(p, G, FLOOR_RHO_K * kk, FLOOR_U_K * std::pow(kk, gam), gam, pre);
+  for (int v = 0; v < NPRIM; v++) P[v] = val(p[v]);
+  if (Ppre && (fl & FF_DRIFT))
+    for (int v = 0; v < NPRIM; v++) Ppre[v] = val(pre[v]);
   return fl;
 }
 

@@ -61,6 +61,7 @@ class Problem:
     P: np.ndarray                # [8][n3][n2][n1] float64
     info: dict = dataclasses.field(default_factory=dict)
     precision: int = 0           # 0 FP64, 1 mixed (FP32 reconstruction and fluxes)
+    floor_frame: int = 0         # bounds: 0 fluid frame, 1 drift frame
     exact: Optional[Callable[[float], np.ndarray]] = None
 
     @property
