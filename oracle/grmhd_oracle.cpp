@@ -104,6 +104,9 @@ static const double BSQ_OVER_RHO_MAX = 400.; /* sigma = b^2/rho < 400 */
 static const double BETA_MIN = 2.5e-5;       /* beta = P_gas/P_b > 2.5e-5 */
 static const double U_OVER_RHO_MAX = 100.;   /* u/rho < 100 */
 static const double GAMMA_MAX = 50.;         /* Lorentz factor < 50 */
+/* READING (drift-frame bounds): a field below this fraction of the density
+ * has no direction worth following (see apply_floors_drift) */
+static const double DRIFT_BSQ_MIN = 1.0e-20;
 
 /* floor flag bits */
 enum {
@@ -919,7 +922,9 @@ static int apply_floors(real P[NPRIM], const GeomPt &g, real rho_fl, real u_fl, 
 /* (gam = sqrt(1 + u~.u~)) and B-hat = B/|B| in the spatial metric g_ij, the  */
 /* drift velocity is v_d = v - (v.B-hat) B-hat, its Lorentz factor is         */
 /* gam/sqrt(1 + (u~.B-hat)^2), hence u~_d = (u~ - (u~.B-hat) B-hat) /        */
-/* sqrt(1 + (u~.B-hat)^2); for B = 0 the parcel moves with the fluid.  The    */
+/* sqrt(1 + (u~.B-hat)^2).  The direction of a field too weak to matter is   */
+/* set by rounding, so a field with g_ij B^i B^j <= 1e-20 rho (rho after the  */
+/* bounds) counts as none: the parcel then moves with the fluid.  The         */
 /* parcel's conserved variables are added to U(P) (P after the Lorentz-factor */
 /* cap) and the sum is inverted by 1D_W from the fluid-frame result; the      */
 /* fluid-frame bounds are then applied once more, so every bound holds on     */
@@ -950,7 +955,7 @@ static int apply_floors_drift(real P[NPRIM], const GeomPt &g, real rho_fl, real 
       udB += g.gcov[i][j] * Pc[U1 + i - 1] * Pc[B1 + j - 1];
       Bsq += g.gcov[i][j] * Pc[B1 + i - 1] * Pc[B1 + j - 1];
     }
-  if (Bsq > 0.0) {
+  if (Bsq > DRIFT_BSQ_MIN * Pf[RHO]) {
     real upar2 = udB * udB / Bsq; /* (u~.B-hat)^2 */
     real f = 1.0 / rsqrt_(1.0 + upar2);
     for (int i = 0; i < 3; i++) Pp[U1 + i] = f * (Pc[U1 + i] - (udB / Bsq) * Pc[B1 + i]);

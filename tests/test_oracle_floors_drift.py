@@ -4,7 +4,8 @@ drift velocity, the part of the fluid 3-velocity perpendicular to B).
 
 What fixes the variant independently of its own formula:
 
-* Without a field, and for flow perpendicular to the field, the parcel moves
+* Without a field (or one below 1e-20 of the density, whose direction is
+  rounding), and for flow perpendicular to the field, the parcel moves
   with the fluid and ideal-MHD stress-energy is linear in (rho, u) at fixed
   4-velocity and field, so the result is the fluid-frame one.
 * For flow along the field the drift velocity vanishes: the conserved
@@ -65,7 +66,7 @@ def _state(rng, X, field="random", glf_max=10.0):
     P = np.array([rho, u, *ut, *B])
     if field != "none":
         bsq = oracle.state_at(1, A, H, X, P)["bsq"]
-        P[5:] *= math.sqrt(1e-3 * rho / bsq)
+        P[5:] *= math.sqrt((1e-25 if field == "weak" else 1e-3) * rho / bsq)
     return P, G
 
 
@@ -73,9 +74,12 @@ def _rel(a, b, scale):
     return np.max(np.abs(a - b)) / scale
 
 
-@pytest.mark.parametrize("field", ["none", "perp"])
+@pytest.mark.parametrize("field", ["none", "perp", "weak"])
 def test_drift_equals_fluid_frame(field):
-    rng, Xs = _points(300, 11 if field == "none" else 12)
+    """No field, flow perpendicular to the field, and a field too weak to
+    have a direction (B^2 below 1e-20 rho, the stated reading): the parcel
+    moves with the fluid."""
+    rng, Xs = _points(300, {"none": 11, "perp": 12, "weak": 16}[field])
     for X in Xs:
         P, G = _state(rng, X, field)
         fl_f, Pf = oracle.floors_at(1, A, H, X, GAM, P)
@@ -86,7 +90,8 @@ def test_drift_equals_fluid_frame(field):
         assert Pd[1] == pytest.approx(Pf[1], rel=1e-12)
         un = math.sqrt(Pf[2:5] @ G["gcov"][1:, 1:] @ Pf[2:5])
         assert _rel(Pd[2:5], Pf[2:5], max(un, 1e-300)) <= 1e-11
-        assert np.array_equal(Pd[5:], P[5:]) or _rel(Pd[5:], P[5:], np.abs(P[5:]).max()) <= 1e-15
+        # B comes back from U_B = sqrt(-g)(b^j u^t - b^t u^j): rounding of |b||u|
+        assert _rel(Pd[5:], P[5:], np.abs(P[5:]).max() + 1e-300) <= 1e-13 or np.array_equal(Pd[5:], P[5:])
 
 
 def test_drift_parallel_flow_adds_a_parcel_at_rest():
