@@ -89,13 +89,27 @@ typedef struct {
  * floors_on: apply the paper's bounds (needs the MKS radius); bc[d][side]:
  * GRMHD_BC_* for direction d, side 0 = low, 1 = high; precision:
  * GRMHD_PREC_* (the state, geometry and conserved variables are FP64 in
- * both modes). */
+ * every mode); floor_frame: GRMHD_FLOOR_* (0, the fluid frame, when
+ * zero-initialised). */
 typedef struct {
   double gamma, cfl, t_final;
   int recon, floors_on;
   int bc[3][2];
   int precision;
+  int floor_frame; /* GRMHD_FLOOR_*: where the bounds add mass and energy */
 } grmhd_params;
+
+/* Frame of the bounds (the paper lists the bounds, not the frame in which
+ * they add material).  FLUID: rho and u are raised in place, the velocity
+ * is kept.  DRIFT: the same mass and internal energy are added as a
+ * field-free parcel moving with the drift velocity (the normal-observer
+ * 3-velocity minus its component along B), its conserved variables added to
+ * U(P) and the sum inverted by 1D_W; the fluid-frame bounds then run once
+ * more so that every bound holds.  The frames agree where the flow is
+ * perpendicular to B, and where B is absent: g_ij B^i B^j <= 1e-20 rho.  Fixed-up zones take the fluid-frame bounds in
+ * either frame. */
+#define GRMHD_FLOOR_FLUID 0
+#define GRMHD_FLOOR_DRIFT 1
 
 /* Running statistics of a simulation (totals over all stages so far). */
 typedef struct {

@@ -121,6 +121,8 @@ int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const g
       params->precision != GRMHD_PREC_FF)
     return GRMHD_ERR_INVALID;
   if (params->floors_on && metric->kind != GRMHD_METRIC_MKS_KERR) return GRMHD_ERR_INVALID;
+  if (params->floor_frame != GRMHD_FLOOR_FLUID && params->floor_frame != GRMHD_FLOOR_DRIFT)
+    return GRMHD_ERR_INVALID;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) {
       const int b = params->bc[d][sd];
@@ -153,7 +155,8 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
     b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
   if (params->precision == GRMHD_PREC_FF)
     b += 2 * sizeof(float) * (NV * tot + (NLOC * G_NCOMP + C_NCOMP) * n2d);
-  b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision);
+  b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision,
+                         params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT);
   *bytes = b;
   return GRMHD_OK;
 }
@@ -274,6 +277,7 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   }
   A.recon = params->recon;
   A.floors_on = params->floors_on;
+  A.floor_drift = params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
   A.flat3 = flat3_of(D, params);

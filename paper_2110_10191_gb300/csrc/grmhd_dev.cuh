@@ -43,7 +43,12 @@ constexpr double FL_SIGMA = 400.0;
 constexpr double FL_BETA = 2.5e-5;
 constexpr double FL_TEMP = 100.0;
 constexpr double FL_GAMMA = 50.0;
-enum { FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32 };
+constexpr double FL_DRIFT_BSQ = 1.0e-20;  // drift-frame bounds: weaker fields count as none
+enum {
+  FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32,
+  FF_DRIFT = 64,      // drift-frame bounds: parcel added, sum inverted
+  FF_DRIFT_FAIL = 128 // that inversion failed: the fluid-frame result was kept
+};
 enum { PF_OK = 0, PF_NOCONV = 1, PF_W = 2, PF_VSQ = 3, PF_RHO = 4, PF_U = 5, PF_D = 6 };
 
 // Reciprocal without the IEEE division sequence: the hardware approximation
@@ -464,6 +469,76 @@ __device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double r
   if (P[UU] < ub) { P[UU] = ub; fl |= FF_BETA; }
   const double rt = P[UU] / FL_TEMP;
   if (P[RHO] < rt) { P[RHO] = rt; fl |= FF_TEMP; }
+  return fl;
+}
+
+// Drift-frame bounds.  The mass and internal energy that the fluid-frame
+// bounds would add go in as a field-free parcel that moves with the drift
+// velocity, the part of the normal-observer 3-velocity v = utilde/gamma
+// perpendicular to B; in terms of utilde and the unit field direction Bh,
+// utilde_d = (utilde - (utilde.Bh) Bh) / sqrt(1 + (utilde.Bh)^2).  A field
+// with g_ij B^i B^j <= 1e-20 rho (rho after the bounds), whose direction
+// rounding decides, counts as none: the parcel then moves with the fluid.
+// U(P) (after the Lorentz-factor cap) plus
+// the parcel's U is inverted from the fluid-frame result, and the fluid-frame
+// bounds run once more.  If that inversion fails the fluid-frame result is
+// kept.
+static __device__ __noinline__ int apply_floors_drift(double P[NV], const Geo &G, double rho_fl,
+                                                      double u_fl, double gam, double igam) {
+  double Pf[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Pf[v] = P[v];
+  int fl = apply_floors(Pf, G, rho_fl, u_fl, gam);
+  if (!(fl & ~FF_GAMMA)) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) P[v] = Pf[v];
+    return fl;
+  }
+  double Pc[NV], Pp[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Pc[v] = P[v];
+  Pc[U1] = Pf[U1];
+  Pc[U2] = Pf[U2];
+  Pc[U3] = Pf[U3];
+  Pp[RHO] = Pf[RHO] - Pc[RHO];
+  Pp[UU] = Pf[UU] - Pc[UU];
+  const double b1 = Pc[B1], b2 = Pc[B2], b3 = Pc[B3];
+  const double l1 = G.gcov[SY(1, 1)] * b1 + G.gcov[SY(1, 2)] * b2 + G.gcov[SY(1, 3)] * b3;
+  const double l2 = G.gcov[SY(1, 2)] * b1 + G.gcov[SY(2, 2)] * b2 + G.gcov[SY(2, 3)] * b3;
+  const double l3 = G.gcov[SY(1, 3)] * b1 + G.gcov[SY(2, 3)] * b2 + G.gcov[SY(3, 3)] * b3;
+  const double Bsq = l1 * b1 + l2 * b2 + l3 * b3;
+  const double udB = l1 * Pc[U1] + l2 * Pc[U2] + l3 * Pc[U3];
+  if (Bsq > FL_DRIFT_BSQ * Pf[RHO]) {
+    const double f = 1.0 / sqrt(1.0 + udB * udB / Bsq);
+    const double q = udB / Bsq;
+    Pp[U1] = f * (Pc[U1] - q * b1);
+    Pp[U2] = f * (Pc[U2] - q * b2);
+    Pp[U3] = f * (Pc[U3] - q * b3);
+  } else {
+    Pp[U1] = Pc[U1];
+    Pp[U2] = Pc[U2];
+    Pp[U3] = Pc[U3];
+  }
+  Pp[B1] = Pp[B2] = Pp[B3] = 0.0;
+  double Us[NV], Up[NV];
+  {
+    FState s;
+    fluid_state(Pc, G, s);
+    prim_flux(Pc, s, G, gam, 0, Us);
+    fluid_state(Pp, G, s);
+    prim_flux(Pp, s, G, gam, 0, Up);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; v++) Us[v] += Up[v];
+  double Pn[NV], bsq, lor;
+  if (invert_1dw(Us, G, gam, igam, Pf, Pn, bsq, lor) != PF_OK) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) P[v] = Pf[v];
+    return fl | FF_DRIFT_FAIL;
+  }
+  fl |= FF_DRIFT | apply_floors(Pn, G, rho_fl, u_fl, gam);
+#pragma unroll
+  for (int v = 0; v < NV; v++) P[v] = Pn[v];
   return fl;
 }
 

@@ -38,6 +38,7 @@ struct StepArgs {
   double gam, igam, cfl;  // adiabatic index, its reciprocal, Courant number
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
+  int floor_drift;  // bounds in the drift frame: a separate pass after the update
   int flat3;  // n3 = 1 with periodic X3: fluxes on the single k layer, copied
   // sides that continue into a neighbouring block of a decomposed grid (1)
   // rather than ending at a physical boundary (0): the fixup may average

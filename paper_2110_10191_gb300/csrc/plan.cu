@@ -161,6 +161,12 @@ __global__ void __maxnreg__(128) kp_update_ff(BView V, int in, double dtfac, int
                  it.fflag, dtfac, it.Uc, ucache_mode, block_tid(V, g));
 }
 
+__global__ void kp_floor_drift(BView V, int out) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  floor_drift_body(it.A, arr(it, out), it.pflag, it.fflag, block_tid(V, g));
+}
+
 __global__ void kp_fixup(BView V, int out) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
@@ -247,7 +253,7 @@ int upload_tables(Plan &p) {
 
 }  // namespace
 
-void plan_counts(const Dims &D, int flat3, int prec, long long c[PC_N]) {
+void plan_counts(const Dims &D, int flat3, int prec, int drift, long long c[PC_N]) {
   const int fl = flat3;
   const bool f64 = prec == GRMHD_PREC_FP64, mx = prec == GRMHD_PREC_MIXED, fx = prec == GRMHD_PREC_FF;
   c[PC_BX1] = n_bounds_x1(D);
@@ -272,11 +278,12 @@ void plan_counts(const Dims &D, int flat3, int prec, long long c[PC_N]) {
   c[PC_ZONE] = n_zone(D);
   c[PC_UPD64] = fx ? 0 : n_zone(D);
   c[PC_UPDX] = fx ? n_zone(D) : 0;
+  c[PC_FLOORD] = drift ? n_zone(D) : 0;
 }
 
-long long plan_bytes(const Dims &D, int flat3, int prec) {
+long long plan_bytes(const Dims &D, int flat3, int prec, int drift) {
   long long c[PC_N], ints = 0;
-  plan_counts(D, flat3, prec, c);
+  plan_counts(D, flat3, prec, drift, c);
   for (int q = 0; q < PC_N; q++) ints += 2 * nblk(c[q], 64);
   return (long long)sizeof(StageItem) + 4 * ints;
 }
@@ -295,7 +302,7 @@ int plan_build(Plan &p, const StageItem *items, int n) {
   long long zones = 0, cap = 0;
   for (int g = 0; g < n; g++) {
     long long c[PC_N];
-    plan_counts(items[g].A.D, items[g].A.flat3, items[g].prec, c);
+    plan_counts(items[g].A.D, items[g].A.flat3, items[g].prec, items[g].A.floor_drift, c);
     for (int q = 0; q < PC_N; q++) {
       p.count[(size_t)q * n + g] = c[q];
       cap += 2 * nblk(c[q], 64);  // the smallest block the tuner tries
@@ -407,6 +414,9 @@ int plan_update_only(const Plan &p, int in, double dtfac, int ucache_mode, cudaS
   });
   nl += launch(p, PC_UPDX, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
     kp_update_ff<<<nb, bs, 0, st>>>(V, in, dtfac, ucache_mode);
+  });
+  nl += launch(p, PC_FLOORD, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
+    kp_floor_drift<<<nb, bs, 0, st>>>(V, 1 - in);
   });
   return nl;
 }

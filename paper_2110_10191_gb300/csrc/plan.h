@@ -56,6 +56,7 @@ enum {
   PC_ZONE,   // fixup (every grid)
   PC_UPD64,  // FP64 update (FP64 and mixed-precision grids)
   PC_UPDX,   // float-float update (float-float grids)
+  PC_FLOORD, // drift-frame bounds (grids with bounds in the drift frame)
   PC_N
 };
 
@@ -92,10 +93,11 @@ struct PlanHook {
 // GRMHD_OK, GRMHD_ERR_INVALID (more than 2^31 - 1 blocks in a launch),
 // GRMHD_ERR_NOMEM or GRMHD_ERR_CUDA.
 int plan_build(Plan &p, const StageItem *items, int n);
-// threads per launch class of one grid (dimensions, flat X3, GRMHD_PREC_*)
-void plan_counts(const Dims &D, int flat3, int prec, long long c[PC_N]);
+// threads per launch class of one grid (dimensions, flat X3, GRMHD_PREC_*,
+// bounds in the drift frame)
+void plan_counts(const Dims &D, int flat3, int prec, int drift, long long c[PC_N]);
 // device bytes a one-grid plan of such a grid holds (item + block tables)
-long long plan_bytes(const Dims &D, int flat3, int prec);
+long long plan_bytes(const Dims &D, int flat3, int prec, int drift);
 void plan_free(Plan &p);
 // Re-lay the block tables of class cls for bs threads per block and block
 // order sched (the results of every grid do not depend on either).

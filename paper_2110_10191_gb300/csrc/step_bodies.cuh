@@ -507,7 +507,7 @@ __device__ __forceinline__ void update_body(const StepArgs &A, const double *Pi,
     }
     double pn[NV], bsq_n = 0.0, lor_n = 1.0;
     pf = invert_1dw(Un, G, A.gam, A.igam, pi, pn, bsq_n, lor_n);
-    if (pf == PF_OK && A.floors_on)
+    if (pf == PF_OK && A.floors_on && !A.floor_drift)
       ff = apply_floors_known(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
                               bsq_n, lor_n);
 #pragma unroll
@@ -516,6 +516,43 @@ __device__ __forceinline__ void update_body(const StepArgs &A, const double *Pi,
     fflag[c] = ff;
   }
   count_warp(active && pf != 0, &A.clk->counters[0]);
+  count_warp(active && ff != 0, &A.clk->counters[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Drift-frame bounds of the zones whose inversion succeeded (the update
+// leaves their bounds to this pass when A.floor_drift is set).  Every thread
+// of the block must call it (warp counters).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void floor_drift_body(const StepArgs &A, double *P,
+                                                 const int *__restrict__ pflag, int *fflag,
+                                                 long long t) {
+  const Dims &D = A.D;
+  if (!(A.clk->dt > 0.0)) return;
+  const long long nz = n_zone(D);
+  const bool active = t < nz;
+  int ff = 0;
+  if (active) {
+    const int i = NG + (int)(t % D.n[0]);
+    const int j = NG + (int)((t / D.n[0]) % D.n[1]);
+    const int k = NG + (int)(t / ((long long)D.n[0] * D.n[1]));
+    const long long c = zid(D, i, j, k), N = D.ntot;
+    if (pflag[c] == 0) {
+      const long long ij = (long long)j * D.s[0] + i;
+      Geo G;
+      load_geo(A.geom, D.n2d, ij, G);
+      double p[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) p[v] = P[v * N + c];
+      ff = apply_floors_drift(p, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
+                              A.igam);
+      if (ff) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) P[v * N + c] = p[v];
+        fflag[c] = ff;
+      }
+    }
+  }
   count_warp(active && ff != 0, &A.clk->counters[1]);
 }
 

@@ -44,12 +44,14 @@ class grmhd_metric(ctypes.Structure):
 
 
 PREC_FP64, PREC_MIXED, PREC_FF = 0, 1, 2
+FLOOR_FLUID, FLOOR_DRIFT = 0, 1
 
 
 class grmhd_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("t_final", ctypes.c_double),
                 ("recon", ctypes.c_int), ("floors_on", ctypes.c_int),
-                ("bc", (ctypes.c_int * 2) * 3), ("precision", ctypes.c_int)]
+                ("bc", (ctypes.c_int * 2) * 3), ("precision", ctypes.c_int),
+                ("floor_frame", ctypes.c_int)]
 
 
 KCLASSES = ["flux", "dt", "ct", "update", "fixup", "bounds", "other", "recon"]
@@ -222,6 +224,7 @@ def _structs(pr):
         for s in range(2):
             p.bc[d][s] = int(pr.bc[d][s])
     p.precision = int(getattr(pr, "precision", PREC_FP64))
+    p.floor_frame = int(getattr(pr, "floor_frame", FLOOR_FLUID))
     return g, m, p
 
 
