@@ -31,7 +31,9 @@ NPRIM = 8
 NG = 3
 # floor flag bits (as in grmhd_oracle.cpp)
 FF_GAMMA, FF_RHO_GEOM, FF_U_GEOM, FF_SIGMA, FF_BETA, FF_TEMP = 1, 2, 4, 8, 16, 32
-FF_DRIFT, FF_DRIFT_FAIL = 64, 128
+FF_DRIFT, FF_DRIFT_FAIL, FF_KTOT = 64, 128, 256
+# electron heating models
+ELEC_OFF, ELEC_CONSTANT, ELEC_KAWAZURA, ELEC_WERNER, ELEC_ROWAN, ELEC_SHARMA, ELEC_HOWES = range(7)
 METRIC_MINKOWSKI, METRIC_MKS_KERR = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_POLAR, BC_FIXED = 0, 1, 2, 3
 RECON_MC, RECON_WENO5 = 0, 1
@@ -108,6 +110,13 @@ def lib(counting: bool = False) -> ctypes.CDLL:
         L.oracle_floors_drift_at.argtypes = [i, d, d, P(d), d, P(d), P(d)]
         L.oracle_floors_drift_at.restype = i
         L.oracle_set_floor_frame.argtypes = [vp, i]
+        L.oracle_set_electrons.argtypes = [vp, i, d, d, d, d, d]
+        L.oracle_set_K.argtypes = [vp, P(d), i]
+        L.oracle_get_K.argtypes = [vp, P(d), i]
+        L.oracle_elec_fraction.argtypes = [i, d, d, d, d, d, d, d, d]
+        L.oracle_elec_fraction.restype = d
+        L.oracle_elec_heat.argtypes = [d, d, d, d, d, d, d]
+        L.oracle_elec_heat.restype = d
         L.oracle_recon.argtypes = [i, P(d), P(d)]
         L.oracle_op_counts.argtypes = [P(d), i]
         L.oracle_is_counting.restype = i
@@ -135,6 +144,25 @@ class Oracle:
                                       float(pr.hslope), float(pr.gamma), float(pr.cfl),
                                       float(pr.t_final), int(pr.recon), int(pr.floors), _ip(bc))
         self.L.oracle_set_floor_frame(self.h, int(getattr(pr, "floor_frame", 0)))
+        el = getattr(pr, "electrons", None)
+        self.electrons = bool(el and el["model"])
+        if self.electrons:
+            self.L.oracle_set_electrons(self.h, int(el["model"]), float(el["game"]),
+                                        float(el["gamp"]), float(el["fel"]),
+                                        float(el["tpte_min"]), float(el["tpte_max"]))
+
+    def set_K(self, K) -> None:
+        """Electron entropies (kappa_tot, kappa_e): [2][n3][n2][n1] or with ghosts."""
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        ghosts = 1 if K.shape == (2,) + self.s[::-1] else 0
+        if not ghosts and K.shape != (2,) + self.n[::-1]:
+            raise ValueError("bad electron shape %s" % (K.shape,))
+        self.L.oracle_set_K(self.h, _dp(K), ghosts)
+
+    def get_K(self, with_ghosts: bool = False) -> np.ndarray:
+        out = np.zeros((2,) + (self.s[::-1] if with_ghosts else self.n[::-1]))
+        self.L.oracle_get_K(self.h, _dp(out), int(with_ghosts))
+        return out
 
     def close(self):
         if self.h:
@@ -267,6 +295,18 @@ def floors_at(kind, a, h, X, gam, P):
     P = np.array(P, dtype=np.float64)
     fl = lib().oracle_floors_at(int(kind), float(a), float(h), _dp(_X(X)), float(gam), _dp(P))
     return int(fl), P
+
+
+def elec_fraction(model, gam, game, gamp, fel, rho, u, kel, bsq):
+    """Electron heating fraction of one zone (model as ELEC_* of the oracle)."""
+    return lib().oracle_elec_fraction(int(model), float(gam), float(game), float(gamp), float(fel),
+                                      float(rho), float(u), float(kel), float(bsq))
+
+
+def elec_heat(gam, game, rho_s, fel, ktot_new, ktot_adv, kel_adv):
+    """One heating update of kappa_e."""
+    return lib().oracle_elec_heat(float(gam), float(game), float(rho_s), float(fel),
+                                  float(ktot_new), float(ktot_adv), float(kel_adv))
 
 
 def floors_drift_at(kind, a, h, X, gam, P):

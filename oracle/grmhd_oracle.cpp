@@ -73,12 +73,19 @@ static inline bool operator>=(real a, real b) { return a.v >= b.v; }
 static inline bool operator==(real a, real b) { return a.v == b.v; }
 static inline bool operator!=(real a, real b) { return a.v != b.v; }
 static inline real rsqrt_(real a) { g_ops.sqrt += 1; return real(std::sqrt(a.v)); }
+/* special functions (electron heating only) are counted with the square roots */
+static inline real rpow(real a, real b) { g_ops.sqrt += 1; return real(std::pow(a.v, b.v)); }
+static inline real rexp(real a) { g_ops.sqrt += 1; return real(std::exp(a.v)); }
+static inline real rlog10(real a) { g_ops.sqrt += 1; return real(std::log10(a.v)); }
 static inline real rabs(real a) { return real(std::fabs(a.v)); }
 static inline double val(real a) { return a.v; }
 static inline bool rfinite(real a) { return std::isfinite(a.v); }
 #else
 typedef double real;
 static inline real rsqrt_(real a) { return std::sqrt(a); }
+static inline real rpow(real a, real b) { return std::pow(a, b); }
+static inline real rexp(real a) { return std::exp(a); }
+static inline real rlog10(real a) { return std::log10(a); }
 static inline real rabs(real a) { return std::fabs(a); }
 static inline double val(real a) { return a; }
 static inline bool rfinite(real a) { return std::isfinite(a); }
@@ -108,11 +115,31 @@ static const double GAMMA_MAX = 50.;         /* Lorentz factor < 50 */
  * has no direction worth following (see apply_floors_drift) */
 static const double DRIFT_BSQ_MIN = 1.0e-20;
 
+/* Electron thermodynamics (paper, "Implementation Notes": the optional
+ * partition of dissipation between ions and electrons of Ressler et al.
+ * (2015) with five heating models, and the bound P_gas/rho^gamma < 3 when
+ * electron temperatures are evolved).  ELEC_CONSTANT (a fixed electron
+ * share) is not one of the five; it serves the tests. */
+enum {
+  ELEC_OFF = 0, ELEC_CONSTANT = 1, ELEC_KAWAZURA = 2, ELEC_WERNER = 3, ELEC_ROWAN = 4,
+  ELEC_SHARMA = 5, ELEC_HOWES = 6
+};
+static const double KTOT_MAX = 3.0;          /* P_gas / rho^gamma < 3 */
+static const double ELEC_BETA_CAP = 1.0e20;  /* READING: beta of an unmagnetised zone */
+static const double MP_OVER_ME = 1836.15267343; /* proton / electron mass */
+struct ElecParams {
+  int model;                  /* ELEC_* */
+  double gam, game, gamp;     /* adiabatic index of the fluid, electrons, protons */
+  double fel_const;           /* ELEC_CONSTANT's share */
+  double tpte_min, tpte_max;  /* bounds on T_p / T_e */
+};
+
 /* floor flag bits */
 enum {
   FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32,
-  FF_DRIFT = 64,      /* drift-frame bounds: the parcel was added and the sum inverted */
-  FF_DRIFT_FAIL = 128 /* drift-frame bounds: that inversion failed, fluid-frame result kept */
+  FF_DRIFT = 64,       /* drift-frame bounds: the parcel was added and the sum inverted */
+  FF_DRIFT_FAIL = 128, /* drift-frame bounds: that inversion failed, fluid-frame result kept */
+  FF_KTOT = 256        /* electrons: u lowered to keep P_gas / rho^gamma below 3 */
 };
 enum { FLOOR_FLUID = 0, FLOOR_DRIFT = 1 };
 /* inversion failure codes (first failing check, fixed order) */
@@ -422,12 +449,17 @@ struct Sim {
   double gam, cfl, t_final;
   int recon, floors_on;
   int floor_frame; /* FLOOR_FLUID or FLOOR_DRIFT */
+  int elec;          /* electron model (ELEC_*), 0: off */
+  ElecParams ep;
   int bc[3][2];
   std::vector<GeomPt> geom[NLOC];       /* [ij] */
   std::vector<real> conn;               /* [ij][4][4][4] */
   std::vector<real> rho_floor, u_floor; /* [ij] floor thresholds */
   std::vector<real> P, Ph;              /* [v][k][j][i] */
   std::vector<real> F[3];               /* [v][k][j][i], face i-1/2 etc. */
+  /* electrons: K = (kappa_tot, kappa_e) = (P_gas / rho^gamma, P_e / rho^gamma_e)
+   * per zone, [s][k][j][i], and their fluxes; stage arrays as P, Ph */
+  std::vector<real> K, Kh, FK[3];
   std::vector<real> emf[3];
   std::vector<int> pflag, fflag;
   real ctop_max[3];
@@ -494,11 +526,14 @@ static int wrap_index(int g, int n) {
   return NG + q;
 }
 
-static void copy_zone(Sim *S, std::vector<real> &P, long dst, long src) {
+/* K (may be empty): the electron entropies, copied as scalars */
+static void copy_zone(Sim *S, std::vector<real> &P, std::vector<real> &K, long dst, long src) {
   for (int v = 0; v < NPRIM; v++) P[v * S->ntot + dst] = P[v * S->ntot + src];
+  if (!K.empty())
+    for (int q = 0; q < 2; q++) K[q * S->ntot + dst] = K[q * S->ntot + src];
 }
 
-static void bounds(Sim *S, std::vector<real> &P) {
+static void bounds(Sim *S, std::vector<real> &P, std::vector<real> &K) {
   const long N = S->ntot;
   const int n1 = S->n[0], n2 = S->n[1], n3 = S->n[2];
   /* X1 */
@@ -508,11 +543,11 @@ static void bounds(Sim *S, std::vector<real> &P) {
         /* lower */
         int ig = g, ia;
         if (S->bc[0][0] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, ig, j, k), IDX(S, wrap_index(ig, n1), j, k));
+          copy_zone(S, P, K, IDX(S, ig, j, k), IDX(S, wrap_index(ig, n1), j, k));
         } else if (S->bc[0][0] == BC_OUTFLOW) {
           ia = NG;
           long d = IDX(S, ig, j, k), s = IDX(S, ia, j, k);
-          copy_zone(S, P, d, s);
+          copy_zone(S, P, K, d, s);
           real rescale = S->geom[LOC_CENT][IJ(S, ia, j)].gdet / S->geom[LOC_CENT][IJ(S, ig, j)].gdet;
           for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;
           if (P[U1 * N + d] > 0.0) P[U1 * N + d] = 0.0;
@@ -520,11 +555,11 @@ static void bounds(Sim *S, std::vector<real> &P) {
         /* upper */
         ig = n1 + NG + g;
         if (S->bc[0][1] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, ig, j, k), IDX(S, wrap_index(ig, n1), j, k));
+          copy_zone(S, P, K, IDX(S, ig, j, k), IDX(S, wrap_index(ig, n1), j, k));
         } else if (S->bc[0][1] == BC_OUTFLOW) {
           ia = n1 + NG - 1;
           long d = IDX(S, ig, j, k), s = IDX(S, ia, j, k);
-          copy_zone(S, P, d, s);
+          copy_zone(S, P, K, d, s);
           real rescale = S->geom[LOC_CENT][IJ(S, ia, j)].gdet / S->geom[LOC_CENT][IJ(S, ig, j)].gdet;
           for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;
           if (P[U1 * N + d] < 0.0) P[U1 * N + d] = 0.0;
@@ -536,25 +571,25 @@ static void bounds(Sim *S, std::vector<real> &P) {
       for (int g = 0; g < NG; g++) {
         int jg = NG - 1 - g;
         if (S->bc[1][0] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, wrap_index(jg, n2), k));
+          copy_zone(S, P, K, IDX(S, i, jg, k), IDX(S, i, wrap_index(jg, n2), k));
         } else if (S->bc[1][0] == BC_POLAR) {
           long d = IDX(S, i, jg, k);
-          copy_zone(S, P, d, IDX(S, i, NG + g, k));
+          copy_zone(S, P, K, d, IDX(S, i, NG + g, k));
           P[U2 * N + d] = -P[U2 * N + d];
           P[B2 * N + d] = -P[B2 * N + d];
         } else if (S->bc[1][0] == BC_OUTFLOW) {
-          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, NG, k));
+          copy_zone(S, P, K, IDX(S, i, jg, k), IDX(S, i, NG, k));
         }
         jg = n2 + NG + g;
         if (S->bc[1][1] == BC_PERIODIC) {
-          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, wrap_index(jg, n2), k));
+          copy_zone(S, P, K, IDX(S, i, jg, k), IDX(S, i, wrap_index(jg, n2), k));
         } else if (S->bc[1][1] == BC_POLAR) {
           long d = IDX(S, i, jg, k);
-          copy_zone(S, P, d, IDX(S, i, n2 + NG - 1 - g, k));
+          copy_zone(S, P, K, d, IDX(S, i, n2 + NG - 1 - g, k));
           P[U2 * N + d] = -P[U2 * N + d];
           P[B2 * N + d] = -P[B2 * N + d];
         } else if (S->bc[1][1] == BC_OUTFLOW) {
-          copy_zone(S, P, IDX(S, i, jg, k), IDX(S, i, n2 + NG - 1, k));
+          copy_zone(S, P, K, IDX(S, i, jg, k), IDX(S, i, n2 + NG - 1, k));
         }
       }
   /* X3 */
@@ -563,14 +598,14 @@ static void bounds(Sim *S, std::vector<real> &P) {
       for (int g = 0; g < NG; g++) {
         int kg = NG - 1 - g;
         if (S->bc[2][0] == BC_PERIODIC)
-          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));
+          copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));
         else if (S->bc[2][0] == BC_OUTFLOW)
-          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, NG));
+          copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, NG));
         kg = n3 + NG + g;
         if (S->bc[2][1] == BC_PERIODIC)
-          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));
+          copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));
         else if (S->bc[2][1] == BC_OUTFLOW)
-          copy_zone(S, P, IDX(S, i, j, kg), IDX(S, i, j, n3 + NG - 1));
+          copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, n3 + NG - 1));
       }
 }
 
@@ -624,7 +659,47 @@ static real llf_face(const Sim *S, const GeomPt &g, int d, const real PL[NPRIM],
   return ctop;
 }
 
-static void get_fluxes(Sim *S, const std::vector<real> &P) {
+/* Reconstructed values of the scalar field A (one variable of ntot) on both
+ * sides of the face between zones c-1 and c along d, as face_states does
+ * for the primitives. */
+static void recon_scalar(const Sim *S, const std::vector<real> &A, long base, int d, int i, int j,
+                         int k, real *L, real *R) {
+  int off[3] = {0, 0, 0};
+  off[d] = 1;
+  real x[6];
+  for (int q = 0; q < 6; q++) {
+    int s = q - 3;
+    x[q] = A[base + IDX(S, i + s * off[0], j + s * off[1], k + s * off[2])];
+  }
+  if (S->recon == RECON_WENO5) {
+    *L = weno5_right(x[0], x[1], x[2], x[3], x[4]);
+    *R = weno5_right(x[5], x[4], x[3], x[2], x[1]);
+  } else {
+    *L = x[2] + 0.5 * mc_slope(x[1], x[2], x[3]);
+    *R = x[3] - 0.5 * mc_slope(x[2], x[3], x[4]);
+  }
+}
+
+/* Fluxes of the electron entropies (Ressler et al. 2015): kappa_tot and
+ * kappa_e are carried with the mass, conserved density sqrt(-g) rho u^t K
+ * and flux sqrt(-g) rho u^d K, combined as the other fluxes are (local
+ * Lax-Friedrichs with the face's ctop) from K reconstructed on each side. */
+static void elec_face(const Sim *S, const std::vector<real> &K, const GeomPt &g, int d, int i,
+                      int j, int k, const real PL[NPRIM], const real PR[NPRIM], real ctop,
+                      real FK[2]) {
+  FluidState sL, sR;
+  get_state(PL, g, sL);
+  get_state(PR, g, sR);
+  real mL = PL[RHO] * sL.ucon[d + 1], mR = PR[RHO] * sR.ucon[d + 1]; /* rho u^d */
+  real dL = PL[RHO] * sL.ucon[0], dR = PR[RHO] * sR.ucon[0];         /* rho u^t */
+  for (int q = 0; q < 2; q++) {
+    real KL, KR;
+    recon_scalar(S, K, (long)q * S->ntot, d, i, j, k, &KL, &KR);
+    FK[q] = 0.5 * g.gdet * (mL * KL + mR * KR - ctop * (dR * KR - dL * KL));
+  }
+}
+
+static void get_fluxes(Sim *S, const std::vector<real> &P, const std::vector<real> &K) {
   const long N = S->ntot;
   for (int d = 0; d < 3; d++) {
     S->ctop_max[d] = 0.0;
@@ -649,6 +724,11 @@ static void get_fluxes(Sim *S, const std::vector<real> &P) {
           real ctop = llf_face(S, g, d, PL, PR, Fo);
           long id = IDX(S, i, j, k);
           for (int v = 0; v < NPRIM; v++) S->F[d][v * N + id] = Fo[v];
+          if (S->elec) {
+            real FK[2];
+            elec_face(S, K, g, d, i, j, k, PL, PR, ctop, FK);
+            for (int q = 0; q < 2; q++) S->FK[d][q * N + id] = FK[q];
+          }
           /* dt uses the faces of interior zones only */
           bool interior = true;
           for (int e = 0; e < 3; e++) {
@@ -662,16 +742,23 @@ static void get_fluxes(Sim *S, const std::vector<real> &P) {
 }
 
 /* READING (boundary flux fixes): X2 polar faces carry no flux; at an X1
- * outflow boundary no mass flows in from outside. */
+ * outflow boundary no mass flows in from outside, nor do the electron
+ * entropies that the mass carries. */
 static void fix_flux(Sim *S) {
   const long N = S->ntot;
   if (S->bc[1][0] == BC_POLAR || S->bc[1][1] == BC_POLAR) {
     for (int k = NG - 1; k <= S->n[2] + NG; k++)
       for (int i = NG - 1; i <= S->n[0] + NG; i++) {
-        if (S->bc[1][0] == BC_POLAR)
+        if (S->bc[1][0] == BC_POLAR) {
           for (int v = 0; v < NPRIM; v++) S->F[1][v * N + IDX(S, i, NG, k)] = 0.0;
-        if (S->bc[1][1] == BC_POLAR)
+          if (S->elec)
+            for (int q = 0; q < 2; q++) S->FK[1][q * N + IDX(S, i, NG, k)] = 0.0;
+        }
+        if (S->bc[1][1] == BC_POLAR) {
           for (int v = 0; v < NPRIM; v++) S->F[1][v * N + IDX(S, i, S->n[1] + NG, k)] = 0.0;
+          if (S->elec)
+            for (int q = 0; q < 2; q++) S->FK[1][q * N + IDX(S, i, S->n[1] + NG, k)] = 0.0;
+        }
       }
   }
   if (S->bc[0][0] == BC_OUTFLOW || S->bc[0][1] == BC_OUTFLOW) {
@@ -679,11 +766,19 @@ static void fix_flux(Sim *S) {
       for (int j = NG - 1; j <= S->n[1] + NG; j++) {
         if (S->bc[0][0] == BC_OUTFLOW) {
           long id = IDX(S, NG, j, k);
-          if (S->F[0][RHO * N + id] > 0.0) S->F[0][RHO * N + id] = 0.0;
+          if (S->F[0][RHO * N + id] > 0.0) {
+            S->F[0][RHO * N + id] = 0.0;
+            if (S->elec)
+              for (int q = 0; q < 2; q++) S->FK[0][q * N + id] = 0.0;
+          }
         }
         if (S->bc[0][1] == BC_OUTFLOW) {
           long id = IDX(S, S->n[0] + NG, j, k);
-          if (S->F[0][RHO * N + id] < 0.0) S->F[0][RHO * N + id] = 0.0;
+          if (S->F[0][RHO * N + id] < 0.0) {
+            S->F[0][RHO * N + id] = 0.0;
+            if (S->elec)
+              for (int q = 0; q < 2; q++) S->FK[0][q * N + id] = 0.0;
+          }
         }
       }
   }
@@ -984,10 +1079,123 @@ static int apply_floors_drift(real P[NPRIM], const GeomPt &g, real rho_fl, real 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Electron heating fraction f_e, the share of the dissipated internal       */
+/* energy that goes to the electrons, from a zone's rho, u, b^2 and          */
+/* kappa_e.  Temperatures (units of m_p c^2): u_e = kappa_e                   */
+/* rho^gamma_e/(gamma_e - 1), T_e = (gamma_e - 1) u_e/rho, T_p = (gamma_p -   */
+/* 1)(u - u_e)/rho; the proton beta is beta_p = rho T_p/(b^2/2).             */
+/* READING: temperatures enter by magnitude, T_p/T_e is clamped to          */
+/* [1e-20, 1e20] and beta_p to [1e-20, 1e20] (1e20: an unmagnetised zone).  */
+/* Each
+/* model is the fit its paper publishes, with f_e = 1/(1 + Q_i/Q_e):          */
+/*  Kawazura et al. 2019  Q_i/Q_e = 35/(1 + (beta_p/15)^-1.4 e^(-0.1 T_e/T_p)) */
+/*  Werner et al. 2018    f_e = (1 + sqrt((s/5)/(2 + s/5)))/4, s = b^2/rho    */
+/*  Rowan et al. 2017     f_e = exp(-(1 - beta_p/beta_max)^3.3 /              */
+/*                        (1 + 1.2 s_w^0.7))/2, s_w = b^2/(rho + u + p),      */
+/*                        beta_max = 1/(4 s_w), beta_p capped at beta_max     */
+/*  Sharma et al. 2007    Q_e/Q_i = 0.33 sqrt(T_e/T_p)                        */
+/*  Howes 2010            Q_i/Q_e = c1 (c2^2 + beta_p^x)/(c3^2 + beta_p^x)    */
+/*                        sqrt(m_p T_p/(m_e T_e)) e^(-1/beta_p), x = 2 -      */
+/*                        0.2 log10(T_p/T_e), c1 = 0.92; c2 = 1.6 T_e/T_p and */
+/*                        c3 = 18 + 5 log10(T_p/T_e) for T_p > T_e, else      */
+/*                        c2 = 1.2 T_e/T_p, c3 = 18                           */
+/* ------------------------------------------------------------------------ */
+static real elec_fraction(const ElecParams &e, real rho, real u, real kel, real bsq) {
+  if (e.model == ELEC_CONSTANT) return e.fel_const;
+  real ue = kel * rpow(rho, e.game) / (e.game - 1.0);
+  real Te = rabs((e.game - 1.0) * ue / rho);
+  real Tp = rabs((e.gamp - 1.0) * (u - ue) / rho);
+  real trat = (Te > 0.0) ? Tp / Te : real(ELEC_BETA_CAP); /* T_p / T_e */
+  trat = rmin(rmax(trat, real(1.0e-20)), real(1.0e20));
+  real beta = (bsq > 0.0) ? 2.0 * rho * Tp / bsq : real(ELEC_BETA_CAP);
+  beta = rmin(rmax(beta, real(1.0 / ELEC_BETA_CAP)), real(ELEC_BETA_CAP));
+  if (e.model == ELEC_KAWAZURA) {
+    real qiqe = 35.0 / (1.0 + rpow(beta / 15.0, -1.4) * rexp(-0.1 / trat));
+    return 1.0 / (1.0 + qiqe);
+  }
+  if (e.model == ELEC_WERNER) {
+    real s = bsq / rho;
+    return 0.25 * (1.0 + rsqrt_((s / 5.0) / (2.0 + s / 5.0)));
+  }
+  if (e.model == ELEC_ROWAN) {
+    real sw = bsq / (rho + e.gam * u);
+    real r = rmin(4.0 * sw * beta, real(1.0)); /* beta_p / beta_max */
+    return 0.5 * rexp(-rpow(1.0 - r, 3.3) / (1.0 + 1.2 * rpow(sw, 0.7)));
+  }
+  if (e.model == ELEC_SHARMA) {
+    real qeqi = 0.33 * rsqrt_(1.0 / trat);
+    return qeqi / (1.0 + qeqi);
+  }
+  if (e.model == ELEC_HOWES) {
+    real lt = rlog10(trat);
+    real c2 = (trat > 1.0) ? 1.6 / trat : 1.2 / trat;
+    real c3 = (trat > 1.0) ? 18.0 + 5.0 * lt : real(18.0);
+    real bx = rpow(beta, 2.0 - 0.2 * lt);
+    real qiqe = 0.92 * (c2 * c2 + bx) / (c3 * c3 + bx) * rsqrt_(MP_OVER_ME * trat) *
+                rexp(-1.0 / beta);
+    return 1.0 / (1.0 + qiqe);
+  }
+  return 0.0;
+}
+
+/* Electron heating (Ressler et al. 2015) of one zone after its inversion.
+ * kappa_tot_new = (gamma - 1) u/rho^gamma of the updated state is the
+ * entropy the fluid has; kappa_tot,adv, carried without dissipation, the
+ * entropy it would have had; the electrons take the share f_e of the
+ * difference, as internal energy at the density rho_s:
+ *   kappa_e = kappa_e,adv + f_e (gamma_e - 1)/(gamma - 1) rho_s^(gamma - gamma_e)
+ *             (kappa_tot_new - kappa_tot,adv),
+ * i.e. rho_s^gamma_e d(kappa_e)/(gamma_e - 1) = f_e rho_s^gamma d(kappa_tot)/(gamma - 1).
+ * READING: rho_s and f_e come from the stage's source state (the state the
+ * geometric source uses), and the heating precedes the bounds, so that
+ * floor material brings the electrons no heat. */
+static real elec_heat(const ElecParams &e, real rho_s, real fel, real ktot_new, real ktot_adv,
+                      real kel_adv) {
+  return kel_adv + fel * (e.game - 1.0) / (e.gam - 1.0) * rpow(rho_s, e.gam - e.game) *
+                       (ktot_new - ktot_adv);
+}
+
+/* Bounds on kappa_e from T_p/T_e in [tpte_min, tpte_max]: with p_e = rho T_e,
+ * p_p = rho T_p and u = p_e/(gamma_e - 1) + p_p/(gamma_p - 1) = p/(gamma - 1),
+ * a ratio R = T_p/T_e gives kappa_e = kappa_tot rho^(gamma - gamma_e) /
+ * ((gamma - 1)/(gamma_e - 1) + R (gamma - 1)/(gamma_p - 1)).  A kappa_e that
+ * is not a number takes the lower bound. */
+static real elec_bound(const ElecParams &e, real rho, real ktot, real kel) {
+  real a = (e.gam - 1.0) / (e.game - 1.0), b = (e.gam - 1.0) / (e.gamp - 1.0);
+  real kk = ktot * rpow(rho, e.gam - e.game);
+  real kmax = kk / (a + e.tpte_min * b);
+  real kmin = kk / (a + e.tpte_max * b);
+  if (!(kel == kel)) kel = kmin;
+  return rmin(rmax(kel, kmin), kmax);
+}
+
+/* The closing steps of a zone's electron state once the fluid's bounds are
+ * done: u lowered so that P_gas/rho^gamma <= 3 (paper, bounds list, when
+ * electron temperatures are evolved; with the bounds on), kappa_tot reset to
+ * the state's, kappa_e bounded.  Returns FF_KTOT if u was lowered. */
+static int elec_close(const Sim *S, real P[NPRIM], real K[2]) {
+  const ElecParams &e = S->ep;
+  int fl = 0;
+  if (S->floors_on) {
+    real kt = (e.gam - 1.0) * P[UU] / rpow(P[RHO], e.gam);
+    if (kt > KTOT_MAX) {
+      P[UU] = KTOT_MAX * rpow(P[RHO], e.gam) / (e.gam - 1.0);
+      fl = FF_KTOT;
+    }
+  }
+  K[0] = (e.gam - 1.0) * P[UU] / rpow(P[RHO], e.gam);
+  K[1] = elec_bound(e, P[RHO], K[0], K[1]);
+  return fl;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One stage: U(Pi) + dt'[-div F + S(Ps)] -> invert -> floors -> fixup.      */
 /* ------------------------------------------------------------------------ */
+/* Ki, Ks, Kout: the electron entropies of the same stage arrays (empty
+ * without electrons; Kout may be Ki, each zone reads its own first). */
 static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<real> &Ps,
-                         std::vector<real> &Pout, double dtp) {
+                         std::vector<real> &Pout, double dtp, const std::vector<real> &Ki,
+                         const std::vector<real> &Ks, std::vector<real> &Kout) {
   const long N = S->ntot;
   const int n1 = S->n[0], n2 = S->n[1], n3 = S->n[2];
   bool same = (&Pi == &Ps);
@@ -1019,13 +1227,43 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
         }
         int pf = u_to_p(Unew, g, S->gam, pi, pn);
         int ff = 0;
-        if (pf == INV_OK && S->floors_on)
+        real kn[2] = {0.0, 0.0};
+        if (S->elec) {
+          /* the entropies carried with the mass: U_K = sqrt(-g) rho u^t K */
+          real kadv[2];
+          for (int q = 0; q < 2; q++) {
+            long o = (long)q * N;
+            real divk = (S->FK[0][o + cp1] - S->FK[0][o + c]) / S->dx[0] +
+                        (S->FK[1][o + cp2] - S->FK[1][o + c]) / S->dx[1] +
+                        (S->FK[2][o + cp3] - S->FK[2][o + c]) / S->dx[2];
+            real Uk = Ui[RHO] * Ki[o + c] + dtp * (0.0 - divk);
+            kadv[q] = Uk / Unew[RHO];
+          }
+          kn[0] = kadv[0];
+          kn[1] = kadv[1];
+          if (pf == INV_OK) {
+            const real *psrc = same ? pi : ps;
+            FluidState st;
+            get_state(psrc, g, st);
+            real fel = elec_fraction(S->ep, psrc[RHO], psrc[UU], Ks[N + c], st.bsq);
+            real ktot_new = (S->gam - 1.0) * pn[UU] / rpow(pn[RHO], S->gam);
+            kn[1] = elec_heat(S->ep, psrc[RHO], fel, ktot_new, kadv[0], kadv[1]);
+            if (S->floors_on)
+              ff = (S->floor_frame == FLOOR_DRIFT)
+                       ? apply_floors_drift(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam, nullptr)
+                       : apply_floors(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam);
+            ff |= elec_close(S, pn, kn);
+          }
+        } else if (pf == INV_OK && S->floors_on) {
           ff = (S->floor_frame == FLOOR_DRIFT)
                    ? apply_floors_drift(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam, nullptr)
                    : apply_floors(pn, g, S->rho_floor[ij], S->u_floor[ij], S->gam);
+        }
         S->pflag[c] = pf;
         S->fflag[c] = ff;
         for (int v = 0; v < NPRIM; v++) Pout[v * N + c] = pn[v];
+        if (S->elec)
+          for (int q = 0; q < 2; q++) Kout[(long)q * N + c] = kn[q];
       }
   /* fixup of failed zones: mean of the non-failed interior zones of the
    * 3x3x3 neighbourhood (rho, u, utilde); B is kept.  READING.  The bounds
@@ -1042,7 +1280,7 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
         long c = IDX(S, i, j, k);
         if (S->pflag[c] == INV_OK) continue;
         S->inv_fail_total++;
-        real sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        real sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, sumk = 0.0;
         int cnt = 0;
         for (int dk = -1; dk <= 1; dk++)
           for (int dj = -1; dj <= 1; dj++)
@@ -1054,6 +1292,7 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
               long nb = IDX(S, ii, jj, kk);
               if (S->pflag[nb] != INV_OK) continue;
               for (int v = 0; v < 5; v++) sum[v] += Pout[v * N + nb];
+              if (S->elec) sumk += Kout[N + nb];
               cnt++;
             }
         if (cnt == 0) {
@@ -1066,6 +1305,12 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
         long ij = IJ(S, i, j);
         if (S->floors_on)
           S->fflag[c] |= apply_floors(pn, S->geom[LOC_CENT][ij], S->rho_floor[ij], S->u_floor[ij], S->gam);
+        if (S->elec) {
+          /* READING: kappa_e takes the same neighbour mean; kappa_tot follows u */
+          real kn[2] = {0.0, sumk / (double)cnt};
+          S->fflag[c] |= elec_close(S, pn, kn);
+          for (int q = 0; q < 2; q++) Kout[(long)q * N + c] = kn[q];
+        }
         for (int v = 0; v < NPRIM; v++) Pout[v * N + c] = pn[v];
       }
   for (int k = NG; k < n3 + NG; k++)
@@ -1076,7 +1321,7 @@ static int advance_stage(Sim *S, const std::vector<real> &Pi, const std::vector<
 #ifdef ORACLE_COUNT
   g_phase = saved_phase;
 #endif
-  bounds(S, Pout);
+  bounds(S, Pout, Kout);
   return unrecoverable;
 }
 
@@ -1110,7 +1355,7 @@ static double compute_dt(Sim *S) {
 static int step_once(Sim *S) {
   /* predictor: Ps = Pi = P^n, dt' = dt/2 -> Ph */
   PHASE(0);
-  get_fluxes(S, S->P);
+  get_fluxes(S, S->P, S->K);
   PHASE(4);
   double dt = compute_dt(S);
   if (!std::isfinite(dt)) return -3;
@@ -1119,15 +1364,15 @@ static int step_once(Sim *S) {
   fix_flux(S);
   flux_ct(S);
   PHASE(2);
-  int bad = advance_stage(S, S->P, S->P, S->Ph, 0.5 * dt);
+  int bad = advance_stage(S, S->P, S->P, S->Ph, 0.5 * dt, S->K, S->K, S->Kh);
   /* corrector: Ps = P^{n+1/2}, Pi = P^n, dt' = dt -> P^{n+1} */
   PHASE(0);
-  get_fluxes(S, S->Ph);
+  get_fluxes(S, S->Ph, S->Kh);
   PHASE(1);
   fix_flux(S);
   flux_ct(S);
   PHASE(2);
-  bad += advance_stage(S, S->P, S->Ph, S->P, dt);
+  bad += advance_stage(S, S->P, S->Ph, S->P, dt, S->K, S->Kh, S->K);
   PHASE(4);
   S->t += dt;
   S->dt = dt;
@@ -1164,6 +1409,8 @@ void *oracle_create(const int n[3], const double xmin[3], const double xmax[3], 
   S->recon = recon;
   S->floors_on = floors_on;
   S->floor_frame = FLOOR_FLUID;
+  S->elec = ELEC_OFF;
+  S->ep = ElecParams{ELEC_OFF, gam, 0.0, 0.0, 0.0, 0.0, 0.0};
   build_geometry(S);
   S->P.assign(NPRIM * S->ntot, real(0.0));
   S->Ph.assign(NPRIM * S->ntot, real(0.0));
@@ -1186,6 +1433,79 @@ void oracle_destroy(void *h) { delete (Sim *)h; }
 /* frame of the bounds: FLOOR_FLUID (default) or FLOOR_DRIFT */
 void oracle_set_floor_frame(void *h, int frame) { ((Sim *)h)->floor_frame = frame; }
 
+/* Evolve the electron entropies with heating model `model` (ELEC_*; 0
+ * turns them off).  Call before setting the state; kappa starts at 0. */
+void oracle_set_electrons(void *h, int model, double game, double gamp, double fel_const,
+                          double tpte_min, double tpte_max) {
+  Sim *S = (Sim *)h;
+  S->elec = model;
+  S->ep.model = model;
+  S->ep.gam = S->gam;
+  S->ep.game = game;
+  S->ep.gamp = gamp;
+  S->ep.fel_const = fel_const;
+  S->ep.tpte_min = tpte_min;
+  S->ep.tpte_max = tpte_max;
+  if (model) {
+    S->K.assign(2 * S->ntot, real(0.0));
+    S->Kh.assign(2 * S->ntot, real(0.0));
+    for (int d = 0; d < 3; d++) S->FK[d].assign(2 * S->ntot, real(0.0));
+  } else {
+    S->K.clear();
+    S->Kh.clear();
+    for (int d = 0; d < 3; d++) S->FK[d].clear();
+  }
+}
+
+/* K: (kappa_tot, kappa_e) as [2][n3][n2][n1] (with_ghosts = 0) or
+ * [2][s3][s2][s1]; ghosts are then filled by the BCs as for the primitives
+ * (which are filled again, unchanged). */
+void oracle_set_K(void *h, const double *K, int with_ghosts) {
+  Sim *S = (Sim *)h;
+  if (!S->elec) return;
+  if (with_ghosts) {
+    for (long q = 0; q < 2 * S->ntot; q++) S->K[q] = K[q];
+  } else {
+    for (int v = 0; v < 2; v++)
+      for (int k = 0; k < S->n[2]; k++)
+        for (int j = 0; j < S->n[1]; j++)
+          for (int i = 0; i < S->n[0]; i++)
+            S->K[v * S->ntot + IDX(S, i + NG, j + NG, k + NG)] =
+                K[(((long)v * S->n[2] + k) * S->n[1] + j) * S->n[0] + i];
+  }
+  bounds(S, S->P, S->K);
+  S->Ph = S->P;
+  S->Kh = S->K;
+}
+
+void oracle_get_K(void *h, double *K, int with_ghosts) {
+  Sim *S = (Sim *)h;
+  if (!S->elec) return;
+  if (with_ghosts) {
+    for (long q = 0; q < 2 * S->ntot; q++) K[q] = val(S->K[q]);
+    return;
+  }
+  for (int v = 0; v < 2; v++)
+    for (int k = 0; k < S->n[2]; k++)
+      for (int j = 0; j < S->n[1]; j++)
+        for (int i = 0; i < S->n[0]; i++)
+          K[(((long)v * S->n[2] + k) * S->n[1] + j) * S->n[0] + i] =
+              val(S->K[v * S->ntot + IDX(S, i + NG, j + NG, k + NG)]);
+}
+
+/* pointwise: the heating fraction of a zone, and one heating update */
+double oracle_elec_fraction(int model, double gam, double game, double gamp, double fel_const,
+                            double rho, double u, double kel, double bsq) {
+  ElecParams e = {model, gam, game, gamp, fel_const, 0.0, 0.0};
+  return val(elec_fraction(e, rho, u, kel, bsq));
+}
+
+double oracle_elec_heat(double gam, double game, double rho_s, double fel, double ktot_new,
+                        double ktot_adv, double kel_adv) {
+  ElecParams e = {ELEC_CONSTANT, gam, game, 0.0, fel, 0.0, 0.0};
+  return val(elec_heat(e, rho_s, fel, ktot_new, ktot_adv, kel_adv));
+}
+
 /* P: [8][n3][n2][n1] interior primitives; ghosts are filled by the BCs
  * (BC_FIXED ghosts are left as they are). */
 /* READING (fixed boundaries): the ghosts of a BC_FIXED side hold their set
@@ -1198,16 +1518,18 @@ void oracle_set_prims(void *h, const double *P) {
         for (int i = 0; i < S->n[0]; i++)
           S->P[v * S->ntot + IDX(S, i + NG, j + NG, k + NG)] =
               P[(((long)v * S->n[2] + k) * S->n[1] + j) * S->n[0] + i];
-  bounds(S, S->P);
+  bounds(S, S->P, S->K);
   S->Ph = S->P;
+  S->Kh = S->K;
 }
 
 /* P: [8][s3][s2][s1] including ghosts; then the BCs are applied. */
 void oracle_set_prims_ghost(void *h, const double *P) {
   Sim *S = (Sim *)h;
   for (long q = 0; q < NPRIM * S->ntot; q++) S->P[q] = P[q];
-  bounds(S, S->P);
+  bounds(S, S->P, S->K);
   S->Ph = S->P;
+  S->Kh = S->K;
 }
 
 void oracle_get_prims(void *h, double *P, int with_ghosts) {
@@ -1243,13 +1565,14 @@ int oracle_step(void *h, int nsteps) {
  * the number of unrecoverable zones. */
 int oracle_predictor(void *h) {
   Sim *S = (Sim *)h;
-  get_fluxes(S, S->P);
+  get_fluxes(S, S->P, S->K);
   double dt = compute_dt(S);
   if (!(dt > 0.0) || !std::isfinite(dt)) return -3;
   fix_flux(S);
   flux_ct(S);
-  int bad = advance_stage(S, S->P, S->P, S->Ph, 0.5 * dt);
+  int bad = advance_stage(S, S->P, S->P, S->Ph, 0.5 * dt, S->K, S->K, S->Kh);
   S->P.swap(S->Ph);
+  S->K.swap(S->Kh);
   return bad;
 }
 
@@ -1294,7 +1617,7 @@ void oracle_get_flags(void *h, int *pflag, int *fflag) {
  * F: [3][8][s3][s2][s1]; ctop: max ctop per direction over interior faces. */
 void oracle_get_fluxes(void *h, double *F, double ctop[3]) {
   Sim *S = (Sim *)h;
-  get_fluxes(S, S->P);
+  get_fluxes(S, S->P, S->K);
   fix_flux(S);
   flux_ct(S);
   for (int d = 0; d < 3; d++) {
@@ -1306,7 +1629,7 @@ void oracle_get_fluxes(void *h, double *F, double ctop[3]) {
 /* The dt the next step would take (from the fluxes of the current state). */
 double oracle_next_dt(void *h) {
   Sim *S = (Sim *)h;
-  get_fluxes(S, S->P);
+  get_fluxes(S, S->P, S->K);
   return compute_dt(S);
 }
 

@@ -62,11 +62,41 @@ class Problem:
     info: dict = dataclasses.field(default_factory=dict)
     precision: int = 0           # 0 FP64, 1 mixed (FP32 reconstruction and fluxes)
     floor_frame: int = 0         # bounds: 0 fluid frame, 1 drift frame
+    # electron entropies: model and constants (None: not evolved), and the
+    # initial (kappa_tot, kappa_e) as [2][n3][n2][n1]
+    electrons: Optional[dict] = None
+    K: Optional[np.ndarray] = None
     exact: Optional[Callable[[float], np.ndarray]] = None
 
     @property
     def zones(self) -> int:
         return int(self.n[0] * self.n[1] * self.n[2])
+
+
+# electron heating models (the five of the paper's list, and a constant share)
+ELEC_OFF, ELEC_CONSTANT, ELEC_KAWAZURA, ELEC_WERNER, ELEC_ROWAN, ELEC_SHARMA, ELEC_HOWES = range(7)
+
+
+def with_electrons(pr, model, game=4.0 / 3.0, gamp=5.0 / 3.0, fel=0.5, tpte_min=1e-3,
+                   tpte_max=1e3, ue_frac=0.1, K=None):
+    """A copy of `pr` that evolves the electron entropies.  Initial data:
+    kappa_tot = (gamma - 1) u / rho^gamma and electrons holding the fraction
+    ue_frac of the internal energy, kappa_e = (gamma_e - 1) ue_frac u /
+    rho^gamma_e (or K as given).  Problems with FIXED ghosts get the same
+    recipe on their ghost zones (info["K_ghost"])."""
+    def kappa(P):
+        rho, u = P[0], P[1]
+        return np.stack([(pr.gamma - 1.0) * u / rho ** pr.gamma,
+                         (game - 1.0) * ue_frac * u / rho ** game])
+    info = dict(pr.info)
+    Pg = info.get("P_ghost")
+    if Pg is not None:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            Kg = np.nan_to_num(kappa(Pg))
+        info["K_ghost"] = Kg
+    el = dict(model=int(model), game=float(game), gamp=float(gamp), fel=float(fel),
+              tpte_min=float(tpte_min), tpte_max=float(tpte_max))
+    return dataclasses.replace(pr, electrons=el, K=kappa(pr.P) if K is None else K, info=info)
 
 
 # --------------------------------------------------------------------------

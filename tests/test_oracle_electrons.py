@@ -1,0 +1,214 @@
+"""Pins of the oracle's electron thermodynamics: the partition of dissipation
+between ions and electrons (Ressler et al. 2015) with the five heating
+models the paper lists, and the electron bounds.
+
+* Heating fractions: each published fit at its closed-form limits -- the
+  ion-to-electron ratios of Kawazura et al. (35 at high beta), Howes (0.92
+  sqrt(m_p/m_e) at high beta and equal temperatures), Sharma et al. (1/3
+  sqrt(T_e/T_p)); Werner et al. between 1/4 (unmagnetised) and 1/2 (sigma ->
+  infinity); Rowan et al. 1/2 at beta = beta_max, e^-1/2 cold and
+  unmagnetised -- electrons taking everything at low beta, monotonic trends,
+  and 0 <= f_e <= 1 on random states.
+* One heating update gives the electrons the share f_e of the dissipated
+  internal energy density.
+* With f_e = 0 the electron entropy is a passive scalar: its conserved
+  total is constant on a periodic grid.  With f_e = 1, gamma_e = gamma and
+  kappa_e = kappa_tot, the electrons carry the whole fluid entropy.
+* Electrons leave the fluid untouched unless the entropy bound acts, and on
+  exit every zone satisfies the bounds (P_gas/rho^gamma <= 3, T_p/T_e in
+  range).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_10191_gb300 import problems as pb
+
+GAM, GAME, GAMP = 4.0 / 3.0, 4.0 / 3.0, 5.0 / 3.0
+MP_ME = 1836.15267343
+
+
+def _fel(model, rho, u, kel, bsq, fel=0.5, gam=GAM, game=GAME, gamp=GAMP):
+    return oracle.elec_fraction(model, gam, game, gamp, fel, rho, u, kel, bsq)
+
+
+def _equal_temperatures(rho=1.0, kel=0.01, game=GAME, gamp=GAMP):
+    """u with T_p = T_e for kappa_e = kel: T_e = kel rho^(game-1) and
+    u = rho T/(gamma_e - 1) + rho T/(gamma_p - 1)."""
+    T = kel * rho ** (game - 1)
+    return rho * T / (game - 1) + rho * T / (gamp - 1)
+
+
+def test_kawazura_limits():
+    u = _equal_temperatures()
+    lo_beta = _fel(oracle.ELEC_KAWAZURA, 1.0, u, 0.01, 1e8)     # beta ~ 1e-10
+    hi_beta = _fel(oracle.ELEC_KAWAZURA, 1.0, u, 0.01, 1e-14)   # beta ~ 1e12
+    assert lo_beta == pytest.approx(1.0, abs=1e-9)
+    assert hi_beta == pytest.approx(1.0 / 36.0, rel=1e-12)
+    fs = [_fel(oracle.ELEC_KAWAZURA, 1.0, u, 0.01, b) for b in np.logspace(3, -8, 40)]
+    assert all(a >= b for a, b in zip(fs, fs[1:]))  # falls as beta grows
+
+
+def test_howes_limits():
+    u = _equal_temperatures()
+    assert _fel(oracle.ELEC_HOWES, 1.0, u, 0.01, 1e8) == pytest.approx(1.0, abs=1e-12)
+    hi = _fel(oracle.ELEC_HOWES, 1.0, u, 0.01, 1e-14)
+    assert hi == pytest.approx(1.0 / (1.0 + 0.92 * math.sqrt(MP_ME)), rel=1e-9)
+    fs = [_fel(oracle.ELEC_HOWES, 1.0, u, 0.01, b) for b in np.logspace(3, -8, 40)]
+    assert all(a >= b for a, b in zip(fs, fs[1:]))
+
+
+def test_sharma_limits():
+    u = _equal_temperatures()
+    assert _fel(oracle.ELEC_SHARMA, 1.0, u, 0.01, 0.3) == pytest.approx(0.33 / 1.33, rel=1e-12)
+    # T_p = 4 T_e: Q_e/Q_i = 0.33/2
+    T = 0.01
+    u4 = T / (GAME - 1) + 4 * T / (GAMP - 1)
+    assert _fel(oracle.ELEC_SHARMA, 1.0, u4, 0.01, 0.3) == pytest.approx(0.165 / 1.165, rel=1e-12)
+
+
+def test_werner_limits():
+    assert _fel(oracle.ELEC_WERNER, 1.0, 0.1, 0.01, 0.0) == 0.25
+    assert _fel(oracle.ELEC_WERNER, 1.0, 0.1, 0.01, 1e14) == pytest.approx(0.5, rel=1e-12)
+    fs = [_fel(oracle.ELEC_WERNER, 1.0, 0.1, 0.01, b) for b in np.logspace(-6, 8, 40)]
+    assert all(a <= b for a, b in zip(fs, fs[1:]))  # rises with sigma
+
+
+def test_rowan_limits():
+    # hot plasma: beta_p >= beta_max, f_e = 1/2
+    assert _fel(oracle.ELEC_ROWAN, 1.0, 100.0, 1e-3, 0.5) == 0.5
+    # cold and unmagnetised: beta_p/beta_max -> 0, sigma_w = 0
+    assert _fel(oracle.ELEC_ROWAN, 1.0, 1e-8, 1e-12, 0.0) == pytest.approx(0.5 / math.e, rel=1e-6)
+    # cold and strongly magnetised: the exponent vanishes
+    assert _fel(oracle.ELEC_ROWAN, 1.0, 1e-8, 1e-12, 1e12) == pytest.approx(0.5, rel=1e-6)
+
+
+def test_fractions_bounded():
+    rng = np.random.default_rng(3)
+    for model in (oracle.ELEC_KAWAZURA, oracle.ELEC_WERNER, oracle.ELEC_ROWAN,
+                  oracle.ELEC_SHARMA, oracle.ELEC_HOWES):
+        for _ in range(300):
+            rho = 10 ** rng.uniform(-8, 1)
+            u = rho * 10 ** rng.uniform(-6, 2)
+            ue = u * 10 ** rng.uniform(-6, 0)
+            kel = (GAME - 1) * ue / rho ** GAME
+            bsq = rho * 10 ** rng.uniform(-10, 4) if rng.uniform() < 0.9 else 0.0
+            f = _fel(model, rho, u, kel, bsq)
+            assert 0.0 <= f <= 1.0 and math.isfinite(f), (model, rho, u, kel, bsq, f)
+    assert _fel(oracle.ELEC_CONSTANT, 1, 1, 1, 1, fel=0.3) == 0.3
+
+
+def test_heating_gives_the_electrons_their_share():
+    """rho^gamma_e dkappa_e/(gamma_e - 1) = f_e rho^gamma dkappa_tot/(gamma - 1)."""
+    rng = np.random.default_rng(4)
+    for game in (4.0 / 3.0, 1.4, 5.0 / 3.0):
+        for _ in range(200):
+            rho = 10 ** rng.uniform(-6, 0)
+            kt_adv = 10 ** rng.uniform(-3, 0)
+            kt_new = kt_adv * (1 + 10 ** rng.uniform(-8, 0))
+            kel_adv = 10 ** rng.uniform(-4, 0)
+            f = rng.uniform()
+            kel = oracle.elec_heat(GAM, game, rho, f, kt_new, kt_adv, kel_adv)
+            due = rho ** game * (kel - kel_adv) / (game - 1)
+            du = rho ** GAM * (kt_new - kt_adv) / (GAM - 1)
+            assert due == pytest.approx(f * du, rel=1e-10, abs=1e-15 * rho ** game * kel / (game - 1))
+
+
+def _golden_ktot_max():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "floors.txt")) as f:
+        for line in f:
+            if line.startswith("ktot_max"):
+                return float(line.split()[1])
+    raise KeyError("ktot_max")
+
+
+def _ot(n=24, **kw):
+    pr = pb.orszag_tang(n, recon=pb.RECON_WENO5)
+    return pb.with_electrons(pr, **kw)
+
+
+def _conserved_kel(o, pr):
+    """sum of rho u^t kappa_e over the grid (flat space: u^t = gamma)."""
+    P = o.get_prims()
+    K = o.get_K()
+    gam = np.sqrt(1 + (P[2:5] ** 2).sum(axis=0))
+    return float((P[0] * gam * K[1]).sum()), float((P[0] * gam).sum())
+
+
+def test_passive_electron_entropy_is_conserved():
+    pr = _ot(model=oracle.ELEC_CONSTANT, fel=0.0, tpte_min=0.0, tpte_max=math.inf)
+    K = pr.K.copy()
+    n = pr.n[0]
+    x = (np.arange(n) + 0.5) / n
+    K[1] *= 1 + 0.5 * np.sin(2 * np.pi * x)[None, None, :] * np.cos(2 * np.pi * x)[None, :, None]
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.set_K(K)
+    k0, m0 = _conserved_kel(o, pr)
+    o.step(4)
+    k1, m1 = _conserved_kel(o, pr)
+    assert m1 == pytest.approx(m0, rel=1e-13)
+    assert k1 == pytest.approx(k0, rel=1e-13)
+    # and it moved: the electron entropy is not frozen
+    assert not np.allclose(o.get_K()[1], K[1], rtol=1e-6, atol=0)
+
+
+def test_uniform_electron_entropy_stays_uniform():
+    """The entropies ride with the mass: a uniform kappa_e (f_e = 0) stays
+    uniform while the flow compresses and shears it."""
+    pr = _ot(model=oracle.ELEC_CONSTANT, fel=0.0, tpte_min=0.0, tpte_max=math.inf)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.set_K(pr.K)
+    o.step(4)
+    k = o.get_K()[1]
+    assert np.abs(k - pr.K[1]).max() <= 1e-13 * np.abs(pr.K[1]).max()
+    assert not np.allclose(o.get_prims()[0], pr.P[0], rtol=1e-6, atol=0)
+
+
+def test_electrons_carry_all_entropy_when_they_take_all_the_heat():
+    pr = pb.orszag_tang(24, recon=pb.RECON_WENO5)
+    pr = pb.with_electrons(pr, model=oracle.ELEC_CONSTANT, fel=1.0, game=pr.gamma, tpte_min=0.0,
+                           tpte_max=math.inf)
+    K0 = pr.K.copy()
+    K0[1] = K0[0]
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.set_K(K0)
+    o.step(6)
+    K = o.get_K()
+    assert np.abs(K[1] - K[0]).max() <= 1e-12 * np.abs(K[0]).max()
+    # the OT vortex dissipates: the entropy rose somewhere
+    assert (K[0] > K0[0] * (1 + 1e-6)).any()
+
+
+def test_electrons_leave_the_fluid_alone_and_bounds_hold():
+    base = pb.fm_torus(24, 20, 8)
+    el = pb.with_electrons(base, model=oracle.ELEC_KAWAZURA)
+    out = {}
+    for pr in (base, el):
+        o = oracle.Oracle(pr)
+        o.set_prims(pr.P)
+        if pr.electrons:
+            o.set_K(pr.K)
+        o.predictor()
+        out[bool(pr.electrons)] = (o.get_prims(), o.flags(), o.get_K() if pr.electrons else None)
+    (P0, (pf0, ff0), _), (P1, (pf1, ff1), K) = out[False], out[True]
+    assert np.array_equal(pf0, pf1)
+    quiet = (ff1 & oracle.FF_KTOT) == 0
+    assert quiet.sum() > 0.5 * quiet.size
+    # the entropy bound acts per zone; elsewhere the fluid is bitwise the same
+    assert np.array_equal(P0[:, quiet & (pf0 == 0)], P1[:, quiet & (pf0 == 0)])
+    rho, u = P1[0], P1[1]
+    e = el.electrons
+    kt = (GAM - 1) * u / rho ** GAM
+    assert np.all(kt <= _golden_ktot_max() * (1 + 1e-14))
+    assert np.allclose(K[0], kt, rtol=1e-14, atol=0)
+    Te = K[1] * rho ** (e["game"] - 1)
+    ue = K[1] * rho ** e["game"] / (e["game"] - 1)
+    Tp = (e["gamp"] - 1) * (u - ue) / rho
+    r = Tp / Te
+    assert np.all(r >= e["tpte_min"] * (1 - 1e-12)) and np.all(r <= e["tpte_max"] * (1 + 1e-12))
