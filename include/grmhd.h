@@ -84,6 +84,49 @@ typedef struct {
   double a, hslope;
 } grmhd_metric;
 
+/* Electron thermodynamics (paper, "Implementation Notes": the optional
+ * tracking and partition of dissipation between ions and electrons of
+ * Ressler et al. 2015, with five heating models).  The total entropy
+ * kappa_tot = P_gas/rho^gamma and the electron entropy kappa_e =
+ * P_e/rho^gamma_e are carried with the mass (conserved sqrt(-g) rho u^t
+ * kappa, fluxes from kappa reconstructed like the primitives and combined
+ * by the same local Lax-Friedrichs rule).  After each stage's inversion the
+ * dissipation kappa_tot(u) - kappa_tot,carried heats the electrons by the
+ * share f_e of the chosen model, evaluated on the stage's source state:
+ * kappa_e += f_e (gamma_e - 1)/(gamma - 1) rho_s^(gamma - gamma_e) x that
+ * difference.  The fluid's bounds follow; then u is lowered to keep
+ * P_gas/rho^gamma <= 3 (with the bounds on), kappa_tot is reset to the
+ * state's and kappa_e is held to tpte_min <= T_p/T_e <= tpte_max.  A failed
+ * zone takes the neighbour mean of kappa_e.  Every heating model: f_e =
+ * 1/(1 + Q_i/Q_e), T_e, T_p from kappa_e and u, beta_p = rho T_p / (b^2/2),
+ * T_p/T_e clamped to [1e-20, 1e20], beta_p to [1e-20, 1e20]:
+ *   KAWAZURA  Q_i/Q_e = 35/(1 + (beta_p/15)^-1.4 exp(-0.1 T_e/T_p))
+ *   WERNER    f_e = (1 + sqrt((s/5)/(2 + s/5)))/4, s = b^2/rho
+ *   ROWAN     f_e = exp(-(1 - beta_p/beta_max)^3.3/(1 + 1.2 s_w^0.7))/2,
+ *             s_w = b^2/(rho + u + p), beta_max = 1/(4 s_w), beta_p <= beta_max
+ *   SHARMA    Q_e/Q_i = 0.33 sqrt(T_e/T_p)
+ *   HOWES     Q_i/Q_e = 0.92 (c2^2 + beta_p^x)/(c3^2 + beta_p^x)
+ *             sqrt(m_p T_p/(m_e T_e)) exp(-1/beta_p), x = 2 - 0.2 log10(T_p/T_e),
+ *             c2 = 1.6 T_e/T_p, c3 = 18 + 5 log10(T_p/T_e) (T_p > T_e), else
+ *             c2 = 1.2 T_e/T_p, c3 = 18
+ *   CONSTANT  f_e = fel (not one of the paper's models; for tests)
+ * Only FP64 grids evolve electrons (GRMHD_PREC_FP64); decomposed grids and
+ * the server take none. */
+#define GRMHD_ELEC_OFF 0
+#define GRMHD_ELEC_CONSTANT 1
+#define GRMHD_ELEC_KAWAZURA 2
+#define GRMHD_ELEC_WERNER 3
+#define GRMHD_ELEC_ROWAN 4
+#define GRMHD_ELEC_SHARMA 5
+#define GRMHD_ELEC_HOWES 6
+
+typedef struct {
+  int model;                  /* GRMHD_ELEC_*; 0 (zero-initialised): off */
+  double game, gamp;          /* adiabatic indices of electrons and protons (> 1) */
+  double fel;                 /* GRMHD_ELEC_CONSTANT's share, in [0, 1] */
+  double tpte_min, tpte_max;  /* 0 <= tpte_min <= tpte_max (may be +inf) */
+} grmhd_electrons;
+
 /* gamma: adiabatic index; cfl: Courant number; t_final > 0 clamps the last
  * step to land on it (steps after it do nothing); recon: GRMHD_RECON_*;
  * floors_on: apply the paper's bounds (needs the MKS radius); bc[d][side]:
@@ -97,6 +140,7 @@ typedef struct {
   int bc[3][2];
   int precision;
   int floor_frame; /* GRMHD_FLOOR_*: where the bounds add mass and energy */
+  grmhd_electrons electrons; /* electron entropies (model 0: not evolved) */
 } grmhd_params;
 
 /* Frame of the bounds (the paper lists the bounds, not the frame in which
@@ -110,6 +154,7 @@ typedef struct {
  * either frame. */
 #define GRMHD_FLOOR_FLUID 0
 #define GRMHD_FLOOR_DRIFT 1
+
 
 /* Running statistics of a simulation (totals over all stages so far). */
 typedef struct {
@@ -141,6 +186,14 @@ int grmhd_set_prims_ghost(grmhd_sim *sim, const double *P, int on_device);
 
 /* Read the primitives, interior ([8][n3][n2][n1]) or with ghosts. */
 int grmhd_get_prims(grmhd_sim *sim, double *P, int with_ghosts, int on_device);
+
+/* The electron entropies (kappa_tot, kappa_e) of a simulation created with
+ * electrons: K is [2][n3][n2][n1] (with_ghosts = 0; the ghosts are then
+ * filled by the boundary conditions, FIXED ghosts kept) or [2][n3+6][n2+6]
+ * [n1+6] (with_ghosts = 1); set them after the primitives.
+ * GRMHD_ERR_INVALID: no electrons. */
+int grmhd_set_electrons(grmhd_sim *sim, const double *K, int with_ghosts, int on_device);
+int grmhd_get_electrons(grmhd_sim *sim, double *K, int with_ghosts, int on_device);
 
 /* Advance nsteps full predictor-corrector steps, enqueued on the stream.
  * stats == NULL: returns after enqueueing (errors of this call surface at

@@ -79,8 +79,10 @@ static void free_all(grmhd_sim *s) {
     s->ev_pool = nullptr;
   }
   plan_free(s->plan);
-  double *d[] = {s->P, s->Ph, s->F[0], s->F[1], s->F[2], s->emf, s->Lf, s->Rf, s->Uc, s->geom,
-                 s->conn, s->floors};
+  double *d[] = {s->P,      s->Ph,    s->F[0], s->F[1], s->F[2],  s->emf,
+                 s->Lf,     s->Rf,    s->Uc,   s->geom, s->conn,  s->floors,
+                 s->K,      s->Kh,    s->FK[0], s->FK[1], s->FK[2], s->Uek,
+                 s->ctop_face};
   for (double *p : d)
     if (p) cudaFree(p);
   if (s->Pf) cudaFree(s->Pf);
@@ -123,6 +125,14 @@ int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const g
   if (params->floors_on && metric->kind != GRMHD_METRIC_MKS_KERR) return GRMHD_ERR_INVALID;
   if (params->floor_frame != GRMHD_FLOOR_FLUID && params->floor_frame != GRMHD_FLOOR_DRIFT)
     return GRMHD_ERR_INVALID;
+  const grmhd_electrons &e = params->electrons;
+  if (e.model < GRMHD_ELEC_OFF || e.model > GRMHD_ELEC_HOWES) return GRMHD_ERR_INVALID;
+  if (e.model != GRMHD_ELEC_OFF) {
+    if (params->precision != GRMHD_PREC_FP64) return GRMHD_ERR_INVALID;
+    if (!(e.game > 1.0) || !(e.gamp > 1.0)) return GRMHD_ERR_INVALID;
+    if (!(e.tpte_min >= 0.0) || !(e.tpte_max >= e.tpte_min)) return GRMHD_ERR_INVALID;
+    if (e.model == GRMHD_ELEC_CONSTANT && !(e.fel >= 0.0 && e.fel <= 1.0)) return GRMHD_ERR_INVALID;
+  }
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) {
       const int b = params->bc[d][sd];
@@ -136,8 +146,10 @@ int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const g
   return GRMHD_OK;
 }
 
+// (grids with electrons take the full extent: their entropy fluxes are not
+// replicated)
 static int flat3_of(const Dims &D, const grmhd_params *params) {
-  return (D.n[2] == 1 && params->bc[2][0] == GRMHD_BC_PERIODIC) ? 1 : 0;
+  return (D.n[2] == 1 && params->bc[2][0] == GRMHD_BC_PERIODIC && !params->electrons.model) ? 1 : 0;
 }
 
 extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metric,
@@ -155,8 +167,11 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
     b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
   if (params->precision == GRMHD_PREC_FF)
     b += 2 * sizeof(float) * (NV * tot + (NLOC * G_NCOMP + C_NCOMP) * n2d);
+  if (params->electrons.model)  // K, Kh, FK[3] (2 each), Uek, ctop_face (3)
+    b += sizeof(double) * 14 * tot;
   b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision,
-                         params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT);
+                         params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT,
+                         params->electrons.model != GRMHD_ELEC_OFF);
   *bytes = b;
   return GRMHD_OK;
 }
@@ -218,6 +233,14 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
     ok = cudaMalloc(&s->Pff, 2 * sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
          cudaMalloc(&s->geomff, 2 * sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
          cudaMalloc(&s->connff, 2 * sizeof(float) * C_NCOMP * (size_t)D.n2d) == cudaSuccess;
+  const bool elec = params->electrons.model != GRMHD_ELEC_OFF;
+  const size_t kb = sizeof(double) * 2 * (size_t)tot;
+  if (ok && elec)
+    ok = cudaMalloc(&s->K, kb) == cudaSuccess && cudaMalloc(&s->Kh, kb) == cudaSuccess &&
+         cudaMalloc(&s->FK[0], kb) == cudaSuccess && cudaMalloc(&s->FK[1], kb) == cudaSuccess &&
+         cudaMalloc(&s->FK[2], kb) == cudaSuccess &&
+         cudaMalloc(&s->Uek, sizeof(double) * (size_t)tot) == cudaSuccess &&
+         cudaMalloc(&s->ctop_face, sizeof(double) * 3 * (size_t)tot) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -226,6 +249,9 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   }
   int rc = GRMHD_OK;
   cudaStream_t st = s->st;
+  if (elec)
+    for (double *q : {s->K, s->Kh, s->FK[0], s->FK[1], s->FK[2]})
+      if (cudaMemsetAsync(q, 0, kb, st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
   // zero every field so that entries outside the computed ranges read as 0
   if (cudaMemsetAsync(s->P, 0, fb, st) != cudaSuccess || cudaMemsetAsync(s->Ph, 0, fb, st) != cudaSuccess ||
       cudaMemsetAsync(s->F[0], 0, fb, st) != cudaSuccess || cudaMemsetAsync(s->F[1], 0, fb, st) != cudaSuccess ||
@@ -278,6 +304,13 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   A.recon = params->recon;
   A.floors_on = params->floors_on;
   A.floor_drift = params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT;
+  A.elec = params->electrons.model;
+  A.game = params->electrons.game;
+  A.gamp = params->electrons.gamp;
+  A.fel_const = params->electrons.fel;
+  A.tpte_min = params->electrons.tpte_min;
+  A.tpte_max = params->electrons.tpte_max;
+  A.ctop_face = s->ctop_face;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
   A.flat3 = flat3_of(D, params);
@@ -309,6 +342,10 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   it.Pff = s->Pff;
   it.geomff = s->geomff;
   it.prec = params->precision;
+  it.K = s->K;
+  it.Kh = s->Kh;
+  for (int d = 0; d < 3; d++) it.FK[d] = s->FK[d];
+  it.Uek = s->Uek;
   rc = plan_build(s->plan, &it, 1);
   if (rc != GRMHD_OK) {
     free_all(s);
@@ -351,6 +388,9 @@ static int set_common(grmhd_sim *s, const double *P, int on_device, int ghost) {
   // the ghosts of a fixed side keep their set values in both stage arrays
   CK(cudaMemcpyAsync(s->Ph, s->P, sizeof(double) * NV * (size_t)D.ntot, cudaMemcpyDeviceToDevice,
                      s->st));
+  if (s->K)
+    CK(cudaMemcpyAsync(s->Kh, s->K, sizeof(double) * 2 * (size_t)D.ntot, cudaMemcpyDeviceToDevice,
+                       s->st));
   int rc = launched();
   if (rc != GRMHD_OK) return rc;
   if (!on_device) CK(cudaStreamSynchronize(s->st));
@@ -363,6 +403,48 @@ extern "C" int grmhd_set_prims(grmhd_sim *s, const double *P, int on_device) {
 
 extern "C" int grmhd_set_prims_ghost(grmhd_sim *s, const double *P, int on_device) {
   return set_common(s, P, on_device, 1);
+}
+
+extern "C" int grmhd_set_electrons(grmhd_sim *s, const double *K, int with_ghosts, int on_device) {
+  if (!s || !K || !s->K) return GRMHD_ERR_INVALID;
+  const Dims &D = s->D;
+  const long long nz = (long long)D.n[0] * D.n[1] * D.n[2];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (with_ghosts) {
+    CK(cudaMemcpyAsync(s->K, K, sizeof(double) * 2 * (size_t)D.ntot, kind, s->st));
+  } else {
+    CK(cudaMemcpyAsync(s->Kh, K, sizeof(double) * 2 * (size_t)nz, kind, s->st));  // scratch
+    launch_pack(D, s->Kh, s->K, 1, s->st, 2);
+  }
+  {
+    SimHook h(s);
+    plan_bounds(s->plan, 0, s->st, &h);  // refills the primitives' ghosts too (unchanged)
+  }
+  CK(cudaMemcpyAsync(s->Kh, s->K, sizeof(double) * 2 * (size_t)D.ntot, cudaMemcpyDeviceToDevice,
+                     s->st));
+  CK(cudaMemcpyAsync(s->Ph, s->P, sizeof(double) * NV * (size_t)D.ntot, cudaMemcpyDeviceToDevice,
+                     s->st));
+  int rc = launched();
+  if (rc != GRMHD_OK) return rc;
+  if (!on_device) CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
+}
+
+extern "C" int grmhd_get_electrons(grmhd_sim *s, double *K, int with_ghosts, int on_device) {
+  if (!s || !K || !s->K) return GRMHD_ERR_INVALID;
+  const Dims &D = s->D;
+  const long long nz = (long long)D.n[0] * D.n[1] * D.n[2];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (with_ghosts) {
+    CK(cudaMemcpyAsync(K, s->K, sizeof(double) * 2 * (size_t)D.ntot, kind, s->st));
+  } else {
+    launch_pack(D, s->K, s->Kh, 0, s->st, 2);
+    int rc = launched();
+    if (rc != GRMHD_OK) return rc;
+    CK(cudaMemcpyAsync(K, s->Kh, sizeof(double) * 2 * (size_t)nz, kind, s->st));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(s->st));
+  return GRMHD_OK;
 }
 
 extern "C" int grmhd_get_prims(grmhd_sim *s, double *P, int with_ghosts, int on_device) {
@@ -444,6 +526,9 @@ extern "C" int grmhd_predictor(grmhd_sim *s) {
   // P <- P^{n+1/2} (ghosts included)
   CK(cudaMemcpyAsync(s->P, s->Ph, sizeof(double) * NV * (size_t)s->D.ntot, cudaMemcpyDeviceToDevice,
                      s->st));
+  if (s->K)
+    CK(cudaMemcpyAsync(s->K, s->Kh, sizeof(double) * 2 * (size_t)s->D.ntot,
+                       cudaMemcpyDeviceToDevice, s->st));
   return read_stats(s, nullptr, true);
 }
 

@@ -160,6 +160,7 @@ extern "C" int grmhd_decomp_create(const grmhd_grid *grid, const grmhd_metric *m
   Dims G;
   int rc = validate_problem(grid, metric, params, &G);
   if (rc != GRMHD_OK) return rc;
+  if (params->electrons.model != GRMHD_ELEC_OFF) return GRMHD_ERR_INVALID;  // not exchanged
   for (int d = 0; d < 3; d++) {
     if (nblocks[d] < 1 || nblocks[d] > G.n[d]) return GRMHD_ERR_INVALID;
     if (nblocks[d] > 1 && G.n[d] / nblocks[d] < NG) return GRMHD_ERR_INVALID;  // blocks >= NG zones

@@ -627,7 +627,7 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
       if (v == RHO || v == UU) pd[v] *= sc.s;
       if (v >= B1) pd[v] *= sc.rs;
     }
-    if (pf == PF_OK && A.floors_on && !A.floor_drift) {
+    if (pf == PF_OK && A.floors_on && !A.floor_drift && !A.elec) {
       const double rho_fl = __ldg(A.floors + ij), u_fl = __ldg(A.floors + D.n2d + ij);
       const double lor = ff_to(lor_n);
       if (lor > FL_GAMMA) {  // the Lorentz-factor cap needs the FP64 fluid state

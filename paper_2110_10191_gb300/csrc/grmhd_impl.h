@@ -39,6 +39,11 @@ struct StepArgs {
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   int floor_drift;  // bounds in the drift frame: a separate pass after the update
+  // electron entropies (GRMHD_ELEC_* model, 0: off): adiabatic indices of
+  // electrons and protons, the constant share, the bounds on T_p/T_e
+  int elec;
+  double game, gamp, fel_const, tpte_min, tpte_max;
+  double *ctop_face;  // electrons: the LLF speed of every face, [3][ntot]
   int flat3;  // n3 = 1 with periodic X3: fluxes on the single k layer, copied
   // sides that continue into a neighbouring block of a decomposed grid (1)
   // rather than ending at a physical boundary (0): the fixup may average
@@ -84,6 +89,8 @@ void launch_to_ff(long long n, const double *src, float *dst, cudaStream_t st);
 // corners' zones, as double bit patterns into out[2] (device)
 void launch_divb(const StepArgs &A, const double *P, unsigned long long *out, cudaStream_t st);
 // pack interior <-> ghost layout
-void launch_pack(const Dims &D, const double *src, double *dst, int to_ghost, cudaStream_t st);
+// nvar variables of ntot (interior <-> with ghosts)
+void launch_pack(const Dims &D, const double *src, double *dst, int to_ghost, cudaStream_t st,
+                 int nvar = NV);
 
 }  // namespace grmhd

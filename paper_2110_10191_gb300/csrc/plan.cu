@@ -10,6 +10,7 @@
 #include "grmhd_impl.h"
 #include "ff_bodies.cuh"
 #include "mixed_bodies.cuh"
+#include "elec_bodies.cuh"
 #include "plan.h"
 #include "step_bodies.cuh"
 
@@ -29,6 +30,10 @@ __device__ __forceinline__ long long block_tid(const BView &V, int) {
 }
 // the stage arrays: 0 = P, 1 = Ph
 __device__ __forceinline__ double *arr(const StageItem &it, int which) { return which ? it.Ph : it.P; }
+// their electron entropies (null without electrons)
+__device__ __forceinline__ double *karr(const StageItem &it, int which) {
+  return it.A.elec ? (which ? it.Kh : it.K) : nullptr;
+}
 
 template <int X>
 __global__ void kp_bounds(BView V, int which) {
@@ -36,9 +41,10 @@ __global__ void kp_bounds(BView V, int which) {
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
   double *P = arr(it, which);
-  if (X == 0) bounds_x1_body(it.A, P, t);
-  if (X == 1) bounds_x2_body(it.A, P, t);
-  if (X == 2) bounds_x3_body(it.A, P, t);
+  double *K = karr(it, which);
+  if (X == 0) bounds_x1_body(it.A, P, K, t);
+  if (X == 1) bounds_x2_body(it.A, P, K, t);
+  if (X == 2) bounds_x3_body(it.A, P, K, t);
 }
 
 template <int DIR>
@@ -129,7 +135,9 @@ __global__ void kp_replicate(BView V) {
 __global__ void kp_fix(BView V) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
-  fix_flux_body(it.A, it.F[0], it.F[1], block_tid(V, g));
+  const bool e = it.A.elec != 0;
+  fix_flux_body(it.A, it.F[0], it.F[1], e ? it.FK[0] : nullptr, e ? it.FK[1] : nullptr,
+                block_tid(V, g));
 }
 
 __global__ void kp_emf(BView V) {
@@ -159,6 +167,28 @@ __global__ void __maxnreg__(128) kp_update_ff(BView V, int in, double dtfac, int
   const StageItem &it = V.items[g];
   update_ff_body(it.A, it.P, arr(it, in), arr(it, 1 - in), it.F[0], it.F[1], it.F[2], it.pflag,
                  it.fflag, dtfac, it.Uc, ucache_mode, block_tid(V, g));
+}
+
+template <int DIR>
+__global__ void kp_elec_flux(BView V, int in) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  elec_flux_body<DIR>(it.A, karr(it, in), it.Lf, it.Rf, it.FK[DIR], block_tid(V, g));
+}
+
+// stage in: P_s = arr(in), output arr(1 - in); kappa_i is always K (of P^n)
+__global__ void kp_elec_post(BView V, int in, double dtfac) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  elec_post_body(it.A, arr(it, in), arr(it, 1 - in), it.F[0], it.F[1], it.F[2], it.FK[0],
+                 it.FK[1], it.FK[2], it.K, karr(it, in), karr(it, 1 - in), it.Uek, it.pflag,
+                 it.fflag, dtfac, in, block_tid(V, g));
+}
+
+__global__ void kp_elec_fix(BView V, int out) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  elec_fix_body(it.A, arr(it, out), karr(it, out), it.pflag, it.fflag, block_tid(V, g));
 }
 
 __global__ void kp_floor_drift(BView V, int out) {
@@ -253,7 +283,7 @@ int upload_tables(Plan &p) {
 
 }  // namespace
 
-void plan_counts(const Dims &D, int flat3, int prec, int drift, long long c[PC_N]) {
+void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long long c[PC_N]) {
   const int fl = flat3;
   const bool f64 = prec == GRMHD_PREC_FP64, mx = prec == GRMHD_PREC_MIXED, fx = prec == GRMHD_PREC_FF;
   c[PC_BX1] = n_bounds_x1(D);
@@ -278,12 +308,14 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, long long c[PC_N
   c[PC_ZONE] = n_zone(D);
   c[PC_UPD64] = fx ? 0 : n_zone(D);
   c[PC_UPDX] = fx ? n_zone(D) : 0;
-  c[PC_FLOORD] = drift ? n_zone(D) : 0;
+  c[PC_FLOORD] = (drift && !elec) ? n_zone(D) : 0;
+  for (int d = 0; d < 3; d++) c[PC_EFACE0 + d] = elec ? n_face(D, d, fl) : 0;
+  c[PC_EZONE] = elec ? n_zone(D) : 0;
 }
 
-long long plan_bytes(const Dims &D, int flat3, int prec, int drift) {
+long long plan_bytes(const Dims &D, int flat3, int prec, int drift, int elec) {
   long long c[PC_N], ints = 0;
-  plan_counts(D, flat3, prec, drift, c);
+  plan_counts(D, flat3, prec, drift, elec, c);
   for (int q = 0; q < PC_N; q++) ints += 2 * nblk(c[q], 64);
   return (long long)sizeof(StageItem) + 4 * ints;
 }
@@ -302,7 +334,8 @@ int plan_build(Plan &p, const StageItem *items, int n) {
   long long zones = 0, cap = 0;
   for (int g = 0; g < n; g++) {
     long long c[PC_N];
-    plan_counts(items[g].A.D, items[g].A.flat3, items[g].prec, items[g].A.floor_drift, c);
+    plan_counts(items[g].A.D, items[g].A.flat3, items[g].prec, items[g].A.floor_drift,
+                items[g].A.elec, c);
     for (int q = 0; q < PC_N; q++) {
       p.count[(size_t)q * n + g] = c[q];
       cap += 2 * nblk(c[q], 64);  // the smallest block the tuner tries
@@ -371,12 +404,17 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   int nl = plan_clock(p, 0, st, h);
   const int R = GRMHD_K_RECON, F = GRMHD_K_FLUX;
   // FP64 grids
+  // (electron entropy fluxes of each direction right after its face fluxes,
+  // before the next reconstruction overwrites the face states)
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<2><<<nb, bs, 0, st>>>(V, in); });
   // mixed-precision grids
   nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_f32<<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });
@@ -418,12 +456,18 @@ int plan_update_only(const Plan &p, int in, double dtfac, int ucache_mode, cudaS
   nl += launch(p, PC_FLOORD, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
     kp_floor_drift<<<nb, bs, 0, st>>>(V, 1 - in);
   });
+  nl += launch(p, PC_EZONE, GRMHD_K_UPDATE, h, [&](unsigned nb, unsigned bs, BView V) {
+    kp_elec_post<<<nb, bs, 0, st>>>(V, in, dtfac);
+  });
   return nl;
 }
 
 int plan_fixup(const Plan &p, int out, cudaStream_t st, PlanHook *h) {
-  return launch(p, PC_ZONE, GRMHD_K_FIXUP, h,
-                [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, out); });
+  int nl = launch(p, PC_ZONE, GRMHD_K_FIXUP, h,
+                  [&](unsigned nb, unsigned bs, BView V) { kp_fixup<<<nb, bs, 0, st>>>(V, out); });
+  nl += launch(p, PC_EZONE, GRMHD_K_FIXUP, h,
+               [&](unsigned nb, unsigned bs, BView V) { kp_elec_fix<<<nb, bs, 0, st>>>(V, out); });
+  return nl;
 }
 
 int plan_update(const Plan &p, int in, double dtfac, int ucache_mode, cudaStream_t st, PlanHook *h) {

@@ -26,6 +26,9 @@ struct StageItem {
   float *Pff;          // float-float: split primitives ([2][8][ntot])
   const float *geomff; // float-float: split geometry ([2][NLOC][G_NCOMP][n2d])
   int prec;            // GRMHD_PREC_*: the flux stage's arithmetic
+  // electrons (A.elec): (kappa_tot, kappa_e) of the stage arrays ([2][ntot]
+  // each, with P and Ph), their fluxes, and U_rho(P^n) kept by the predictor
+  double *K, *Kh, *FK[3], *Uek;
 };
 
 // launch classes, each with its own block table
@@ -56,7 +59,11 @@ enum {
   PC_ZONE,   // fixup (every grid)
   PC_UPD64,  // FP64 update (FP64 and mixed-precision grids)
   PC_UPDX,   // float-float update (float-float grids)
-  PC_FLOORD, // drift-frame bounds (grids with bounds in the drift frame)
+  PC_FLOORD, // drift-frame bounds (grids with bounds in the drift frame, no electrons)
+  PC_EFACE0, // electron entropy fluxes per direction (FP64 grids with electrons)
+  PC_EFACE1,
+  PC_EFACE2,
+  PC_EZONE,  // electron heating + bounds, and their fixup (grids with electrons)
   PC_N
 };
 
@@ -94,10 +101,10 @@ struct PlanHook {
 // GRMHD_ERR_NOMEM or GRMHD_ERR_CUDA.
 int plan_build(Plan &p, const StageItem *items, int n);
 // threads per launch class of one grid (dimensions, flat X3, GRMHD_PREC_*,
-// bounds in the drift frame)
-void plan_counts(const Dims &D, int flat3, int prec, int drift, long long c[PC_N]);
+// bounds in the drift frame, electrons evolved)
+void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long long c[PC_N]);
 // device bytes a one-grid plan of such a grid holds (item + block tables)
-long long plan_bytes(const Dims &D, int flat3, int prec, int drift);
+long long plan_bytes(const Dims &D, int flat3, int prec, int drift, int elec);
 void plan_free(Plan &p);
 // Re-lay the block tables of class cls for bs threads per block and block
 // order sched (the results of every grid do not depend on either).

@@ -296,6 +296,8 @@ extern "C" int grmhd_server_submit(grmhd_server *s, long long id, const grmhd_gr
                                    int out_ghosts, long long nsteps, double t_arrival) {
   if (!s || !grid || !metric || !params || !P_in || !P_out || nsteps < 1 || nsteps > (1ll << 30))
     return GRMHD_ERR_INVALID;
+  // requests carry primitives only, not electron entropies
+  if (params->electrons.model != GRMHD_ELEC_OFF) return GRMHD_ERR_INVALID;
   size_t bytes = 0;
   const int rc = grmhd_footprint(grid, metric, params, &bytes);
   if (rc != GRMHD_OK) return rc;

@@ -19,6 +19,9 @@ struct grmhd_sim {
   double *geom, *conn, *floors;
   float *Pf, *geomf;    // FP32 copies (mixed precision only)
   float *Pff, *geomff, *connff;  // split float-float copies (float-float mode only)
+  // electrons only: entropies of the stage arrays, their fluxes, U_rho(P^n),
+  // the faces' signal speeds
+  double *K, *Kh, *FK[3], *Uek, *ctop_face;
   int *pflag, *fflag;
   grmhd::Clock *clk;
   unsigned long long unrec_seen, dterr_seen;

@@ -110,7 +110,9 @@ void launch_ctop_reset(const StepArgs &A, cudaStream_t st) { k_reset_ctop<<<1, 1
 // ---------------------------------------------------------------------------
 // Boundary flux fixes and flux-CT
 // ---------------------------------------------------------------------------
-__global__ void k_fix_flux(StepArgs A, double *F1, double *F2) { fix_flux_body(A, F1, F2, gtid()); }
+__global__ void k_fix_flux(StepArgs A, double *F1, double *F2) {
+  fix_flux_body(A, F1, F2, nullptr, nullptr, gtid());
+}
 
 __global__ void k_emf(StepArgs A, const double *__restrict__ F1, const double *__restrict__ F2,
                       const double *__restrict__ F3, double *__restrict__ emf) {
@@ -132,10 +134,10 @@ void launch_fix_ct(const StepArgs &A, double *F[3], double *emf, cudaStream_t st
 // Interior <-> ghost layout copies
 // ---------------------------------------------------------------------------
 __global__ void k_pack(Dims D, const double *__restrict__ src, double *__restrict__ dst,
-                       int to_ghost) {
+                       int to_ghost, int nvar) {
   const long long nz = (long long)D.n[0] * D.n[1] * D.n[2];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nz * NV) return;
+  if (t >= nz * nvar) return;
   const long long v = t / nz, r = t % nz;
   const int i = (int)(r % D.n[0]);
   const int j = (int)((r / D.n[0]) % D.n[1]);
@@ -147,9 +149,10 @@ __global__ void k_pack(Dims D, const double *__restrict__ src, double *__restric
     dst[t] = src[g];
 }
 
-void launch_pack(const Dims &D, const double *src, double *dst, int to_ghost, cudaStream_t st) {
-  const long long n = (long long)D.n[0] * D.n[1] * D.n[2] * NV;
-  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, src, dst, to_ghost);
+void launch_pack(const Dims &D, const double *src, double *dst, int to_ghost, cudaStream_t st,
+                 int nvar) {
+  const long long n = (long long)D.n[0] * D.n[1] * D.n[2] * nvar;
+  k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, src, dst, to_ghost, nvar);
 }
 
 }  // namespace grmhd

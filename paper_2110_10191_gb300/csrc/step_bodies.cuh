@@ -83,13 +83,20 @@ __host__ __device__ inline long long n_zone(const Dims &D) {
 // ---------------------------------------------------------------------------
 // Boundary conditions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void copy_zone(const Dims &D, double *P, long long dst, long long src) {
+// K (null without electrons): the two electron entropies, copied as scalars
+__device__ __forceinline__ void copy_zone(const Dims &D, double *P, double *K, long long dst,
+                                          long long src) {
 #pragma unroll
   for (int v = 0; v < NV; v++) P[v * D.ntot + dst] = P[v * D.ntot + src];
+  if (K) {
+    K[dst] = K[src];
+    K[D.ntot + dst] = K[D.ntot + src];
+  }
 }
 
 // X1 ghosts for interior (j, k); one thread per (ghost layer, side, j, k)
-__device__ __forceinline__ void bounds_x1_body(const StepArgs &A, double *P, long long t) {
+__device__ __forceinline__ void bounds_x1_body(const StepArgs &A, double *P, double *K,
+                                               long long t) {
   const Dims &D = A.D;
   if (t >= n_bounds_x1(D)) return;
   const int g = (int)(t % NG);
@@ -101,10 +108,10 @@ __device__ __forceinline__ void bounds_x1_body(const StepArgs &A, double *P, lon
   const int ig = side ? D.n[0] + NG + g : g;
   const long long d = zid(D, ig, j, k);
   if (bc == 0) {
-    copy_zone(D, P, d, zid(D, wrap(ig, D.n[0]), j, k));
+    copy_zone(D, P, K, d, zid(D, wrap(ig, D.n[0]), j, k));
   } else if (bc == 1) {
     const int ia = side ? D.n[0] + NG - 1 : NG;
-    copy_zone(D, P, d, zid(D, ia, j, k));
+    copy_zone(D, P, K, d, zid(D, ia, j, k));
     const double *gd = A.geom + (LOC_CENT * G_NCOMP + G_GDET) * D.n2d;
     const double rs = gd[(long long)j * D.s[0] + ia] / gd[(long long)j * D.s[0] + ig];
     P[B1 * D.ntot + d] *= rs;
@@ -116,7 +123,8 @@ __device__ __forceinline__ void bounds_x1_body(const StepArgs &A, double *P, lon
 }
 
 // X2 ghosts for all i and interior k
-__device__ __forceinline__ void bounds_x2_body(const StepArgs &A, double *P, long long t) {
+__device__ __forceinline__ void bounds_x2_body(const StepArgs &A, double *P, double *K,
+                                               long long t) {
   const Dims &D = A.D;
   if (t >= n_bounds_x2(D)) return;
   const int i = (int)(t % D.s[0]);
@@ -128,19 +136,20 @@ __device__ __forceinline__ void bounds_x2_body(const StepArgs &A, double *P, lon
   const int jg = side ? D.n[1] + NG + g : NG - 1 - g;
   const long long d = zid(D, i, jg, k);
   if (bc == 0) {
-    copy_zone(D, P, d, zid(D, i, wrap(jg, D.n[1]), k));
+    copy_zone(D, P, K, d, zid(D, i, wrap(jg, D.n[1]), k));
   } else if (bc == 2) {
     const int jm = side ? D.n[1] + NG - 1 - g : NG + g;
-    copy_zone(D, P, d, zid(D, i, jm, k));
+    copy_zone(D, P, K, d, zid(D, i, jm, k));
     P[U2 * D.ntot + d] = -P[U2 * D.ntot + d];
     P[B2 * D.ntot + d] = -P[B2 * D.ntot + d];
   } else if (bc == 1) {
-    copy_zone(D, P, d, zid(D, i, side ? D.n[1] + NG - 1 : NG, k));
+    copy_zone(D, P, K, d, zid(D, i, side ? D.n[1] + NG - 1 : NG, k));
   }
 }
 
 // X3 ghosts for all i, j
-__device__ __forceinline__ void bounds_x3_body(const StepArgs &A, double *P, long long t) {
+__device__ __forceinline__ void bounds_x3_body(const StepArgs &A, double *P, double *K,
+                                               long long t) {
   const Dims &D = A.D;
   const long long nrow = D.n2d;
   if (t >= n_bounds_x3(D)) return;
@@ -152,9 +161,9 @@ __device__ __forceinline__ void bounds_x3_body(const StepArgs &A, double *P, lon
   const int kg = side ? D.n[2] + NG + g : NG - 1 - g;
   const long long d = (long long)kg * D.n2d + ij;
   if (bc == 0) {
-    copy_zone(D, P, d, (long long)wrap(kg, D.n[2]) * D.n2d + ij);
+    copy_zone(D, P, K, d, (long long)wrap(kg, D.n[2]) * D.n2d + ij);
   } else if (bc == 1) {
-    copy_zone(D, P, d, (long long)(side ? D.n[2] + NG - 1 : NG) * D.n2d + ij);
+    copy_zone(D, P, K, d, (long long)(side ? D.n[2] + NG - 1 : NG) * D.n2d + ij);
   }
 }
 
@@ -260,6 +269,7 @@ __device__ __forceinline__ void face_body(const StepArgs &A, const double *__res
     const double hg = 0.5 * G.gdet;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v * D.ntot + c] = hg * acc[v];
+    if (A.ctop_face) A.ctop_face[DIR * D.ntot + c] = ct;  // the electron fluxes use it
     bool interior = true;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
@@ -330,7 +340,10 @@ __device__ __forceinline__ void advance_body(const StepArgs &A) {
 // ---------------------------------------------------------------------------
 // Boundary flux fixes and flux-CT
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void fix_flux_body(const StepArgs &A, double *F1, double *F2, long long t) {
+// FK1, FK2 (null without electrons): the electron entropy fluxes of X1 and
+// X2 faces, zeroed with the polar fluxes and with a zeroed mass inflow.
+__device__ __forceinline__ void fix_flux_body(const StepArgs &A, double *F1, double *F2,
+                                              double *FK1, double *FK2, long long t) {
   const Dims &D = A.D;
   // polar faces: (i, k) over the extended ranges
   const long long np = (long long)(D.n[0] + 2) * (D.n[2] + 2);
@@ -341,22 +354,32 @@ __device__ __forceinline__ void fix_flux_body(const StepArgs &A, double *F1, dou
     if (A.bc[1][0] == 2) {
       const long long c = zid(D, i, NG, k);
       for (int v = 0; v < NV; v++) F2[v * D.ntot + c] = 0.0;
+      if (FK2) FK2[c] = FK2[D.ntot + c] = 0.0;
     }
     if (A.bc[1][1] == 2) {
       const long long c = zid(D, i, D.n[1] + NG, k);
       for (int v = 0; v < NV; v++) F2[v * D.ntot + c] = 0.0;
+      if (FK2) FK2[c] = FK2[D.ntot + c] = 0.0;
     }
   }
   if (t < nr) {
     const int j = NG - 1 + (int)(t % (D.n[1] + 2));
     const int k = NG - 1 + (int)(t / (D.n[1] + 2));
     if (A.bc[0][0] == 1) {
-      double *f = F1 + RHO * D.ntot + zid(D, NG, j, k);
-      if (*f > 0.0) *f = 0.0;
+      const long long c = zid(D, NG, j, k);
+      double *f = F1 + RHO * D.ntot + c;
+      if (*f > 0.0) {
+        *f = 0.0;
+        if (FK1) FK1[c] = FK1[D.ntot + c] = 0.0;
+      }
     }
     if (A.bc[0][1] == 1) {
-      double *f = F1 + RHO * D.ntot + zid(D, D.n[0] + NG, j, k);
-      if (*f < 0.0) *f = 0.0;
+      const long long c = zid(D, D.n[0] + NG, j, k);
+      double *f = F1 + RHO * D.ntot + c;
+      if (*f < 0.0) {
+        *f = 0.0;
+        if (FK1) FK1[c] = FK1[D.ntot + c] = 0.0;
+      }
     }
   }
 }
@@ -507,7 +530,7 @@ __device__ __forceinline__ void update_body(const StepArgs &A, const double *Pi,
     }
     double pn[NV], bsq_n = 0.0, lor_n = 1.0;
     pf = invert_1dw(Un, G, A.gam, A.igam, pi, pn, bsq_n, lor_n);
-    if (pf == PF_OK && A.floors_on && !A.floor_drift)
+    if (pf == PF_OK && A.floors_on && !A.floor_drift && !A.elec)
       ff = apply_floors_known(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
                               bsq_n, lor_n);
 #pragma unroll

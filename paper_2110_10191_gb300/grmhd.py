@@ -47,11 +47,16 @@ PREC_FP64, PREC_MIXED, PREC_FF = 0, 1, 2
 FLOOR_FLUID, FLOOR_DRIFT = 0, 1
 
 
+class grmhd_electrons(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("game", ctypes.c_double), ("gamp", ctypes.c_double),
+                ("fel", ctypes.c_double), ("tpte_min", ctypes.c_double), ("tpte_max", ctypes.c_double)]
+
+
 class grmhd_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("t_final", ctypes.c_double),
                 ("recon", ctypes.c_int), ("floors_on", ctypes.c_int),
                 ("bc", (ctypes.c_int * 2) * 3), ("precision", ctypes.c_int),
-                ("floor_frame", ctypes.c_int)]
+                ("floor_frame", ctypes.c_int), ("electrons", grmhd_electrons)]
 
 
 KCLASSES = ["flux", "dt", "ct", "update", "fixup", "bounds", "other", "recon"]
@@ -113,7 +118,8 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_server_submit", "grmhd_server_poll", "grmhd_server_drain", "grmhd_server_get_stats",
            "grmhd_server_now", "grmhd_server_destroy", "grmhd_decomp_create", "grmhd_decomp_destroy",
            "grmhd_decomp_set_prims", "grmhd_decomp_get_prims", "grmhd_decomp_step",
-           "grmhd_decomp_get_stats", "grmhd_strerror"]
+           "grmhd_decomp_get_stats", "grmhd_set_electrons", "grmhd_get_electrons",
+           "grmhd_strerror"]
 
 
 def lib_path() -> str:
@@ -138,6 +144,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_set_prims.argtypes = [vp, vp, i]
         L.grmhd_set_prims_ghost.argtypes = [vp, vp, i]
         L.grmhd_get_prims.argtypes = [vp, vp, i, i]
+        L.grmhd_set_electrons.argtypes = [vp, vp, i, i]
+        L.grmhd_get_electrons.argtypes = [vp, vp, i, i]
         L.grmhd_step.argtypes = [vp, i, P(grmhd_stats)]
         L.grmhd_get_stats.argtypes = [vp, P(grmhd_stats)]
         L.grmhd_set_time.argtypes = [vp, d, d, ctypes.c_longlong]
@@ -225,6 +233,10 @@ def _structs(pr):
             p.bc[d][s] = int(pr.bc[d][s])
     p.precision = int(getattr(pr, "precision", PREC_FP64))
     p.floor_frame = int(getattr(pr, "floor_frame", FLOOR_FLUID))
+    el = getattr(pr, "electrons", None)
+    if el and el["model"]:
+        p.electrons = grmhd_electrons(int(el["model"]), float(el["game"]), float(el["gamp"]),
+                                      float(el["fel"]), float(el["tpte_min"]), float(el["tpte_max"]))
     return g, m, p
 
 
@@ -294,6 +306,27 @@ class Sim:
             _check(self.L.grmhd_set_prims_ghost(self.h, ptr, dev), "grmhd_set_prims_ghost")
         else:
             raise ValueError("bad primitive shape %s" % (shape,))
+
+    def set_electrons(self, K) -> None:
+        """Electron entropies (kappa_tot, kappa_e), [2][n3][n2][n1] or with ghosts."""
+        n1, n2, n3 = self.n
+        shape = tuple(K.shape)
+        if shape == (2, n3, n2, n1):
+            ghosts = 0
+        elif shape == (2,) + self.s[::-1]:
+            ghosts = 1
+        else:
+            raise ValueError("bad electron shape %s" % (shape,))
+        if isinstance(K, np.ndarray):
+            K = np.ascontiguousarray(K, dtype=np.float64)
+        ptr, dev = _ptr(K)
+        _check(self.L.grmhd_set_electrons(self.h, ptr, ghosts, dev), "grmhd_set_electrons")
+
+    def get_electrons(self, with_ghosts: bool = False):
+        out = np.empty((2,) + (self.s[::-1] if with_ghosts else self.n[::-1]))
+        _check(self.L.grmhd_get_electrons(self.h, out.ctypes.data, int(with_ghosts), 0),
+               "grmhd_get_electrons")
+        return out
 
     def get_prims(self, with_ghosts: bool = False, out=None):
         shape = (NPRIM,) + (self.s[::-1] if with_ghosts else self.n[::-1])
