@@ -51,9 +51,9 @@ WORKLOADS = {
 # summaries are under profiles/ (kp_recon<0>, kp_face<0>, kp_update).  The
 # figures hold while the kernel sources hash to SRC_HASH; otherwise the
 # bench reports the traffic as unknown (null).
-NCU_TRAFFIC = {"src_hash": "76d8c53e2dfa0d22",
-               "torus128": {"recon": 152427520 + 229693440, "flux": 297958912 + 113437696,
-                            "update": 593855488 + 271379200}}
+NCU_TRAFFIC = {"src_hash": "dfe7b283177982fa",
+               "torus128": {"recon": 152959232 + 230360576, "flux": 297922048 + 113394432,
+                            "update": 593884672 + 270656512}}
 # sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of the same
 # captures (the hardware's view of the same launches)
 NCU_FP64_PIPE = {"torus128": {"recon": 0.855, "flux": 0.889, "update": 0.887}}
@@ -271,6 +271,38 @@ def mixed_throughput(grmhd, pr, steps, warmup, stream, precision=1):
     z = pr.n[0] * pr.n[1] * pr.n[2]
     return {"value": z * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "dtype": PREC_DTYPE[precision], "steps": steps,
+            "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()}}
+
+
+def variant_throughput(grmhd, pr, steps, warmup, stream, what):
+    """The FP64 workload with a variant switched on: the bounds in the drift
+    frame ("drift") or electron entropies with the Kawazura heating model
+    ("electrons"), with the device time of each kernel class."""
+    import dataclasses
+    from paper_2110_10191_gb300 import problems as pb
+    if what == "drift":
+        pv = dataclasses.replace(pr, floor_frame=1)
+        desc = "bounds in the drift frame (floor parcel added in U and inverted)"
+    else:
+        pv = pb.with_electrons(pr, model=pb.ELEC_KAWAZURA)
+        desc = ("electron entropies carried with the mass, Kawazura et al. heating, "
+                "T_p/T_e in [1e-3, 1e3], P_gas/rho^gamma <= 3")
+    s = grmhd.Sim(pv, stream=stream)
+    s.set_prims(pv.P)
+    if pv.electrons:
+        s.set_electrons(pv.K)
+    s.step(warmup)
+    ms = _timed(stream, lambda: s.step(steps, sync=False))
+    s.profile(True)
+    s.get_profile(reset=True)
+    s.step(2, sync=False)
+    prof = s.get_profile(reset=True)
+    st = s.stats()
+    s.close()
+    z = pr.n[0] * pr.n[1] * pr.n[2]
+    return {"variant": desc, "value": z * steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / steps, "dtype": "f64", "steps": steps,
+            "floor_hits": st["floor_hits"], "inv_failures": st["inv_failures"],
             "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()}}
 
 
@@ -542,6 +574,10 @@ def main():
         extras["float_float"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream, 2)
         extras["float_float"]["parity"] = ("one step against the FP64 oracle within 3e-11 of each "
                                            "primitive group's scale (tests/test_gpu_ff.py)")
+        extras["drift_frame"] = variant_throughput(grmhd, pr, max(args.steps // 2, 5), args.warmup,
+                                                   stream, "drift")
+        extras["electrons"] = variant_throughput(grmhd, pr, max(args.steps // 2, 5), args.warmup,
+                                                 stream, "electrons")
         extras["batched"] = batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, stream)
         extras["batched_small"] = batched_throughput(grmhd, args.steps, args.warmup, stream,
                                                      nmin=32, nmax=48)
