@@ -82,7 +82,7 @@ static void free_all(grmhd_sim *s) {
   double *d[] = {s->P,      s->Ph,    s->F[0], s->F[1], s->F[2],  s->emf,
                  s->Lf,     s->Rf,    s->Uc,   s->geom, s->conn,  s->floors,
                  s->K,      s->Kh,    s->FK[0], s->FK[1], s->FK[2], s->Uek,
-                 s->ctop_face};
+                 s->ctop_face, s->KLf, s->KRf};
   for (double *p : d)
     if (p) cudaFree(p);
   if (s->Pf) cudaFree(s->Pf);
@@ -167,8 +167,8 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
     b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
   if (params->precision == GRMHD_PREC_FF)
     b += 2 * sizeof(float) * (NV * tot + (NLOC * G_NCOMP + C_NCOMP) * n2d);
-  if (params->electrons.model)  // K, Kh, FK[3] (2 each), Uek, ctop_face (3)
-    b += sizeof(double) * 14 * tot;
+  if (params->electrons.model)  // K, Kh, FK[3], KLf, KRf (2 each), Uek, ctop_face (3)
+    b += sizeof(double) * 18 * tot;
   b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision,
                          params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT,
                          params->electrons.model != GRMHD_ELEC_OFF);
@@ -238,7 +238,8 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   if (ok && elec)
     ok = cudaMalloc(&s->K, kb) == cudaSuccess && cudaMalloc(&s->Kh, kb) == cudaSuccess &&
          cudaMalloc(&s->FK[0], kb) == cudaSuccess && cudaMalloc(&s->FK[1], kb) == cudaSuccess &&
-         cudaMalloc(&s->FK[2], kb) == cudaSuccess &&
+         cudaMalloc(&s->FK[2], kb) == cudaSuccess && cudaMalloc(&s->KLf, kb) == cudaSuccess &&
+         cudaMalloc(&s->KRf, kb) == cudaSuccess &&
          cudaMalloc(&s->Uek, sizeof(double) * (size_t)tot) == cudaSuccess &&
          cudaMalloc(&s->ctop_face, sizeof(double) * 3 * (size_t)tot) == cudaSuccess;
   if (!ok) {
@@ -250,7 +251,7 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   int rc = GRMHD_OK;
   cudaStream_t st = s->st;
   if (elec)
-    for (double *q : {s->K, s->Kh, s->FK[0], s->FK[1], s->FK[2]})
+    for (double *q : {s->K, s->Kh, s->FK[0], s->FK[1], s->FK[2], s->KLf, s->KRf})
       if (cudaMemsetAsync(q, 0, kb, st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
   // zero every field so that entries outside the computed ranges read as 0
   if (cudaMemsetAsync(s->P, 0, fb, st) != cudaSuccess || cudaMemsetAsync(s->Ph, 0, fb, st) != cudaSuccess ||
@@ -346,6 +347,8 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   it.Kh = s->Kh;
   for (int d = 0; d < 3; d++) it.FK[d] = s->FK[d];
   it.Uek = s->Uek;
+  it.KLf = s->KLf;
+  it.KRf = s->KRf;
   rc = plan_build(s->plan, &it, 1);
   if (rc != GRMHD_OK) {
     free_all(s);

@@ -5,10 +5,11 @@
 //
 // kappa_tot = P_gas/rho^gamma and kappa_e = P_e/rho^gamma_e ride with the
 // mass.  Per stage, after the fluid's kernels:
-//   elec_flux_body<d>  (after the face fluxes along d) reconstructs both
-//                      entropies on either side of every face along d and
-//                      forms their local Lax-Friedrichs flux with the mass
-//                      flux's ingredients and the face's signal speed;
+//   elec_recon_body<d> reconstructs both entropies at the two faces of every
+//                      zone along d (as recon_body does the primitives);
+//   elec_flux_body<d>  (after the face fluxes along d) forms their local
+//                      Lax-Friedrichs flux with the mass flux's ingredients
+//                      and the face's signal speed;
 //   fix_flux_body      zeroes them where the mass flux is zeroed;
 //   elec_post_body     (after the update, whose bounds wait for it) carries
 //                      the entropies to the new state, heats the electrons by
@@ -28,12 +29,16 @@ constexpr double ELEC_CLAMP = 1.0e20;     // T_p/T_e and beta_p within [1/C, C]
 constexpr double MP_OVER_ME = 1836.15267343;
 constexpr int FF_KTOT = 256;              // bound flag: u lowered for kappa_tot <= 3
 
-// Heating share f_e of a zone (rho, u, kappa_e, b^2); models as documented
-// with GRMHD_ELEC_* in grmhd.h.
-__device__ __noinline__ double elec_fraction(const StepArgs &A, double rho, double u, double kel,
-                                             double bsq) {
+// Powers of the density come from one logarithm per density value,
+// rho^a = exp(a ln rho) (relative error about |a ln rho| x 1e-16, far below
+// the step's rounding), instead of one pow() each.
+
+// Heating share f_e of a zone (rho, u, kappa_e, b^2; lr = ln rho); models as
+// documented with GRMHD_ELEC_* in grmhd.h.
+__device__ __noinline__ double elec_fraction(const StepArgs &A, double rho, double lr, double u,
+                                             double kel, double bsq) {
   if (A.elec == GRMHD_ELEC_CONSTANT) return A.fel_const;
-  const double ue = kel * pow(rho, A.game) / (A.game - 1.0);
+  const double ue = kel * exp(A.game * lr) / (A.game - 1.0);
   const double Te = fabs((A.game - 1.0) * ue / rho);
   const double Tp = fabs((A.gamp - 1.0) * (u - ue) / rho);
   double trat = (Te > 0.0) ? Tp / Te : ELEC_CLAMP;  // T_p / T_e
@@ -77,19 +82,21 @@ __device__ __noinline__ double elec_fraction(const StepArgs &A, double rho, doub
 // tpte_min <= T_p/T_e <= tpte_max, i.e. within kappa_tot rho^(gamma -
 // gamma_e) / ((gamma - 1)/(gamma_e - 1) + R (gamma - 1)/(gamma_p - 1)) at
 // R = tpte_max .. tpte_min (a kappa_e that is not a number takes the lower).
-__device__ __forceinline__ int elec_close(const StepArgs &A, double P[NV], double K[2]) {
+// lr = ln P[RHO].
+__device__ __forceinline__ int elec_close(const StepArgs &A, double P[NV], double K[2], double lr) {
   int fl = 0;
   const double g1 = A.gam - 1.0;
+  const double rg = exp(A.gam * lr);
   if (A.floors_on) {
-    const double kt = g1 * P[UU] / pow(P[RHO], A.gam);
+    const double kt = g1 * P[UU] / rg;
     if (kt > KTOT_MAX) {
-      P[UU] = KTOT_MAX * pow(P[RHO], A.gam) / g1;
+      P[UU] = KTOT_MAX * rg / g1;
       fl = FF_KTOT;
     }
   }
-  K[0] = g1 * P[UU] / pow(P[RHO], A.gam);
+  K[0] = g1 * P[UU] / rg;
   const double a = g1 / (A.game - 1.0), b = g1 / (A.gamp - 1.0);
-  const double kk = K[0] * pow(P[RHO], A.gam - A.game);
+  const double kk = K[0] * exp((A.gam - A.game) * lr);
   const double kmax = kk / (a + A.tpte_min * b);
   const double kmin = kk / (a + A.tpte_max * b);
   double kel = K[1];
@@ -98,12 +105,45 @@ __device__ __forceinline__ int elec_close(const StepArgs &A, double P[NV], doubl
   return fl;
 }
 
-// Entropy fluxes of one face along DIR (the face box of face_body):
-// K_L, K_R reconstructed like the primitives, and
+// Zone-centric reconstruction of both entropies along DIR (the zones of
+// recon_body): KLf = value at the zone's low face, KRf = at its high face,
+// [2][ntot] each.
+template <int DIR>
+__device__ __forceinline__ void elec_recon_body(const StepArgs &A, const double *__restrict__ K,
+                                                double *__restrict__ KLf,
+                                                double *__restrict__ KRf, long long t) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2;
+  if (t >= n_recon(D, A.flat3)) return;
+  const int i = NG - 1 + (int)(t % e0);
+  const int j = NG - 1 + (int)((t / e0) % e1);
+  const int k = (A.flat3 ? NG : NG - 1) + (int)(t / ((long long)e0 * e1));
+  const long long c = zid(D, i, j, k);
+  const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    const double *p = K + q * D.ntot + c;
+    double lo, hi;
+    if (A.recon == 1) {
+      weno5_pair(__ldg(p - 2 * st), __ldg(p - st), __ldg(p), __ldg(p + st), __ldg(p + 2 * st), lo, hi);
+    } else {
+      const double x1 = __ldg(p), h = 0.5 * mc_slope(__ldg(p - st), x1, __ldg(p + st));
+      lo = x1 - h;
+      hi = x1 + h;
+    }
+    KLf[q * D.ntot + c] = lo;
+    KRf[q * D.ntot + c] = hi;
+  }
+}
+
+// Entropy fluxes of one face along DIR (the face box of face_body), from the
+// face values of the zones on either side (K_L: high face of zone c-1, K_R:
+// low face of zone c) and the face states' mass terms:
 // F_K = sqrt(-g)/2 [rho_L u^d_L K_L + rho_R u^d_R K_R - c (rho_R u^t_R K_R - rho_L u^t_L K_L)]
 // with c the face's LLF speed.
 template <int DIR>
-__device__ __forceinline__ void elec_flux_body(const StepArgs &A, const double *__restrict__ K,
+__device__ __forceinline__ void elec_flux_body(const StepArgs &A, const double *__restrict__ KLf,
+                                               const double *__restrict__ KRf,
                                                const double *__restrict__ Lf,
                                                const double *__restrict__ Rf,
                                                double *__restrict__ FK, long long t) {
@@ -139,18 +179,7 @@ __device__ __forceinline__ void elec_flux_body(const StepArgs &A, const double *
   const double ct = A.ctop_face[DIR * N + c];
 #pragma unroll
   for (int q = 0; q < 2; q++) {
-    const double *p = K + q * N + c;
-    double KL, KR, lo_c, hi_m;
-    if (A.recon == 1) {
-      double dummy;
-      weno5_pair(p[-3 * st], p[-2 * st], p[-st], p[0], p[st], dummy, hi_m);
-      weno5_pair(p[-2 * st], p[-st], p[0], p[st], p[2 * st], lo_c, dummy);
-    } else {
-      hi_m = p[-st] + 0.5 * mc_slope(p[-2 * st], p[-st], p[0]);
-      lo_c = p[0] - 0.5 * mc_slope(p[-st], p[0], p[st]);
-    }
-    KL = hi_m;
-    KR = lo_c;
+    const double KL = KRf[q * N + c - st], KR = KLf[q * N + c];
     FK[q * N + c] = 0.5 * G.gdet * (m[0] * KL + m[1] * KR - ct * (dn[1] * KR - dn[0] * KL));
   }
 }
@@ -217,16 +246,18 @@ __device__ __forceinline__ void elec_post_body(const StepArgs &A, const double *
       double pn[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) pn[v] = Pout[v * N + c];
-      const double fel = elec_fraction(A, ps[RHO], ps[UU], Ks[N + c], ss.bsq);
-      const double ktot_new = (A.gam - 1.0) * pn[UU] / pow(pn[RHO], A.gam);
-      kn[1] = kn[1] + fel * (A.game - 1.0) / (A.gam - 1.0) * pow(ps[RHO], A.gam - A.game) *
+      const double ls = log(ps[RHO]), ln = log(pn[RHO]);
+      const double fel = elec_fraction(A, ps[RHO], ls, ps[UU], Ks[N + c], ss.bsq);
+      const double ktot_new = (A.gam - 1.0) * pn[UU] / exp(A.gam * ln);
+      kn[1] = kn[1] + fel * (A.game - 1.0) / (A.gam - 1.0) * exp((A.gam - A.game) * ls) *
                           (ktot_new - kn[0]);
+      const double rho_n = pn[RHO];
       if (A.floors_on) {
         const double rho_fl = __ldg(A.floors + ij), u_fl = __ldg(A.floors + D.n2d + ij);
         ff = A.floor_drift ? apply_floors_drift(pn, G, rho_fl, u_fl, A.gam, A.igam)
                            : apply_floors(pn, G, rho_fl, u_fl, A.gam);
       }
-      ff |= elec_close(A, pn, kn);
+      ff |= elec_close(A, pn, kn, (pn[RHO] == rho_n) ? ln : log(pn[RHO]));
 #pragma unroll
       for (int v = 0; v < NV; v++) Pout[v * N + c] = pn[v];
       fflag[c] = ff;
@@ -272,7 +303,7 @@ __device__ __forceinline__ void elec_fix_body(const StepArgs &A, double *P, doub
         double p[NV], kn[2] = {0.0, sum / (double)cnt};
 #pragma unroll
         for (int v = 0; v < NV; v++) p[v] = P[v * N + c];
-        const int f = elec_close(A, p, kn);
+        const int f = elec_close(A, p, kn, log(p[RHO]));
         P[UU * N + c] = p[UU];
         K[c] = kn[0];
         K[N + c] = kn[1];

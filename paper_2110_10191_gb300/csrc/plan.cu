@@ -170,10 +170,17 @@ __global__ void __maxnreg__(128) kp_update_ff(BView V, int in, double dtfac, int
 }
 
 template <int DIR>
-__global__ void kp_elec_flux(BView V, int in) {
+__global__ void kp_elec_recon(BView V, int in) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
-  elec_flux_body<DIR>(it.A, karr(it, in), it.Lf, it.Rf, it.FK[DIR], block_tid(V, g));
+  elec_recon_body<DIR>(it.A, karr(it, in), it.KLf, it.KRf, block_tid(V, g));
+}
+
+template <int DIR>
+__global__ void kp_elec_flux(BView V) {
+  const int g = block_grid(V);
+  const StageItem &it = V.items[g];
+  elec_flux_body<DIR>(it.A, it.KLf, it.KRf, it.Lf, it.Rf, it.FK[DIR], block_tid(V, g));
 }
 
 // stage in: P_s = arr(in), output arr(1 - in); kappa_i is always K (of P^n)
@@ -310,6 +317,8 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
   c[PC_UPDX] = fx ? n_zone(D) : 0;
   c[PC_FLOORD] = (drift && !elec) ? n_zone(D) : 0;
   for (int d = 0; d < 3; d++) c[PC_EFACE0 + d] = elec ? n_face(D, d, fl) : 0;
+  c[PC_EREC01] = elec ? n_recon(D, fl) : 0;
+  c[PC_EREC2] = (elec && !fl) ? n_recon(D, 0) : 0;
   c[PC_EZONE] = elec ? n_zone(D) : 0;
 }
 
@@ -408,13 +417,16 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   // before the next reconstruction overwrites the face states)
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EFACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EREC01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<0><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EFACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EREC01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<1><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EFACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<2><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EREC2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<2><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<2><<<nb, bs, 0, st>>>(V); });
   // mixed-precision grids
   nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_f32<<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });

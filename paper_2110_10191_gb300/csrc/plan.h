@@ -29,6 +29,7 @@ struct StageItem {
   // electrons (A.elec): (kappa_tot, kappa_e) of the stage arrays ([2][ntot]
   // each, with P and Ph), their fluxes, and U_rho(P^n) kept by the predictor
   double *K, *Kh, *FK[3], *Uek;
+  double *KLf, *KRf;  // their face values along the current direction
 };
 
 // launch classes, each with its own block table
@@ -60,7 +61,9 @@ enum {
   PC_UPD64,  // FP64 update (FP64 and mixed-precision grids)
   PC_UPDX,   // float-float update (float-float grids)
   PC_FLOORD, // drift-frame bounds (grids with bounds in the drift frame, no electrons)
-  PC_EFACE0, // electron entropy fluxes per direction (FP64 grids with electrons)
+  PC_EREC01, // electron entropy reconstruction along X1, X2 (FP64 grids with electrons)
+  PC_EREC2,  // along X3
+  PC_EFACE0, // electron entropy fluxes per direction
   PC_EFACE1,
   PC_EFACE2,
   PC_EZONE,  // electron heating + bounds, and their fixup (grids with electrons)
