@@ -248,6 +248,9 @@ def _timed(stream, fn):
 PREC_DTYPE = {
     1: "mixed: FP32 reconstruction, fluid states, signal speeds, LLF fluxes; "
        "FP64 geometry, flux-CT, update, 1D_W inversion, bounds",
+    3: "mixed + float-float update: FP32 reconstruction, fluid states, signal speeds, LLF "
+       "fluxes; float-float U(P), geometric source and 1D_W inversion; FP64 state, geometry, "
+       "flux divergence, flux-CT, bounds",
     2: "float-float: reconstruction, fluid states, signal speeds, LLF fluxes, U(P), geometric "
        "source and 1D_W inversion in pairs of FP32 words (~48 significant bits); FP64 state, "
        "geometry, flux divergence, flux-CT, bounds",
@@ -419,16 +422,15 @@ def corner_divb(P, gdet, dx, n):
 
 
 def mixed_accuracy(grmhd, steps, stream):
-    """The 288x128x128 torus (R_out = 1000) advanced `steps` cycles in FP64
-    and in the mixed mode: per-primitive L1 and Linf of the difference,
-    relative to the FP64 state's mean |value| and max |value|, and the
-    corner divergence of both."""
+    """The 288x128x128 torus (R_out = 1000) advanced `steps` cycles in FP64,
+    in the mixed mode and in the mixed mode with the float-float update:
+    per-primitive L1 and Linf of the difference from FP64, relative to the
+    FP64 state's mean |value| and max |value|, and the corner divergence."""
     import dataclasses
     import numpy as np
     pr = make_problem("torus288")
-    out = {}
     states = {}
-    for prec in (0, 1):
+    for prec in (0, 1, 3):
         p = dataclasses.replace(pr, precision=prec)
         s = grmhd.Sim(p, stream=stream)
         s.set_prims(p.P)
@@ -437,21 +439,27 @@ def mixed_accuracy(grmhd, steps, stream):
         gdet = s.geom(0)[32]
         s.close()
     names = ["rho", "u", "u1", "u2", "u3", "B1", "B2", "B3"]
-    a, b = states[1][:, 3:-3, 3:-3, 3:-3], states[0][:, 3:-3, 3:-3, 3:-3]
+    b = states[0][:, 3:-3, 3:-3, 3:-3]
     body = b[0] > 1e-2  # the torus itself (max rho = 1), without the floor-held atmosphere
     # group scales: mean over zones of |rho|, |u|, the velocity norm, the field norm
     grp = {0: np.abs(b[0]).mean(), 1: np.abs(b[1]).mean(),
            2: np.sqrt((b[2:5] ** 2).sum(axis=0)).mean(), 5: np.sqrt((b[5:8] ** 2).sum(axis=0)).mean()}
-    for v, nm in enumerate(names):
-        d = np.abs(a[v] - b[v])
-        gs = grp[0 if v == 0 else 1 if v == 1 else 2 if v < 5 else 5]
-        out[nm] = {"group_l1_rel": float(d.mean() / max(gs, 1e-300)),
-                   "l1_rel": float(d.mean() / max(np.abs(b[v]).mean(), 1e-300)),
-                   "linf_rel": float(d.max() / max(np.abs(b[v]).max(), 1e-300)),
-                   "torus_l1_rel": float(d[body].mean() / max(np.abs(b[v][body]).mean(), 1e-300)),
-                   "torus_linf_rel": float(d[body].max() / max(np.abs(b[v][body]).max(), 1e-300))}
+
+    def norms(a):
+        out = {}
+        for v, nm in enumerate(names):
+            d = np.abs(a[v] - b[v])
+            gs = grp[0 if v == 0 else 1 if v == 1 else 2 if v < 5 else 5]
+            out[nm] = {"group_l1_rel": float(d.mean() / max(gs, 1e-300)),
+                       "l1_rel": float(d.mean() / max(np.abs(b[v]).mean(), 1e-300)),
+                       "linf_rel": float(d.max() / max(np.abs(b[v]).max(), 1e-300)),
+                       "torus_l1_rel": float(d[body].mean() / max(np.abs(b[v][body]).mean(), 1e-300)),
+                       "torus_linf_rel": float(d[body].max() / max(np.abs(b[v][body]).max(), 1e-300))}
+        return out
+
+    out = norms(states[1][:, 3:-3, 3:-3, 3:-3])
     dx = [(pr.xmax[d] - pr.xmin[d]) / pr.n[d] for d in range(3)]
-    for prec, key in ((0, "divb_fp64"), (1, "divb_mixed")):
+    for prec, key in ((0, "divb_fp64"), (1, "divb_mixed"), (3, "divb_mixed_ff")):
         m, sc = corner_divb(states[prec], gdet, dx, pr.n)
         out[key] = {"max": m, "scale": sc, "rel": m / sc}
     return {"workload": WORKLOADS["torus288"]["label"].replace("_fp64", ""), "steps": steps,
@@ -459,7 +467,8 @@ def mixed_accuracy(grmhd, steps, stream):
             "norms": "group_l1_rel: mean |mixed - fp64| / mean of the group's magnitude (rho; u; "
                      "|utilde|; |B|); l1_rel: / mean |fp64| of the component; linf_rel: max / max; "
                      "over all interior zones; torus_*: over zones with rho > 1e-2",
-            "primitives": out}
+            "primitives": out,
+            "mixed_ff_primitives": norms(states[3][:, 3:-3, 3:-3, 3:-3])}
 
 
 def workload_config(name):
@@ -482,7 +491,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="torus128", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff", "mixed_ff"],
                     help="arithmetic of the flux stage of the timed workload (fp64: the headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
@@ -517,7 +526,7 @@ def main():
             dist.barrier()
 
     pr = make_problem(args.config)
-    pr.precision = {"fp64": 0, "mixed": 1, "ff": 2}[args.precision]
+    pr.precision = {"fp64": 0, "mixed": 1, "ff": 2, "mixed_ff": 3}[args.precision]
     zones = pr.n[0] * pr.n[1] * pr.n[2]
     stream = torch.cuda.current_stream()
     sim = grmhd.Sim(pr, stream=stream)
@@ -572,6 +581,7 @@ def main():
     if not args.no_extras:
         extras["mixed"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream, 1)
         extras["float_float"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream, 2)
+        extras["mixed_ff"] = mixed_throughput(grmhd, pr, args.steps, args.warmup, stream, 3)
         extras["float_float"]["parity"] = ("one step against the FP64 oracle within 3e-11 of each "
                                            "primitive group's scale (tests/test_gpu_ff.py)")
         extras["drift_frame"] = variant_throughput(grmhd, pr, max(args.steps // 2, 5), args.warmup,

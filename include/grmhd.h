@@ -66,6 +66,8 @@ extern "C" {
                               and the 1D_W inversion in pairs of FP32 words (~48
                               significant bits) on the FP32 pipe, in per-zone scaled
                               units; flux divergence, flux-CT, bounds and the state FP64 */
+#define GRMHD_PREC_MIXED_FF 3 /* the fluxes of GRMHD_PREC_MIXED (FP32) with the update of
+                                 GRMHD_PREC_FF (float-float U(P), source, inversion) */
 
 typedef struct grmhd_sim grmhd_sim; /* opaque, library-owned */
 

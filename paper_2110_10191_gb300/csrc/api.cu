@@ -120,7 +120,7 @@ int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const g
   if (!(params->gamma > 1.0) || !(params->cfl > 0.0)) return GRMHD_ERR_INVALID;
   if (params->recon != GRMHD_RECON_MC && params->recon != GRMHD_RECON_WENO5) return GRMHD_ERR_INVALID;
   if (params->precision != GRMHD_PREC_FP64 && params->precision != GRMHD_PREC_MIXED &&
-      params->precision != GRMHD_PREC_FF)
+      params->precision != GRMHD_PREC_FF && params->precision != GRMHD_PREC_MIXED_FF)
     return GRMHD_ERR_INVALID;
   if (params->floors_on && metric->kind != GRMHD_METRIC_MKS_KERR) return GRMHD_ERR_INVALID;
   if (params->floor_frame != GRMHD_FLOOR_FLUID && params->floor_frame != GRMHD_FLOOR_DRIFT)
@@ -163,10 +163,13 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
              + sizeof(double) * 3 * tot                    // EMFs
              + sizeof(double) * (NLOC * G_NCOMP + C_NCOMP + 2) * n2d  // geometry, connection, bounds
              + sizeof(int) * 2 * tot + sizeof(Clock);     // flags, clock
-  if (params->precision == GRMHD_PREC_MIXED)
+  const int pr = params->precision;
+  if (pr == GRMHD_PREC_MIXED || pr == GRMHD_PREC_MIXED_FF)  // FP32 stage input and geometry
     b += sizeof(float) * NV * tot + sizeof(float) * NLOC * G_NCOMP * n2d;
-  if (params->precision == GRMHD_PREC_FF)
-    b += 2 * sizeof(float) * (NV * tot + (NLOC * G_NCOMP + C_NCOMP) * n2d);
+  if (pr == GRMHD_PREC_FF)  // split stage input
+    b += 2 * sizeof(float) * NV * tot;
+  if (pr == GRMHD_PREC_FF || pr == GRMHD_PREC_MIXED_FF)  // split geometry and connection
+    b += 2 * sizeof(float) * (NLOC * G_NCOMP + C_NCOMP) * n2d;
   if (params->electrons.model)  // K, Kh, FK[3], KLf, KRf (2 each), Uek, ctop_face (3)
     b += sizeof(double) * 18 * tot;
   b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision,
@@ -226,12 +229,14 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
             cudaMalloc(&s->pflag, sizeof(int) * (size_t)tot) == cudaSuccess &&
             cudaMalloc(&s->fflag, sizeof(int) * (size_t)tot) == cudaSuccess &&
             cudaMalloc(&s->clk, sizeof(Clock)) == cudaSuccess;
-  if (ok && params->precision == GRMHD_PREC_MIXED)
+  const int prec = params->precision;
+  if (ok && (prec == GRMHD_PREC_MIXED || prec == GRMHD_PREC_MIXED_FF))
     ok = cudaMalloc(&s->Pf, sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
          cudaMalloc(&s->geomf, sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess;
-  if (ok && params->precision == GRMHD_PREC_FF)
-    ok = cudaMalloc(&s->Pff, 2 * sizeof(float) * NV * (size_t)tot) == cudaSuccess &&
-         cudaMalloc(&s->geomff, 2 * sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
+  if (ok && prec == GRMHD_PREC_FF)
+    ok = cudaMalloc(&s->Pff, 2 * sizeof(float) * NV * (size_t)tot) == cudaSuccess;
+  if (ok && (prec == GRMHD_PREC_FF || prec == GRMHD_PREC_MIXED_FF))
+    ok = cudaMalloc(&s->geomff, 2 * sizeof(float) * NLOC * G_NCOMP * (size_t)D.n2d) == cudaSuccess &&
          cudaMalloc(&s->connff, 2 * sizeof(float) * C_NCOMP * (size_t)D.n2d) == cudaSuccess;
   const bool elec = params->electrons.model != GRMHD_ELEC_OFF;
   const size_t kb = sizeof(double) * 2 * (size_t)tot;

@@ -292,7 +292,11 @@ int upload_tables(Plan &p) {
 
 void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long long c[PC_N]) {
   const int fl = flat3;
-  const bool f64 = prec == GRMHD_PREC_FP64, mx = prec == GRMHD_PREC_MIXED, fx = prec == GRMHD_PREC_FF;
+  // the flux stage: FP64, FP32 (mixed, and mixed with the float-float
+  // update) or float-float; the update: FP64 or float-float
+  const bool f64 = prec == GRMHD_PREC_FP64, fx = prec == GRMHD_PREC_FF;
+  const bool mx = prec == GRMHD_PREC_MIXED || prec == GRMHD_PREC_MIXED_FF;
+  const bool ux = prec == GRMHD_PREC_FF || prec == GRMHD_PREC_MIXED_FF;
   c[PC_BX1] = n_bounds_x1(D);
   c[PC_BX2] = n_bounds_x2(D);
   c[PC_BX3] = n_bounds_x3(D);
@@ -313,8 +317,8 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
   c[PC_FIX] = n_fix(D);
   c[PC_EDGE] = n_edge(D);
   c[PC_ZONE] = n_zone(D);
-  c[PC_UPD64] = fx ? 0 : n_zone(D);
-  c[PC_UPDX] = fx ? n_zone(D) : 0;
+  c[PC_UPD64] = ux ? 0 : n_zone(D);
+  c[PC_UPDX] = ux ? n_zone(D) : 0;
   c[PC_FLOORD] = (drift && !elec) ? n_zone(D) : 0;
   for (int d = 0; d < 3; d++) c[PC_EFACE0 + d] = elec ? n_face(D, d, fl) : 0;
   c[PC_EREC01] = elec ? n_recon(D, fl) : 0;

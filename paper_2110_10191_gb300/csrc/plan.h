@@ -59,7 +59,7 @@ enum {
   PC_EDGE,   // EMFs and CT
   PC_ZONE,   // fixup (every grid)
   PC_UPD64,  // FP64 update (FP64 and mixed-precision grids)
-  PC_UPDX,   // float-float update (float-float grids)
+  PC_UPDX,   // float-float update (float-float and mixed + float-float grids)
   PC_FLOORD, // drift-frame bounds (grids with bounds in the drift frame, no electrons)
   PC_EREC01, // electron entropy reconstruction along X1, X2 (FP64 grids with electrons)
   PC_EREC2,  // along X3

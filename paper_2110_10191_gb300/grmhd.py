@@ -43,7 +43,7 @@ class grmhd_metric(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("hslope", ctypes.c_double)]
 
 
-PREC_FP64, PREC_MIXED, PREC_FF = 0, 1, 2
+PREC_FP64, PREC_MIXED, PREC_FF, PREC_MIXED_FF = 0, 1, 2, 3
 FLOOR_FLUID, FLOOR_DRIFT = 0, 1
 
 

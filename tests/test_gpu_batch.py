@@ -183,13 +183,14 @@ def test_batch_rejects_bad_members(grmhd):
 
 
 def test_batch_mixed_precision_members(grmhd):
-    """FP64 and mixed-precision grids in one batch: each bitwise its alone
-    result (the FP32 flux kernels run only on the mixed grids' blocks)."""
-    probs = pb.batch_2d(ngrid=6, nmin=12, nmax=32, seed=4)
+    """Grids of all four precision modes in one batch: each bitwise its
+    alone result (each flux and update kernel runs only on its own grids'
+    blocks)."""
+    probs = pb.batch_2d(ngrid=7, nmin=12, nmax=32, seed=4)
     tor = pb.fm_torus(24, 20, 8)
     probs.append(tor)
     for q, pr in enumerate(probs):
-        pr.precision = q % 2
+        pr.precision = q % 4
     ref = [_alone(grmhd, pr, 2)[0] for pr in probs]
     sims = []
     for pr in probs:

@@ -2,7 +2,7 @@
 blocks is bitwise that of the undecomposed grid -- the paper's
 decomposition tests -- for every boundary kind (periodic seams, X1
 outflow, polar axis, fixed Bondi ghosts), both reconstructions, the flat
-2D path, all three precisions, and failed zones fixed up across block
+2D path, all four precision modes, and failed zones fixed up across block
 edges."""
 import numpy as np
 import pytest
@@ -67,11 +67,15 @@ def _case(name):
         pr = pb.fm_torus(24, 20, 8)
         pr.precision = 2
         return pr, (1, 2, 2), 2
+    if name == "torus_mixed_ff":
+        pr = pb.fm_torus(24, 20, 8)
+        pr.precision = 3
+        return pr, (2, 1, 2), 2
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("name", ["torus222", "torus_mc_x1", "torus_x2x3", "mode2d", "ot", "bondi",
-                                  "torus_mixed", "torus_ff"])
+                                  "torus_mixed", "torus_ff", "torus_mixed_ff"])
 def test_decomposition_bitwise(grmhd, name):
     pr, nb, n = _case(name)
     a, sa = _whole(grmhd, pr, n)

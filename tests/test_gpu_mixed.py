@@ -1,7 +1,9 @@
 """Mixed-precision mode (FP32 reconstruction, fluid states, signal speeds
 and LLF fluxes; FP64 geometry, flux-CT, update, 1D_W inversion, bounds):
 its error against the FP64 oracle, div B at round-off, second-order
-convergence of the linear mode."""
+convergence of the linear mode.  The same fluxes with the float-float
+update (GRMHD_PREC_MIXED_FF): the same error bound against the oracle, and
+within the float-float update's rounding of the mixed mode itself."""
 import numpy as np
 import pytest
 
@@ -102,6 +104,56 @@ def test_mixed_orszag_tang_close_to_fp64(grmhd):
     pm.precision = 1
     sm = grmhd.Sim(pm)
     sm.set_prims(pm.P)
+    sm.step(10)
+    a, b = sm.get_prims(), s64.get_prims()
+    sc = _scales(b)
+    assert max(np.abs(a[v] - b[v]).max() / sc[v] for v in range(8)) < 1e-4
+
+
+def test_mixed_ff_one_step_error_vs_fp64_oracle(grmhd):
+    """Mixed fluxes with the float-float update: the FP32 fluxes still set
+    the error, and the result is the mixed mode's up to the update's
+    rounding (the float-float bar, 3e-11 of each group's scale)."""
+    pr = pb.fm_torus(32, 32, 16)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.step(1)
+    out = {}
+    for prec in (1, 3):
+        pm = pb.fm_torus(32, 32, 16)
+        pm.precision = prec
+        s = grmhd.Sim(pm)
+        for loc in range(4):
+            s.set_geom(loc, o.geom(loc))
+        s.set_prims(pm.P)
+        s.step(1)
+        out[prec] = s.get_prims()
+    b = o.get_prims()
+    sc = _scales(b)
+    err = [np.abs(out[3][v] - b[v]).max() / sc[v] for v in range(8)]
+    assert max(err) < 1e-5, err
+    diff = [np.abs(out[3][v] - out[1][v]).max() / sc[v] for v in range(8)]
+    assert max(diff) < 3e-11, diff
+    assert max(diff) > 0  # it is genuinely the float-float update
+
+
+def test_mixed_ff_divb_and_orszag_tang(grmhd):
+    pr = pb.fm_torus(24, 24, 8)
+    pr.precision = 3
+    s = grmhd.Sim(pr)
+    s.set_prims(pr.P)
+    gdet = s.geom(0)[32]
+    dx = [(pr.xmax[d] - pr.xmin[d]) / pr.n[d] for d in range(3)]
+    s.step(5)
+    d1, scale = corner_divb(s.get_prims(True), gdet, dx, pr.n)
+    assert d1 <= 1e-12 * scale
+    po = pb.orszag_tang(64, recon=pb.RECON_WENO5)
+    s64 = grmhd.Sim(po)
+    s64.set_prims(po.P)
+    s64.step(10)
+    po.precision = 3
+    sm = grmhd.Sim(po)
+    sm.set_prims(po.P)
     sm.step(10)
     a, b = sm.get_prims(), s64.get_prims()
     sc = _scales(b)
