@@ -547,13 +547,18 @@ __device__ __forceinline__ int invert_1dw_ff(const ff U[NV], const GeoFF &G, ff 
 // source of P_s, the inversion in float-float; the flux divergence, the
 // conserved sum, the bounds and all stored arrays in FP64.  Every thread
 // of the block must call it (warp counters).
+// Pff (may be null): the split stage input of the flux stage; in the
+// predictor it is P^n = P_i, whose words the update then reads instead of
+// splitting P_i again.  Ucache holds U(P^n) as split words in P^n's scaled
+// units ([2][8][ntot] floats in the space of [8][ntot] doubles): the
+// corrector, which scales by the same P^n density, reads it back as is.
 __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *Pi,
                                                const double *__restrict__ Ps, double *Pout,
                                                const double *__restrict__ F1,
                                                const double *__restrict__ F2,
                                                const double *__restrict__ F3, int *pflag, int *fflag,
                                                double dtfac, double *Ucache, int ucache_mode,
-                                               long long t) {
+                                               const float *__restrict__ Pff, long long t) {
   const Dims &D = A.D;
   const double dt = A.clk->dt;
   if (!(dt > 0.0)) return;  // uniform across the grid
@@ -573,8 +578,15 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
     const ff igam = {A.igam_ff[0], A.igam_ff[1]}, gf = {A.gf_ff[0], A.gf_ff[1]};
     const long long clo = (long long)C_NCOMP * D.n2d;
     ff pi[NV], Ui[NV], S[4];
+    if (Ps == Pi && Pff) {
 #pragma unroll
-    for (int v = 0; v < NV; v++) pi[v] = ff_from(Pi[v * N + c]);
+      for (int v = 0; v < NV; v++) pi[v] = ff_load(Pff, (long long)NV * N, v * N + c);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; v++) pi[v] = ff_from(Pi[v * N + c]);
+    }
+    float *Ucf = reinterpret_cast<float *>(Ucache);
+    const long long uhalf = (long long)NV * N;
     // scaled units from P^n's density (the same in both stages, so that
     // U(P^n) kept by the predictor is read back in the corrector's units)
     const FFScale sc = ff_scale_for(pi[RHO].hi);
@@ -585,14 +597,13 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
       prim_cons_ff(pi, si, G, gm1, Ui);
       if (ucache_mode == 1) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) Ucache[v * N + c] = ff_to(Ui[v]) * (v < B1 ? sc.s : sc.rs);
+        for (int v = 0; v < NV; v++) ff_store(Ucf, uhalf, v * N + c, Ui[v]);
       }
       geo_source_ff(pi, si, G, A.connff, clo, D.n2d, ij, gm1, S);
     } else {
       if (ucache_mode == 2) {
 #pragma unroll
-        for (int v = 0; v < NV; v++)
-          Ui[v] = ff_from(Ucache[v * N + c] * (double)(v < B1 ? sc.is : sc.irs));
+        for (int v = 0; v < NV; v++) Ui[v] = ff_load(Ucf, uhalf, v * N + c);
       } else {
         FStateFF si;
         fluid_state_ff(pi, G, si);

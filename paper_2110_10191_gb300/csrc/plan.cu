@@ -166,7 +166,7 @@ __global__ void __maxnreg__(128) kp_update_ff(BView V, int in, double dtfac, int
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   update_ff_body(it.A, it.P, arr(it, in), arr(it, 1 - in), it.F[0], it.F[1], it.F[2], it.pflag,
-                 it.fflag, dtfac, it.Uc, ucache_mode, block_tid(V, g));
+                 it.fflag, dtfac, it.Uc, ucache_mode, it.Pff, block_tid(V, g));
 }
 
 template <int DIR>
