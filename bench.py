@@ -185,6 +185,48 @@ def cpu_oracle_sample(name, steps, count=True):
     return out
 
 
+def _oracle_slab_worker(name, steps, barrier, out_q):
+    """One host core's share of the all-cores oracle baseline: the same slab
+    sample as cpu_oracle_sample, timed after a barrier with the others."""
+    import oracle
+    n3s = 8 if WORKLOADS[name]["n"][2] > 8 else WORKLOADS[name]["n"][2]
+    pr = make_problem(name, n3_override=n3s) if name != "mode64" else make_problem(name)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.step(1)
+    barrier.wait()
+    t0 = time.perf_counter()
+    o.step(steps)
+    out_q.put((time.perf_counter() - t0, pr.n[0] * pr.n[1] * pr.n[2]))
+
+
+def cpu_oracle_all_cores(name, steps):
+    """The oracle as it stands on every host core this process may use: one
+    slab sample per core in separate processes (started with spawn, so no
+    CUDA state is inherited), all timed together; aggregate = the zone-cycles
+    of all slabs / the slowest slab's time."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_slab_worker, args=(name, steps, barrier, q))
+             for _ in range(cores)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=900) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    wall = max(r[0] for r in res)
+    zones = res[0][1]
+    return {"value": cores * zones * steps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d independent %d-step samples of the same slab, one process per core, "
+                      "timed together (aggregate over the slowest)" % (cores, steps),
+            "seconds": wall}
+
+
 def reference_arm(args, rank, world):
     """--impl reference: the oracle, timed on the host cores, one bounded
     sample (a slab of the workload) per step."""
@@ -605,8 +647,11 @@ def main():
         return
 
     cpu = None
+    cpu_all = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_sample(args.config, steps=2)
+        if not args.no_extras:
+            cpu_all = cpu_oracle_all_cores(args.config, steps=2)
 
     launches = sum(v[1] for v in prof.values())
     roofline = None
@@ -681,6 +726,7 @@ def main():
             "roofline": roofline,
             "kernels": kernels,
             "cpu_baseline": None if cpu is None else {k: v for k, v in cpu.items() if not k.startswith("_")},
+            "cpu_baseline_all_cores": cpu_all,
             "algorithmic_fp64_flops_per_zone_cycle": None if cpu is None else cpu["_flops_per_zone_cycle"],
             "clocks": clk,
             "sim": {"t": st["t"], "steps": st["steps"], "inv_failures": st["inv_failures"],
