@@ -547,9 +547,9 @@ __device__ __forceinline__ int invert_1dw_ff(const ff U[NV], const GeoFF &G, ff 
 // source of P_s, the inversion in float-float; the flux divergence, the
 // conserved sum, the bounds and all stored arrays in FP64.  Every thread
 // of the block must call it (warp counters).
-// Pff (may be null): the split stage input of the flux stage; in the
-// predictor it is P^n = P_i, whose words the update then reads instead of
-// splitting P_i again.  Ucache holds U(P^n) as split words in P^n's scaled
+// Pff (may be null): the split stage input of the flux stage, which is P_s:
+// the update reads P_s's words there instead of splitting P_s again (in the
+// predictor P_s = P_i = P^n).  Ucache holds U(P^n) as split words in P^n's scaled
 // units ([2][8][ntot] floats in the space of [8][ntot] doubles): the
 // corrector, which scales by the same P^n density, reads it back as is.
 __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *Pi,
@@ -610,8 +610,13 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
         prim_cons_ff(pi, si, G, gm1, Ui);
       }
       ff ps[NV];
+      if (Pff) {  // the corrector's flux stage split P_s
 #pragma unroll
-      for (int v = 0; v < NV; v++) ps[v] = ff_from(Ps[v * N + c]);
+        for (int v = 0; v < NV; v++) ps[v] = ff_load(Pff, (long long)NV * N, v * N + c);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; v++) ps[v] = ff_from(Ps[v * N + c]);
+      }
       ff_scale_prims(ps, sc);
       FStateFF ss;
       fluid_state_ff(ps, G, ss);
