@@ -112,8 +112,10 @@ typedef struct {
  *             c2 = 1.6 T_e/T_p, c3 = 18 + 5 log10(T_p/T_e) (T_p > T_e), else
  *             c2 = 1.2 T_e/T_p, c3 = 18
  *   CONSTANT  f_e = fel (not one of the paper's models; for tests)
- * Only FP64 grids evolve electrons (GRMHD_PREC_FP64); decomposed grids and
- * the server take none. */
+ * Grids of every precision mode evolve them (the mass-flux weights of the
+ * entropy fluxes come from the grid's face kernels, in their arithmetic;
+ * everything else about the entropies is FP64); decomposed grids and the
+ * server take none. */
 #define GRMHD_ELEC_OFF 0
 #define GRMHD_ELEC_CONSTANT 1
 #define GRMHD_ELEC_KAWAZURA 2

@@ -82,7 +82,7 @@ static void free_all(grmhd_sim *s) {
   double *d[] = {s->P,      s->Ph,    s->F[0], s->F[1], s->F[2],  s->emf,
                  s->Lf,     s->Rf,    s->Uc,   s->geom, s->conn,  s->floors,
                  s->K,      s->Kh,    s->FK[0], s->FK[1], s->FK[2], s->Uek,
-                 s->ctop_face, s->KLf, s->KRf};
+                 s->elec_w, s->KLf, s->KRf};
   for (double *p : d)
     if (p) cudaFree(p);
   if (s->Pf) cudaFree(s->Pf);
@@ -128,7 +128,6 @@ int validate_problem(const grmhd_grid *grid, const grmhd_metric *metric, const g
   const grmhd_electrons &e = params->electrons;
   if (e.model < GRMHD_ELEC_OFF || e.model > GRMHD_ELEC_HOWES) return GRMHD_ERR_INVALID;
   if (e.model != GRMHD_ELEC_OFF) {
-    if (params->precision != GRMHD_PREC_FP64) return GRMHD_ERR_INVALID;
     if (!(e.game > 1.0) || !(e.gamp > 1.0)) return GRMHD_ERR_INVALID;
     if (!(e.tpte_min >= 0.0) || !(e.tpte_max >= e.tpte_min)) return GRMHD_ERR_INVALID;
     if (e.model == GRMHD_ELEC_CONSTANT && !(e.fel >= 0.0 && e.fel <= 1.0)) return GRMHD_ERR_INVALID;
@@ -170,8 +169,8 @@ extern "C" int grmhd_footprint(const grmhd_grid *grid, const grmhd_metric *metri
     b += 2 * sizeof(float) * NV * tot;
   if (pr == GRMHD_PREC_FF || pr == GRMHD_PREC_MIXED_FF)  // split geometry and connection
     b += 2 * sizeof(float) * (NLOC * G_NCOMP + C_NCOMP) * n2d;
-  if (params->electrons.model)  // K, Kh, FK[3], KLf, KRf (2 each), Uek, ctop_face (3)
-    b += sizeof(double) * 18 * tot;
+  if (params->electrons.model)  // K, Kh, FK[3], KLf, KRf (2 each), Uek, elec_w (6)
+    b += sizeof(double) * 21 * tot;
   b += (size_t)plan_bytes(D, flat3_of(D, params), params->precision,
                          params->floors_on && params->floor_frame == GRMHD_FLOOR_DRIFT,
                          params->electrons.model != GRMHD_ELEC_OFF);
@@ -246,7 +245,7 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
          cudaMalloc(&s->FK[2], kb) == cudaSuccess && cudaMalloc(&s->KLf, kb) == cudaSuccess &&
          cudaMalloc(&s->KRf, kb) == cudaSuccess &&
          cudaMalloc(&s->Uek, sizeof(double) * (size_t)tot) == cudaSuccess &&
-         cudaMalloc(&s->ctop_face, sizeof(double) * 3 * (size_t)tot) == cudaSuccess;
+         cudaMalloc(&s->elec_w, sizeof(double) * 6 * (size_t)tot) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -316,7 +315,7 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
   A.fel_const = params->electrons.fel;
   A.tpte_min = params->electrons.tpte_min;
   A.tpte_max = params->electrons.tpte_max;
-  A.ctop_face = s->ctop_face;
+  A.elec_w = s->elec_w;
   for (int d = 0; d < 3; d++)
     for (int sd = 0; sd < 2; sd++) A.bc[d][sd] = params->bc[d][sd];
   A.flat3 = flat3_of(D, params);

@@ -7,9 +7,9 @@
 // mass.  Per stage, after the fluid's kernels:
 //   elec_recon_body<d> reconstructs both entropies at the two faces of every
 //                      zone along d (as recon_body does the primitives);
-//   elec_flux_body<d>  (after the face fluxes along d) forms their local
-//                      Lax-Friedrichs flux with the mass flux's ingredients
-//                      and the face's signal speed;
+//   elec_flux_body<d>  (after the face fluxes of every direction) forms their
+//                      local Lax-Friedrichs flux from the weights that the
+//                      face kernels (FP64, FP32 or float-float) stored;
 //   fix_flux_body      zeroes them where the mass flux is zeroed;
 //   elec_post_body     (after the update, whose bounds wait for it) carries
 //                      the entropies to the new state, heats the electrons by
@@ -136,16 +136,15 @@ __device__ __forceinline__ void elec_recon_body(const StepArgs &A, const double 
   }
 }
 
-// Entropy fluxes of one face along DIR (the face box of face_body), from the
-// face values of the zones on either side (K_L: high face of zone c-1, K_R:
-// low face of zone c) and the face states' mass terms:
-// F_K = sqrt(-g)/2 [rho_L u^d_L K_L + rho_R u^d_R K_R - c (rho_R u^t_R K_R - rho_L u^t_L K_L)]
-// with c the face's LLF speed.
+// Entropy fluxes of one face along DIR (the face box of face_body):
+// F_K = w_L K_L + w_R K_R with K_L the high-face value of zone c-1, K_R the
+// low-face value of zone c, and the weights the face kernel of the grid's
+// precision stored, w_L = sqrt(-g)/2 rho_L (u^d_L + c u^t_L),
+// w_R = sqrt(-g)/2 rho_R (u^d_R - c u^t_R) (c: the face's LLF speed), so
+// that F_K is the LLF combination of rho u^d K and rho u^t K.
 template <int DIR>
 __device__ __forceinline__ void elec_flux_body(const StepArgs &A, const double *__restrict__ KLf,
                                                const double *__restrict__ KRf,
-                                               const double *__restrict__ Lf,
-                                               const double *__restrict__ Rf,
                                                double *__restrict__ FK, long long t) {
   const Dims &D = A.D;
   int lo[3], ext[3];
@@ -156,32 +155,9 @@ __device__ __forceinline__ void elec_flux_body(const StepArgs &A, const double *
   const int k = lo[2] + (int)(t / ((long long)ext[0] * ext[1]));
   const long long c = zid(D, i, j, k), N = D.ntot;
   const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
-  const int loc = (DIR == 0) ? LOC_FACE1 : (DIR == 1) ? LOC_FACE2 : LOC_CENT;
-  Geo G;
-  load_geo(A.geom + (long long)loc * G_NCOMP * D.n2d, D.n2d, (long long)j * D.s[0] + i, G);
-  // rho u^d and rho u^t of the two face states
-  double m[2], dn[2];
+  const double wl = A.elec_w[(2 * DIR) * N + c], wr = A.elec_w[(2 * DIR + 1) * N + c];
 #pragma unroll
-  for (int side = 0; side < 2; side++) {
-    const double *S = side ? Lf : Rf;
-    const long long z = side ? c : c - st;
-    const double rho = S[RHO * N + z];
-    const double v1 = S[U1 * N + z], v2 = S[U2 * N + z], v3 = S[U3 * N + z];
-    const double qsq =
-        v1 * (G.gcov[SY(1, 1)] * v1 + G.gcov[SY(1, 2)] * v2 + G.gcov[SY(1, 3)] * v3) +
-        v2 * (G.gcov[SY(1, 2)] * v1 + G.gcov[SY(2, 2)] * v2 + G.gcov[SY(2, 3)] * v3) +
-        v3 * (G.gcov[SY(1, 3)] * v1 + G.gcov[SY(2, 3)] * v2 + G.gcov[SY(3, 3)] * v3);
-    const double gam = sqrt(1.0 + qsq);
-    const double vd = (DIR == 0) ? v1 : (DIR == 1) ? v2 : v3;
-    m[side] = rho * (vd - gam * G.alpha * G.gcon[SY(0, DIR + 1)]);
-    dn[side] = rho * (gam * G.ialpha);
-  }
-  const double ct = A.ctop_face[DIR * N + c];
-#pragma unroll
-  for (int q = 0; q < 2; q++) {
-    const double KL = KRf[q * N + c - st], KR = KLf[q * N + c];
-    FK[q * N + c] = 0.5 * G.gdet * (m[0] * KL + m[1] * KR - ct * (dn[1] * KR - dn[0] * KL));
-  }
+  for (int q = 0; q < 2; q++) FK[q * N + c] = wl * KRf[q * N + c - st] + wr * KLf[q * N + c];
 }
 
 // After the update: the entropies carried to the new state, U_K = U_rho(P_i)

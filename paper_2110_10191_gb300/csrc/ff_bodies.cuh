@@ -351,6 +351,12 @@ __device__ __forceinline__ void face_ff_body(const StepArgs &A, const float *__r
 #pragma unroll
     for (int v = 0; v < NV; v++)
       F[v * D.ntot + c] = ff_to(ff_mul(hg, acc[v])) * (v < B1 ? sc.s : sc.rs);
+    if (A.elec_w) {  // the electron entropies' flux weights (rho scales with s)
+      const ff wl = ff_mul(hg, ff_mul(PL[RHO], ff_add(sL.ucon[DIR + 1], ff_mul(ct, sL.ucon[0]))));
+      const ff wr = ff_mul(hg, ff_mul(PR[RHO], ff_sub(sR.ucon[DIR + 1], ff_mul(ct, sR.ucon[0]))));
+      A.elec_w[(2 * DIR) * D.ntot + c] = ff_to(wl) * sc.s;
+      A.elec_w[(2 * DIR + 1) * D.ntot + c] = ff_to(wr) * sc.s;
+    }
     bool interior = true;
 #pragma unroll
     for (int e = 0; e < 3; e++) {

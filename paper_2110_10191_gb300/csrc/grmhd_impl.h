@@ -43,7 +43,9 @@ struct StepArgs {
   // electrons and protons, the constant share, the bounds on T_p/T_e
   int elec;
   double game, gamp, fel_const, tpte_min, tpte_max;
-  double *ctop_face;  // electrons: the LLF speed of every face, [3][ntot]
+  // electrons: per face, the weights of the left and right entropies in
+  // their LLF flux, [3][2][ntot] (direction, side)
+  double *elec_w;
   int flat3;  // n3 = 1 with periodic X3: fluxes on the single k layer, copied
   // sides that continue into a neighbouring block of a decomposed grid (1)
   // rather than ending at a physical boundary (0): the fixup may average

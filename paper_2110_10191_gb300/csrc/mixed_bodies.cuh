@@ -99,6 +99,11 @@ __device__ __forceinline__ void face_f32_body(const StepArgs &A, const float *__
     const float hg = 0.5f * G.gdet;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v * D.ntot + c] = (double)(hg * acc[v]);
+    if (A.elec_w) {  // the electron entropies' flux weights, in FP32 as the fluxes
+      A.elec_w[(2 * DIR) * D.ntot + c] = (double)(hg * (PL[RHO] * (sL.ucon[DIR + 1] + ct * sL.ucon[0])));
+      A.elec_w[(2 * DIR + 1) * D.ntot + c] =
+          (double)(hg * (PR[RHO] * (sR.ucon[DIR + 1] - ct * sR.ucon[0])));
+    }
     bool interior = true;
 #pragma unroll
     for (int e = 0; e < 3; e++) {

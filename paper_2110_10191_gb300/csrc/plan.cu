@@ -180,7 +180,7 @@ template <int DIR>
 __global__ void kp_elec_flux(BView V) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
-  elec_flux_body<DIR>(it.A, it.KLf, it.KRf, it.Lf, it.Rf, it.FK[DIR], block_tid(V, g));
+  elec_flux_body<DIR>(it.A, it.KLf, it.KRf, it.FK[DIR], block_tid(V, g));
 }
 
 // stage in: P_s = arr(in), output arr(1 - in); kappa_i is always K (of P^n)
@@ -417,20 +417,12 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   int nl = plan_clock(p, 0, st, h);
   const int R = GRMHD_K_RECON, F = GRMHD_K_FLUX;
   // FP64 grids
-  // (electron entropy fluxes of each direction right after its face fluxes,
-  // before the next reconstruction overwrites the face states)
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EREC01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<0><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EFACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<0><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EREC01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<1><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EFACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<1><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EREC2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<2><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_EFACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<2><<<nb, bs, 0, st>>>(V); });
   // mixed-precision grids
   nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_f32<<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });
@@ -447,6 +439,14 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   nl += launch(p, PC_FACE1X, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<1><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_RECON2X, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<2><<<nb, bs, 0, st>>>(V); });
   nl += launch(p, PC_FACE2X, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_ff<2><<<nb, bs, 0, st>>>(V); });
+  // electron entropies (grids with electrons, any precision): per direction,
+  // reconstruction and the fluxes from the face kernels' weights
+  nl += launch(p, PC_EREC01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<0><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_EREC01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<1><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_EREC2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_recon<2><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_EFACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_elec_flux<2><<<nb, bs, 0, st>>>(V); });
   // flat-X3 grids
   nl += launch(p, PC_REPL, GRMHD_K_OTHER, h,
                [&](unsigned nb, unsigned bs, BView V) { kp_replicate<<<nb, bs, 0, st>>>(V); });

@@ -61,7 +61,7 @@ enum {
   PC_UPD64,  // FP64 update (FP64 and mixed-precision grids)
   PC_UPDX,   // float-float update (float-float and mixed + float-float grids)
   PC_FLOORD, // drift-frame bounds (grids with bounds in the drift frame, no electrons)
-  PC_EREC01, // electron entropy reconstruction along X1, X2 (FP64 grids with electrons)
+  PC_EREC01, // electron entropy reconstruction along X1, X2 (grids with electrons)
   PC_EREC2,  // along X3
   PC_EFACE0, // electron entropy fluxes per direction
   PC_EFACE1,

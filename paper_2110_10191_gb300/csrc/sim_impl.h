@@ -21,7 +21,7 @@ struct grmhd_sim {
   float *Pff, *geomff, *connff;  // split float-float copies (float-float mode only)
   // electrons only: entropies of the stage arrays, their fluxes, U_rho(P^n),
   // the faces' signal speeds
-  double *K, *Kh, *FK[3], *Uek, *ctop_face, *KLf, *KRf;
+  double *K, *Kh, *FK[3], *Uek, *elec_w, *KLf, *KRf;
   int *pflag, *fflag;
   grmhd::Clock *clk;
   unsigned long long unrec_seen, dterr_seen;

@@ -269,7 +269,10 @@ __device__ __forceinline__ void face_body(const StepArgs &A, const double *__res
     const double hg = 0.5 * G.gdet;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v * D.ntot + c] = hg * acc[v];
-    if (A.ctop_face) A.ctop_face[DIR * D.ntot + c] = ct;  // the electron fluxes use it
+    if (A.elec_w) {  // the electron entropies' flux weights (LLF of rho u^d K, rho u^t K)
+      A.elec_w[(2 * DIR) * D.ntot + c] = hg * (PL[RHO] * (sL.ucon[DIR + 1] + ct * sL.ucon[0]));
+      A.elec_w[(2 * DIR + 1) * D.ntot + c] = hg * (PR[RHO] * (sR.ucon[DIR + 1] - ct * sR.ucon[0]));
+    }
     bool interior = true;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
