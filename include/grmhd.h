@@ -114,8 +114,8 @@ typedef struct {
  *   CONSTANT  f_e = fel (not one of the paper's models; for tests)
  * Grids of every precision mode evolve them (the mass-flux weights of the
  * entropy fluxes come from the grid's face kernels, in their arithmetic;
- * everything else about the entropies is FP64); decomposed grids and the
- * server take none. */
+ * everything else about the entropies is FP64); decomposed grids exchange
+ * them with the primitives; the server takes none. */
 #define GRMHD_ELEC_OFF 0
 #define GRMHD_ELEC_CONSTANT 1
 #define GRMHD_ELEC_KAWAZURA 2
@@ -521,6 +521,12 @@ int grmhd_decomp_set_prims(grmhd_decomp *dc, const double *P, int with_ghosts);
 
 /* The global primitives into host memory, interior or with ghosts. */
 int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghosts);
+
+/* The global electron entropies (kappa_tot, kappa_e), [2][...] as
+ * grmhd_set_electrons, host memory; set them after the primitives.
+ * GRMHD_ERR_INVALID: the grid evolves no electrons. */
+int grmhd_decomp_set_electrons(grmhd_decomp *dc, const double *K, int with_ghosts);
+int grmhd_decomp_get_electrons(grmhd_decomp *dc, double *K, int with_ghosts);
 
 /* Advance nsteps cycles, as grmhd_step (stats: the blocks' counters summed). */
 int grmhd_decomp_step(grmhd_decomp *dc, int nsteps, grmhd_stats *stats);

@@ -12,7 +12,8 @@
 // there.  The signal-speed maxima are combined over the blocks before the
 // time step, and before the fixup the first layer of primitives and failure
 // flags is exchanged, so a failed zone at a block edge averages over the
-// same neighbours as in the undecomposed grid.  The evolution is therefore
+// same neighbours as in the undecomposed grid.  Blocks that evolve the
+// electron entropies exchange them with the primitives in both.  The evolution is therefore
 // bitwise independent of the decomposition (the paper's decomposition
 // tests, end of its "Tests" section).
 #include <cstring>
@@ -36,6 +37,7 @@ struct XDesc {
   int lo[3], ext[3], shift[3];
   int nvars;  // primitives copied (the first nvars)
   int flag;   // 1: the failure flags too
+  int kvars;  // electron entropies copied (blocks that evolve them: 2)
 };
 
 __global__ void kx_exchange(const StageItem *__restrict__ items, const XDesc *__restrict__ desc,
@@ -53,6 +55,11 @@ __global__ void kx_exchange(const StageItem *__restrict__ items, const XDesc *__
   const double *Ps = which ? s.Ph : s.P;
   for (int v = 0; v < x.nvars; v++) Pd[v * d.A.D.ntot + cd] = Ps[v * s.A.D.ntot + cs];
   if (x.flag) d.pflag[cd] = s.pflag[cs];
+  if (x.kvars) {
+    double *Kd = which ? d.Kh : d.K;
+    const double *Ks = which ? s.Kh : s.K;
+    for (int q = 0; q < x.kvars; q++) Kd[q * d.A.D.ntot + cd] = Ks[q * s.A.D.ntot + cs];
+  }
 }
 
 // the signal-speed maxima of all blocks, given to every block
@@ -160,7 +167,6 @@ extern "C" int grmhd_decomp_create(const grmhd_grid *grid, const grmhd_metric *m
   Dims G;
   int rc = validate_problem(grid, metric, params, &G);
   if (rc != GRMHD_OK) return rc;
-  if (params->electrons.model != GRMHD_ELEC_OFF) return GRMHD_ERR_INVALID;  // not exchanged
   for (int d = 0; d < 3; d++) {
     if (nblocks[d] < 1 || nblocks[d] > G.n[d]) return GRMHD_ERR_INVALID;
     if (nblocks[d] > 1 && G.n[d] / nblocks[d] < NG) return GRMHD_ERR_INVALID;  // blocks >= NG zones
@@ -261,6 +267,7 @@ extern "C" int grmhd_decomp_create(const grmhd_grid *grid, const grmhd_metric *m
               x.shift[d] = side ? -sp.n[d] : nsrc;
               x.nvars = kind ? 5 : NV;
               x.flag = kind;
+              x.kvars = params->electrons.model != GRMHD_ELEC_OFF ? 2 : 0;
               (kind ? layer : full)[d].push_back(x);
             }
           }
@@ -286,8 +293,11 @@ extern "C" int grmhd_decomp_destroy(grmhd_decomp *dc) {
   return GRMHD_OK;
 }
 
-extern "C" int grmhd_decomp_set_prims(grmhd_decomp *dc, const double *P, int with_ghosts) {
-  if (!dc || !P) return GRMHD_ERR_INVALID;
+// The global array of nvar variables (interior or with ghosts) into the
+// blocks' stage array 0 (the primitives, or the electron entropies with
+// elec), then the ghost fill.
+static int set_global(grmhd_decomp *dc, const double *P, int with_ghosts, bool elec) {
+  const int nvar = elec ? 2 : NV;
   const int gn[3] = {dc->grid.n1, dc->grid.n2, dc->grid.n3};
   const long long gs0 = gn[0] + 2 * NG, gs1 = gn[1] + 2 * NG, gs2 = gn[2] + 2 * NG;
   const long long gtot = gs0 * gs1 * gs2;
@@ -295,9 +305,9 @@ extern "C" int grmhd_decomp_set_prims(grmhd_decomp *dc, const double *P, int wit
   std::vector<double> g;
   const double *src = P;
   if (!with_ghosts) {
-    g.assign((size_t)(NV * gtot), 0.0);
+    g.assign((size_t)(nvar * gtot), 0.0);
     const long long nz = (long long)gn[0] * gn[1] * gn[2];
-    for (int v = 0; v < NV; v++)
+    for (int v = 0; v < nvar; v++)
       for (int k = 0; k < gn[2]; k++)
         for (int j = 0; j < gn[1]; j++)
           memcpy(&g[(size_t)(v * gtot + ((k + NG) * gs1 + j + NG) * gs0 + NG)],
@@ -308,31 +318,37 @@ extern "C" int grmhd_decomp_set_prims(grmhd_decomp *dc, const double *P, int wit
     grmhd_sim *s = dc->blocks[b];
     const BlockSpec &sp = dc->spec[b];
     const Dims &D = s->D;
-    std::vector<double> h((size_t)(NV * D.ntot));
-    for (int v = 0; v < NV; v++)
+    std::vector<double> h((size_t)(nvar * D.ntot));
+    for (int v = 0; v < nvar; v++)
       for (int k = 0; k < D.s[2]; k++)
         for (int j = 0; j < D.s[1]; j++)
           memcpy(&h[(size_t)(v * D.ntot + ((long long)k * D.s[1] + j) * D.s[0])],
                  src + v * gtot + ((long long)(k + sp.off[2]) * gs1 + (j + sp.off[1])) * gs0 + sp.off[0],
                  sizeof(double) * D.s[0]);
-    if (cudaMemcpyAsync(s->P, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, dc->st) !=
-            cudaSuccess ||
+    if (cudaMemcpyAsync(elec ? s->K : s->P, h.data(), sizeof(double) * h.size(),
+                        cudaMemcpyHostToDevice, dc->st) != cudaSuccess ||
         cudaStreamSynchronize(dc->st) != cudaSuccess)
       return GRMHD_ERR_CUDA;
   }
   fill(dc, 0);
   // the ghosts of a fixed side keep their set values in both stage arrays
-  for (grmhd_sim *s : dc->blocks)
+  for (grmhd_sim *s : dc->blocks) {
     if (cudaMemcpyAsync(s->Ph, s->P, sizeof(double) * NV * (size_t)s->D.ntot, cudaMemcpyDeviceToDevice,
                         dc->st) != cudaSuccess)
       return GRMHD_ERR_CUDA;
+    if (s->K && cudaMemcpyAsync(s->Kh, s->K, sizeof(double) * 2 * (size_t)s->D.ntot,
+                                cudaMemcpyDeviceToDevice, dc->st) != cudaSuccess)
+      return GRMHD_ERR_CUDA;
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(dc->st) != cudaSuccess)
     return GRMHD_ERR_CUDA;
   return GRMHD_OK;
 }
 
-extern "C" int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghosts) {
-  if (!dc || !P) return GRMHD_ERR_INVALID;
+// The blocks' stage array 0 (primitives or electron entropies) as the
+// global array, interior or with ghosts.
+static int get_global(grmhd_decomp *dc, double *P, int with_ghosts, bool elec) {
+  const int nvar = elec ? 2 : NV;
   const int gn[3] = {dc->grid.n1, dc->grid.n2, dc->grid.n3};
   const long long gs[3] = {gn[0] + 2 * NG, gn[1] + 2 * NG, gn[2] + 2 * NG};
   const long long gtot = gs[0] * gs[1] * gs[2], nz = (long long)gn[0] * gn[1] * gn[2];
@@ -340,9 +356,9 @@ extern "C" int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghos
     grmhd_sim *s = dc->blocks[b];
     const BlockSpec &sp = dc->spec[b];
     const Dims &D = s->D;
-    std::vector<double> h((size_t)(NV * D.ntot));
-    if (cudaMemcpyAsync(h.data(), s->P, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, dc->st) !=
-            cudaSuccess ||
+    std::vector<double> h((size_t)(nvar * D.ntot));
+    if (cudaMemcpyAsync(h.data(), elec ? s->K : s->P, sizeof(double) * h.size(),
+                        cudaMemcpyDeviceToHost, dc->st) != cudaSuccess ||
         cudaStreamSynchronize(dc->st) != cudaSuccess)
       return GRMHD_ERR_CUDA;
     // the zones this block owns: its interior, and the global ghosts beyond
@@ -354,7 +370,7 @@ extern "C" int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghos
       lo[d] = (with_ghosts && c[d] == 0) ? 0 : NG;
       hi[d] = (with_ghosts && c[d] == dc->nb[d] - 1) ? sp.n[d] + 2 * NG : sp.n[d] + NG;
     }
-    for (int v = 0; v < NV; v++)
+    for (int v = 0; v < nvar; v++)
       for (int k = lo[2]; k < hi[2]; k++)
         for (int j = lo[1]; j < hi[1]; j++) {
           const double *row = &h[(size_t)(v * D.ntot + ((long long)k * D.s[1] + j) * D.s[0] + lo[0])];
@@ -365,6 +381,26 @@ extern "C" int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghos
         }
   }
   return GRMHD_OK;
+}
+
+extern "C" int grmhd_decomp_set_prims(grmhd_decomp *dc, const double *P, int with_ghosts) {
+  if (!dc || !P) return GRMHD_ERR_INVALID;
+  return set_global(dc, P, with_ghosts, false);
+}
+
+extern "C" int grmhd_decomp_get_prims(grmhd_decomp *dc, double *P, int with_ghosts) {
+  if (!dc || !P) return GRMHD_ERR_INVALID;
+  return get_global(dc, P, with_ghosts, false);
+}
+
+extern "C" int grmhd_decomp_set_electrons(grmhd_decomp *dc, const double *K, int with_ghosts) {
+  if (!dc || !K || dc->params.electrons.model == GRMHD_ELEC_OFF) return GRMHD_ERR_INVALID;
+  return set_global(dc, K, with_ghosts, true);
+}
+
+extern "C" int grmhd_decomp_get_electrons(grmhd_decomp *dc, double *K, int with_ghosts) {
+  if (!dc || !K || dc->params.electrons.model == GRMHD_ELEC_OFF) return GRMHD_ERR_INVALID;
+  return get_global(dc, K, with_ghosts, true);
 }
 
 extern "C" int grmhd_decomp_step(grmhd_decomp *dc, int nsteps, grmhd_stats *stats) {

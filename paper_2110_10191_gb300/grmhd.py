@@ -119,6 +119,7 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_server_now", "grmhd_server_destroy", "grmhd_decomp_create", "grmhd_decomp_destroy",
            "grmhd_decomp_set_prims", "grmhd_decomp_get_prims", "grmhd_decomp_step",
            "grmhd_decomp_get_stats", "grmhd_set_electrons", "grmhd_get_electrons",
+           "grmhd_decomp_set_electrons", "grmhd_decomp_get_electrons",
            "grmhd_strerror"]
 
 
@@ -184,6 +185,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_decomp_destroy.argtypes = [vp]
         L.grmhd_decomp_set_prims.argtypes = [vp, vp, i]
         L.grmhd_decomp_get_prims.argtypes = [vp, vp, i]
+        L.grmhd_decomp_set_electrons.argtypes = [vp, vp, i]
+        L.grmhd_decomp_get_electrons.argtypes = [vp, vp, i]
         L.grmhd_decomp_step.argtypes = [vp, i, P(grmhd_stats)]
         L.grmhd_decomp_get_stats.argtypes = [vp, P(grmhd_stats), i]
         L.grmhd_strerror.argtypes = [i]
@@ -604,6 +607,24 @@ class Decomp:
         out = np.zeros((NPRIM,) + (self.s[::-1] if with_ghosts else self.n[::-1]))
         _check(self.L.grmhd_decomp_get_prims(self.h, out.ctypes.data, int(with_ghosts)),
                "grmhd_decomp_get_prims")
+        return out
+
+    def set_electrons(self, K) -> None:
+        a = np.ascontiguousarray(K, dtype=np.float64)
+        n1, n2, n3 = self.n
+        if a.shape == (2, n3, n2, n1):
+            ghosts = 0
+        elif a.shape == (2,) + self.s[::-1]:
+            ghosts = 1
+        else:
+            raise ValueError("bad electron shape %s" % (a.shape,))
+        _check(self.L.grmhd_decomp_set_electrons(self.h, a.ctypes.data, ghosts),
+               "grmhd_decomp_set_electrons")
+
+    def get_electrons(self, with_ghosts: bool = False) -> np.ndarray:
+        out = np.zeros((2,) + (self.s[::-1] if with_ghosts else self.n[::-1]))
+        _check(self.L.grmhd_decomp_get_electrons(self.h, out.ctypes.data, int(with_ghosts)),
+               "grmhd_decomp_get_electrons")
         return out
 
     def step(self, nsteps: int = 1):

@@ -12,7 +12,8 @@ oracle's electron thermodynamics.
 * Every precision mode evolves them: float-float grids within that mode's
   bar (3e-11) of the oracle, the FP32-flux modes within the mixed mode's
   (1e-5); batches mixing the modes stay bitwise.
-* Decomposition and serving refuse electrons.
+* Decomposed grids exchange the entropies: bitwise the whole grid's.
+* Serving refuses electrons.
 """
 import dataclasses
 import math
@@ -222,10 +223,31 @@ def test_electron_batch_of_all_precisions(grmhd):
         s.close()
 
 
+@pytest.mark.parametrize("nb,prec", [((2, 2, 2), 0), ((1, 3, 2), 3)])
+def test_electron_decomposition_bitwise(grmhd, nb, prec):
+    """Blocks exchange the entropies with the primitives: the decomposed
+    evolution is bitwise the whole grid's, entropies included."""
+    pr = dataclasses.replace(pb.with_electrons(pb.fm_torus(24, 20, 8), model=pb.ELEC_KAWAZURA),
+                             precision=prec)
+    s = grmhd.Sim(pr)
+    s.set_prims(pr.P)
+    s.set_electrons(pr.K)
+    s.step(3)
+    P, K = s.get_prims(with_ghosts=True), s.get_electrons(with_ghosts=True)
+    st = s.stats()
+    s.close()
+    d = grmhd.Decomp(pr, nb)
+    d.set_prims(pr.P)
+    d.set_electrons(pr.K)
+    sd = d.step(3)
+    assert np.array_equal(d.get_prims(with_ghosts=True), P)
+    assert np.array_equal(d.get_electrons(with_ghosts=True), K)
+    assert sd["floor_hits"] == st["floor_hits"] and sd["inv_failures"] == st["inv_failures"]
+    d.close()
+
+
 def test_electron_refusals(grmhd):
     pr = pb.with_electrons(pb.fm_torus(12, 12, 4), model=pb.ELEC_KAWAZURA)
-    with pytest.raises(Exception):
-        grmhd.Decomp(pr, (2, 1, 1))
     bad = dict(pr.electrons, game=1.0)
     with pytest.raises(Exception):
         grmhd.Sim(dataclasses.replace(pr, electrons=bad))
@@ -233,3 +255,6 @@ def test_electron_refusals(grmhd):
     with pytest.raises(Exception):
         s.set_electrons(pr.K)
     s.close()
+    with grmhd.Server() as srv:
+        with pytest.raises(Exception):
+            srv.submit(1, pr, 2)
