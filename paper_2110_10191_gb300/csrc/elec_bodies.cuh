@@ -35,8 +35,8 @@ constexpr int FF_KTOT = 256;              // bound flag: u lowered for kappa_tot
 
 // Heating share f_e of a zone (rho, u, kappa_e, b^2; lr = ln rho); models as
 // documented with GRMHD_ELEC_* in grmhd.h.
-__device__ __noinline__ double elec_fraction(const StepArgs &A, double rho, double lr, double u,
-                                             double kel, double bsq) {
+static __device__ __noinline__ double elec_fraction(const StepArgs &A, double rho, double lr,
+                                                    double u, double kel, double bsq) {
   if (A.elec == GRMHD_ELEC_CONSTANT) return A.fel_const;
   const double ue = kel * exp(A.game * lr) / (A.game - 1.0);
   const double Te = fabs((A.game - 1.0) * ue / rho);
