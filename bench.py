@@ -351,6 +351,30 @@ def variant_throughput(grmhd, pr, steps, warmup, stream, what):
             "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()}}
 
 
+def small_single(grmhd, steps, stream):
+    """The 64x64 fast mode (the accuracy workload, far too small to fill the
+    GPU) stepped alone: one grmhd_step call of `steps` cycles (a graph
+    replay per cycle) against `steps` calls of one cycle (one host launch per
+    kernel)."""
+    import dataclasses
+    pr = dataclasses.replace(make_problem("mode64"), t_final=0.0)  # no end time: every cycle works
+    out = {}
+    for graph in (True, False):
+        s = grmhd.Sim(pr, stream=stream)
+        s.set_prims(pr.P)
+        s.step(3)
+        if graph:
+            out[graph] = _timed(stream, lambda: s.step(steps, sync=False)) / steps
+        else:
+            out[graph] = _timed(stream, lambda: [s.step(1, sync=False) for _ in range(steps)]) / steps
+        s.close()
+    z = pr.n[0] * pr.n[1] * pr.n[2]
+    return {"workload": WORKLOADS["mode64"]["label"], "steps": steps,
+            "graph_ms_per_step": out[True], "direct_ms_per_step": out[False],
+            "graph_value": z / (out[True] * 1e-3), "unit": UNIT,
+            "speedup": out[False] / out[True]}
+
+
 def batched_throughput(grmhd, steps, warmup, stream, nmin=32, nmax=256):
     """64 uneven flat 2D grids (slow/Alfven/fast modes, Orszag-Tang) stepped
     as one batch (one CUDA graph per step), before and after the autotuner,
@@ -630,6 +654,7 @@ def main():
                                                    stream, "drift")
         extras["electrons"] = variant_throughput(grmhd, pr, max(args.steps // 2, 5), args.warmup,
                                                  stream, "electrons")
+        extras["single_small"] = small_single(grmhd, 200, stream)
         extras["batched"] = batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, stream)
         extras["batched_small"] = batched_throughput(grmhd, args.steps, args.warmup, stream,
                                                      nmin=32, nmax=48)

@@ -203,7 +203,11 @@ int grmhd_get_electrons(grmhd_sim *sim, double *K, int with_ghosts, int on_devic
  * stats == NULL: returns after enqueueing (errors of this call surface at
  * the next synchronising call).  stats != NULL: synchronises, fills *stats
  * and returns GRMHD_ERR_INVERSION if any failed zone had no valid neighbour
- * since the previous synchronising call. */
+ * since the previous synchronising call.  With nsteps >= 2 and profiling
+ * off, the cycles are replays of a CUDA graph of one cycle (captured on the
+ * first such call, on a stream of the simulation's own that is ordered
+ * after and before the simulation's stream): the same kernels and results,
+ * without a host launch per kernel. */
 int grmhd_step(grmhd_sim *sim, int nsteps, grmhd_stats *stats);
 
 /* Synchronise and read the running statistics. */

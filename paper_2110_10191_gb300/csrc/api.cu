@@ -18,6 +18,14 @@ using namespace grmhd;
 
 // Counts the launches of each kernel class and, when profiling, records an
 // event pair on the stream around each launch.
+// Counts the launches per class of a captured cycle.
+struct CountHook : PlanHook {
+  long long *n;
+  explicit CountHook(long long *n_) : n(n_) {}
+  void begin(int cls, int nlaunch) override { n[cls] += nlaunch; }
+  void end(int) override {}
+};
+
 struct SimHook : PlanHook {
   grmhd_sim *s;
   cudaEvent_t e0;
@@ -78,6 +86,11 @@ static void free_all(grmhd_sim *s) {
     s->prof_ev = nullptr;
     s->ev_pool = nullptr;
   }
+  sim_drop_graph(s);
+  if (s->gev) cudaEventDestroy(s->gev);
+  if (s->gst) cudaStreamDestroy(s->gst);
+  s->gev = nullptr;
+  s->gst = nullptr;
   plan_free(s->plan);
   double *d[] = {s->P,      s->Ph,    s->F[0], s->F[1], s->F[2],  s->emf,
                  s->Lf,     s->Rf,    s->Uc,   s->geom, s->conn,  s->floors,
@@ -491,9 +504,58 @@ static int read_stats(grmhd_sim *s, grmhd_stats *out, bool check) {
   return rc;
 }
 
+void sim_drop_graph(grmhd_sim *s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->gexec = nullptr;
+  s->graph = nullptr;
+}
+
+// nsteps cycles as replays of a CUDA graph of one cycle, captured on first
+// use on the simulation's own capture stream, which waits for the work
+// already enqueued on st and which st then waits for.  The graph runs the
+// same kernels with the same arguments as direct launches.
+static int step_graph(grmhd_sim *s, int nsteps) {
+  if (!s->gst) {
+    if (cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->gev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return GRMHD_ERR_CUDA;
+    }
+  }
+  CK(cudaEventRecord(s->gev, s->st));
+  CK(cudaStreamWaitEvent(s->gst, s->gev, 0));
+  if (!s->gexec) {
+    long long n[GRMHD_NKCLASS] = {0};
+    CK(cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal));
+    {
+      CountHook h(n);
+      plan_steps(s->plan, 1, s->gst, &h);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s->gst, &g);
+    if (e != cudaSuccess || !g || cudaGraphInstantiate(&s->gexec, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      s->gexec = nullptr;
+      cudaGetLastError();
+      return GRMHD_ERR_CUDA;
+    }
+    s->graph = g;
+    memcpy(s->graph_launches, n, sizeof(n));
+  }
+  for (int q = 0; q < nsteps; q++) CK(cudaGraphLaunch(s->gexec, s->gst));
+  for (int c = 0; c < GRMHD_NKCLASS; c++) s->launches[c] += nsteps * s->graph_launches[c];
+  CK(cudaEventRecord(s->gev, s->gst));
+  CK(cudaStreamWaitEvent(s->st, s->gev, 0));
+  return GRMHD_OK;
+}
+
 extern "C" int grmhd_step(grmhd_sim *s, int nsteps, grmhd_stats *stats) {
   if (!s || nsteps < 0) return GRMHD_ERR_INVALID;
-  {
+  if (nsteps >= 2 && !s->prof_on) {  // many cycles, no per-class timing: replay a graph
+    const int rc = step_graph(s, nsteps);
+    if (rc != GRMHD_OK) return rc;
+  } else {
     SimHook h(s);
     plan_steps(s->plan, nsteps, s->st, &h);
   }
@@ -689,6 +751,7 @@ extern "C" int grmhd_divb(grmhd_sim *s, double *divb_max, double *gb_max) {
 
 extern "C" int grmhd_autotune(grmhd_sim *s, int trials, double *ms_before, double *ms_after) {
   if (!s || trials < 1) return GRMHD_ERR_INVALID;
+  sim_drop_graph(s);  // the launch shapes may change
   return plan_autotune(s->plan, trials, s->st, ms_before, ms_after);
 }
 

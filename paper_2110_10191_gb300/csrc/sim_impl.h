@@ -33,7 +33,17 @@ struct grmhd_sim {
   std::vector<cudaEvent_t> *ev_pool;
   long long launches[GRMHD_NKCLASS];
   double prof_ms[GRMHD_NKCLASS];
+  // grmhd_step's CUDA graph of one cycle (replayed on gst, ordered after and
+  // before st by gev), with the kernels it launches per class
+  cudaStream_t gst;
+  cudaEvent_t gev;
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  long long graph_launches[GRMHD_NKCLASS];
 };
+
+// drop grmhd_step's graph (the launch shapes it holds changed)
+void sim_drop_graph(grmhd_sim *s);
 
 
 // A block of a decomposed grid: the global index of its first interior
