@@ -59,14 +59,15 @@ __global__ void __launch_bounds__(BS_MAX) kp_recon(BView V, int in) {
     recon_body<DIR, 0>(it.A, Ps, it.Lf, it.Rf, t);
 }
 
-template <int DIR>
+// ELEC: the grids of the launch evolve electron entropies (a class of their own)
+template <int DIR, bool ELEC = false>
 __global__ void __launch_bounds__(BS_MAX) kp_face(BView V, int in) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
   const double *Lf = it.Lf, *Rf = it.Rf;
   if (DIR == 2 && it.A.flat3) Lf = Rf = arr(it, in);  // flat X3: the primitives
-  face_body<DIR>(it.A, Lf, Rf, it.F[DIR], t);
+  face_body<DIR, ELEC>(it.A, Lf, Rf, it.F[DIR], t);
 }
 
 __global__ void kp_to_f32(BView V, int in) {
@@ -303,7 +304,8 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
   c[PC_RECON01] = f64 ? n_recon(D, fl) : 0;
   c[PC_RECON2] = (f64 && !fl) ? n_recon(D, 0) : 0;
   for (int d = 0; d < 3; d++) {
-    c[PC_FACE0 + d] = f64 ? n_face(D, d, fl) : 0;
+    c[PC_FACE0 + d] = (f64 && !elec) ? n_face(D, d, fl) : 0;
+    c[PC_FACE0E + d] = (f64 && elec) ? n_face(D, d, fl) : 0;
     c[PC_FACE0F + d] = mx ? n_face(D, d, fl) : 0;
     c[PC_FACE0X + d] = fx ? n_face(D, d, fl) : 0;
   }
@@ -419,10 +421,13 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   // FP64 grids
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_FACE0E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0, true><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_FACE1E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1, true><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE2, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_FACE2E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2, true><<<nb, bs, 0, st>>>(V, in); });
   // mixed-precision grids
   nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_f32<<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });

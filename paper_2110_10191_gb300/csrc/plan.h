@@ -42,6 +42,9 @@ enum {
   PC_FACE0,
   PC_FACE1,
   PC_FACE2,
+  PC_FACE0E,  // FP64 face fluxes of grids with electrons (they also store the entropy weights)
+  PC_FACE1E,
+  PC_FACE2E,
   PC_TOF32,  // mixed: FP32 copy of the stage input
   PC_RECON01F,
   PC_RECON2F,

@@ -226,7 +226,8 @@ __device__ __forceinline__ void recon_body(const StepArgs &A, const double *__re
 
 // One thread per face combines Rf of zone c-1 (left state) and Lf of zone c
 // (right state) into the LLF flux; every thread of the block must call it.
-template <int DIR>
+// ELEC: the grid evolves electron entropies, whose flux weights it stores.
+template <int DIR, bool ELEC = false>
 __device__ __forceinline__ void face_body(const StepArgs &A, const double *__restrict__ Lf,
                                           const double *__restrict__ Rf, double *__restrict__ F,
                                           long long t) {
@@ -265,13 +266,14 @@ __device__ __forceinline__ void face_body(const StepArgs &A, const double *__res
 #pragma unroll
     for (int v = 0; v < NV; v++) acc[v] = 0.0;
     flux_cons_acc(PL, sL, A.gam, DIR + 1, ct, acc);
+    const double mL = acc[RHO];  // rho_L (u^d_L + ct u^t_L): the left mass term
     flux_cons_acc(PR, sR, A.gam, DIR + 1, -ct, acc);
     const double hg = 0.5 * G.gdet;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v * D.ntot + c] = hg * acc[v];
-    if (A.elec_w) {  // the electron entropies' flux weights (LLF of rho u^d K, rho u^t K)
-      A.elec_w[(2 * DIR) * D.ntot + c] = hg * (PL[RHO] * (sL.ucon[DIR + 1] + ct * sL.ucon[0]));
-      A.elec_w[(2 * DIR + 1) * D.ntot + c] = hg * (PR[RHO] * (sR.ucon[DIR + 1] - ct * sR.ucon[0]));
+    if (ELEC) {  // the electron entropies' flux weights (LLF of rho u^d K, rho u^t K)
+      A.elec_w[(2 * DIR) * D.ntot + c] = hg * mL;
+      A.elec_w[(2 * DIR + 1) * D.ntot + c] = hg * (acc[RHO] - mL);
     }
     bool interior = true;
 #pragma unroll
