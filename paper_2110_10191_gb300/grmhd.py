@@ -205,14 +205,19 @@ def _check(rc, where):
 
 
 def _ptr(a):
-    """(pointer, on_device) of a numpy array or a torch tensor."""
+    """(pointer, on_device) of a C-contiguous float64 numpy array or torch
+    tensor (the library reads and writes doubles)."""
     if isinstance(a, np.ndarray):
         if not a.flags["C_CONTIGUOUS"]:
             raise ValueError("array must be C-contiguous")
+        if a.dtype != np.float64:
+            raise ValueError("array must be float64, not %s" % a.dtype)
         return a.ctypes.data, 0
     if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if str(a.dtype) != "torch.float64":
+            raise ValueError("tensor must be torch.float64, not %s" % a.dtype)
         return a.data_ptr(), 1 if a.is_cuda else 0
     raise TypeError("expected a numpy array or a torch tensor")
 

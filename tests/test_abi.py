@@ -41,3 +41,19 @@ def test_strerror_without_gpu():
     L = grmhd.load()
     assert L.grmhd_strerror(0) == b"ok"
     assert L.grmhd_strerror(-4) == b"failed zone with no valid neighbour"
+
+
+def test_buffers_must_be_contiguous_float64():
+    """The binding hands the library raw pointers to doubles: other dtypes
+    and non-contiguous views are refused before any call."""
+    import numpy as np
+    from paper_2110_10191_gb300 import grmhd
+    assert grmhd._ptr(np.zeros((2, 3)))[1] == 0
+    with pytest.raises(ValueError):
+        grmhd._ptr(np.zeros(3, dtype=np.float32))
+    with pytest.raises(ValueError):
+        grmhd._ptr(np.zeros((4, 4))[:, ::2])
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        grmhd._ptr(torch.zeros(3, dtype=torch.float32))
+    assert grmhd._ptr(torch.zeros(3, dtype=torch.float64))[1] == 0
