@@ -161,7 +161,7 @@ extern "C" int grmhd_batch_set_launch(grmhd_batch *b, int kclass, int threads, i
   } else {
     return GRMHD_ERR_INVALID;
   }
-  if (threads < 64 || threads > 256 || threads % 32 || order < 0 || order >= SCHED_N)
+  if (threads < 64 || threads > 256 || threads % 32 || order < 0 || order >= PLAN_SCHED_N)
     return GRMHD_ERR_INVALID;
   drop_graph(b);
   for (int q = 0; q < ncls; q++) {

@@ -6,6 +6,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/grmhd.h"
 #include "grmhd_impl.h"
 #include "ff_bodies.cuh"
@@ -231,14 +233,22 @@ BView view(const Plan &p, int cls) {
   return V;
 }
 
+// NVTX range names of the kernel classes (GRMHD_K_*): a timeline tool sees
+// every launch under its class; without a tool the ranges cost a pointer test.
+const char *const KCLASS_NAME[GRMHD_NKCLASS] = {"grmhd:flux",  "grmhd:dt",     "grmhd:ct",
+                                                 "grmhd:update", "grmhd:fixup", "grmhd:bounds",
+                                                 "grmhd:other", "grmhd:recon"};
+
 // Launch one kernel of class cls (skipped when no grid has blocks in it),
-// bracketed for the hook as kernel class kclass.
+// bracketed for the hook and an NVTX range as kernel class kclass.
 template <typename L>
 int launch(const Plan &p, int cls, int kclass, PlanHook *h, L &&body) {
   if (p.nblocks[cls] <= 0) return 0;
+  nvtxRangePushA(KCLASS_NAME[kclass]);
   if (h) h->begin(kclass, 1);
   body((unsigned)p.nblocks[cls], (unsigned)p.bs[cls], view(p, cls));
   if (h) h->end(kclass);
+  nvtxRangePop();
   return 1;
 }
 
@@ -259,7 +269,7 @@ int upload_tables(Plan &p) {
     std::vector<int> map, loc;
     map.reserve((size_t)tot);
     loc.reserve((size_t)tot);
-    if (p.sched[q] == SCHED_RR) {
+    if (p.sched[q] == PLAN_SCHED_RR) {
       for (long long r = 0; (long long)map.size() < tot; r++)
         for (int g = 0; g < n; g++)
           if (r < nb[g]) {
@@ -269,7 +279,7 @@ int upload_tables(Plan &p) {
     } else {
       std::vector<int> order(n);
       for (int g = 0; g < n; g++) order[g] = g;
-      if (p.sched[q] == SCHED_LPT)
+      if (p.sched[q] == PLAN_SCHED_LPT)
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[a] > nb[b]; });
       for (int g : order)
         for (long long r = 0; r < nb[g]; r++) {
@@ -359,7 +369,7 @@ int plan_build(Plan &p, const StageItem *items, int n) {
   }
   for (int q = 0; q < PC_N; q++) {
     p.bs[q] = BS;
-    p.sched[q] = SCHED_GRID;
+    p.sched[q] = PLAN_SCHED_GRID;
   }
   p.zones = zones;
   p.tab_cap = cap;
@@ -391,7 +401,7 @@ void plan_free(Plan &p) {
 }
 
 int plan_set_class(Plan &p, int cls, int bs, int sched) {
-  if (cls < 0 || cls >= PC_N || bs < 64 || bs > BS_MAX || bs % 32 || sched < 0 || sched >= SCHED_N)
+  if (cls < 0 || cls >= PC_N || bs < 64 || bs > BS_MAX || bs % 32 || sched < 0 || sched >= PLAN_SCHED_N)
     return GRMHD_ERR_INVALID;
   // kernels still in flight may read the tables
   if (cudaDeviceSynchronize() != cudaSuccess) return GRMHD_ERR_CUDA;
@@ -642,7 +652,7 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     before += best;
     int best_bs = bs0, best_sc = sc0;
     for (int bs : sizes)
-      for (int sc = 0; sc < (n > 1 ? SCHED_N : 1); sc++) {
+      for (int sc = 0; sc < (n > 1 ? PLAN_SCHED_N : 1); sc++) {
         if (bs == bs0 && sc == sc0) continue;
         rc = plan_set_class(p, gr.cls, bs, sc);
         if (rc != GRMHD_OK) break;

@@ -75,10 +75,10 @@ enum {
 
 // block order of a launch class
 enum {
-  SCHED_GRID = 0,  // grids in plan order, each grid's blocks contiguous
-  SCHED_LPT = 1,   // grids by decreasing block count (largest first), contiguous
-  SCHED_RR = 2,    // round robin: one block of each grid that has blocks left, in turn
-  SCHED_N
+  PLAN_SCHED_GRID = 0,  // grids in plan order, each grid's blocks contiguous
+  PLAN_SCHED_LPT = 1,   // grids by decreasing block count (largest first), contiguous
+  PLAN_SCHED_RR = 2,    // round robin: one block of each grid that has blocks left, in turn
+  PLAN_SCHED_N
 };
 
 struct Plan {
