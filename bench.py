@@ -60,14 +60,20 @@ NCU_FP64_PIPE = {"torus128": {"recon": 0.855, "flux": 0.889, "update": 0.887}}
 
 
 def kernel_source_hash():
+    """Hash of the translation unit that compiles the step kernels (plan.cu,
+    every header under csrc/, the public header): the measured kernels'
+    source, not the host-side files that only launch or hold them."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2110_10191_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2110_10191_gb300", "csrc")
+    files = [os.path.join(csrc, "plan.cu")] + sorted(glob.glob(os.path.join(csrc, "*.h")) +
+                                                   glob.glob(os.path.join(csrc, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "grmhd.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -115,7 +115,8 @@ typedef struct {
  * Grids of every precision mode evolve them (the mass-flux weights of the
  * entropy fluxes come from the grid's face kernels, in their arithmetic;
  * everything else about the entropies is FP64); decomposed grids exchange
- * them with the primitives; the server takes none. */
+ * them with the primitives; server requests carry them
+ * (grmhd_server_submit_electrons). */
 #define GRMHD_ELEC_OFF 0
 #define GRMHD_ELEC_CONSTANT 1
 #define GRMHD_ELEC_KAWAZURA 2
@@ -474,6 +475,16 @@ int grmhd_server_submit(grmhd_server *srv, long long id, const grmhd_grid *grid,
                         const grmhd_metric *metric, const grmhd_params *params,
                         const double *P_in, int in_ghosts, double *P_out, int out_ghosts,
                         long long nsteps, double t_arrival);
+
+/* grmhd_server_submit for a simulation that evolves electron entropies
+ * (params->electrons.model != 0; grmhd_server_submit refuses those): K_in
+ * and K_out are the host entropies (kappa_tot, kappa_e) in and out, with
+ * the ghosts as P_in and P_out, kept alive by the caller like them. */
+int grmhd_server_submit_electrons(grmhd_server *srv, long long id, const grmhd_grid *grid,
+                                  const grmhd_metric *metric, const grmhd_params *params,
+                                  const double *P_in, const double *K_in, int in_ghosts,
+                                  double *P_out, double *K_out, int out_ghosts, long long nsteps,
+                                  double t_arrival);
 
 /* Move up to max finished requests into res (oldest first), waiting up to
  * wait_ms milliseconds for the first; returns how many (>= 0) or an

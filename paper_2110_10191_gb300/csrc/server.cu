@@ -30,6 +30,8 @@ struct Request {
   grmhd_params params;
   const double *P_in;
   double *P_out;
+  const double *K_in;  // electron entropies (requests with electrons), same ghosts as P
+  double *K_out;
   int in_ghosts, out_ghosts;
   long long nsteps, remaining;
   size_t bytes;
@@ -138,6 +140,7 @@ static void admit(grmhd_server *s) {
     r->t_admit = (rc == GRMHD_OK) ? 0.0 : -1.0;  // marks the bytes as held
     if (rc == GRMHD_OK)
       rc = r->in_ghosts ? grmhd_set_prims_ghost(r->sim, r->P_in, 0) : grmhd_set_prims(r->sim, r->P_in, 0);
+    if (rc == GRMHD_OK && r->K_in) rc = grmhd_set_electrons(r->sim, r->K_in, r->in_ghosts, 0);
     if (rc != GRMHD_OK) {
       finish(s, r, rc);
       continue;
@@ -202,6 +205,7 @@ static void round_once(grmhd_server *s) {
   s->active = keep;
   for (Request *r : fin) {
     int frc = grmhd_get_prims(r->sim, r->P_out, r->out_ghosts, 0);
+    if (frc == GRMHD_OK && r->K_out) frc = grmhd_get_electrons(r->sim, r->K_out, r->out_ghosts, 0);
     if (frc == GRMHD_OK) frc = grmhd_step(r->sim, 0, &r->stats);  // statistics + failure check
     finish(s, r, frc);
   }
@@ -290,14 +294,15 @@ extern "C" int grmhd_server_create(const grmhd_server_config *cfg, grmhd_server 
   return GRMHD_OK;
 }
 
-extern "C" int grmhd_server_submit(grmhd_server *s, long long id, const grmhd_grid *grid,
-                                   const grmhd_metric *metric, const grmhd_params *params,
-                                   const double *P_in, int in_ghosts, double *P_out,
-                                   int out_ghosts, long long nsteps, double t_arrival) {
+static int submit(grmhd_server *s, long long id, const grmhd_grid *grid,
+                  const grmhd_metric *metric, const grmhd_params *params, const double *P_in,
+                  int in_ghosts, double *P_out, int out_ghosts, const double *K_in, double *K_out,
+                  long long nsteps, double t_arrival) {
   if (!s || !grid || !metric || !params || !P_in || !P_out || nsteps < 1 || nsteps > (1ll << 30))
     return GRMHD_ERR_INVALID;
-  // requests carry primitives only, not electron entropies
-  if (params->electrons.model != GRMHD_ELEC_OFF) return GRMHD_ERR_INVALID;
+  // the electron entropies come and go with the request exactly when it evolves them
+  const bool elec = params->electrons.model != GRMHD_ELEC_OFF;
+  if (elec != (K_in != nullptr) || elec != (K_out != nullptr)) return GRMHD_ERR_INVALID;
   size_t bytes = 0;
   const int rc = grmhd_footprint(grid, metric, params, &bytes);
   if (rc != GRMHD_OK) return rc;
@@ -311,6 +316,8 @@ extern "C" int grmhd_server_submit(grmhd_server *s, long long id, const grmhd_gr
   r->params = *params;
   r->P_in = P_in;
   r->P_out = P_out;
+  r->K_in = K_in;
+  r->K_out = K_out;
   r->in_ghosts = in_ghosts ? 1 : 0;
   r->out_ghosts = out_ghosts ? 1 : 0;
   r->nsteps = r->remaining = nsteps;
@@ -326,6 +333,24 @@ extern "C" int grmhd_server_submit(grmhd_server *s, long long id, const grmhd_gr
   }
   s->cv.notify_all();
   return GRMHD_OK;
+}
+
+extern "C" int grmhd_server_submit(grmhd_server *s, long long id, const grmhd_grid *grid,
+                                   const grmhd_metric *metric, const grmhd_params *params,
+                                   const double *P_in, int in_ghosts, double *P_out,
+                                   int out_ghosts, long long nsteps, double t_arrival) {
+  return submit(s, id, grid, metric, params, P_in, in_ghosts, P_out, out_ghosts, nullptr, nullptr,
+                nsteps, t_arrival);
+}
+
+extern "C" int grmhd_server_submit_electrons(grmhd_server *s, long long id, const grmhd_grid *grid,
+                                             const grmhd_metric *metric,
+                                             const grmhd_params *params, const double *P_in,
+                                             const double *K_in, int in_ghosts, double *P_out,
+                                             double *K_out, int out_ghosts, long long nsteps,
+                                             double t_arrival) {
+  return submit(s, id, grid, metric, params, P_in, in_ghosts, P_out, out_ghosts, K_in, K_out,
+                nsteps, t_arrival);
 }
 
 extern "C" int grmhd_server_poll(grmhd_server *s, grmhd_server_result *res, int max, int wait_ms) {

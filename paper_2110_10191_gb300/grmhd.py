@@ -120,6 +120,7 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_decomp_set_prims", "grmhd_decomp_get_prims", "grmhd_decomp_step",
            "grmhd_decomp_get_stats", "grmhd_set_electrons", "grmhd_get_electrons",
            "grmhd_decomp_set_electrons", "grmhd_decomp_get_electrons",
+           "grmhd_server_submit_electrons",
            "grmhd_strerror"]
 
 
@@ -175,6 +176,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_server_create.argtypes = [P(grmhd_server_config), P(vp)]
         L.grmhd_server_submit.argtypes = [vp, ctypes.c_longlong, P(grmhd_grid), P(grmhd_metric),
                                           P(grmhd_params), vp, i, vp, i, ctypes.c_longlong, d]
+        L.grmhd_server_submit_electrons.argtypes = [vp, ctypes.c_longlong, P(grmhd_grid),
+                                                    P(grmhd_metric), P(grmhd_params), vp, vp, i,
+                                                    vp, vp, i, ctypes.c_longlong, d]
         L.grmhd_server_poll.argtypes = [vp, P(grmhd_server_result), i, i]
         L.grmhd_server_drain.argtypes = [vp, i]
         L.grmhd_server_get_stats.argtypes = [vp, P(grmhd_server_stats)]
@@ -537,11 +541,23 @@ class Server:
         n1, n2, n3 = (int(x) for x in problem.n)
         shape = (NPRIM, n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG) if out_ghosts else (NPRIM, n3, n2, n1)
         out = np.empty(shape, dtype=np.float64)
-        _check(self.L.grmhd_server_submit(self.h, int(rid), ctypes.byref(g), ctypes.byref(m),
-                                          ctypes.byref(p), P_in.ctypes.data, int(Pg is not None),
-                                          out.ctypes.data, int(out_ghosts), int(nsteps),
-                                          float(t_arrival)), "grmhd_server_submit")
-        self._held[int(rid)] = (P_in, out)
+        el = getattr(problem, "electrons", None)
+        if el and el["model"]:  # the electron entropies travel with the request
+            Kg = problem.info.get("K_ghost") if problem.info else None
+            K_in = np.ascontiguousarray(Kg if Pg is not None else problem.K, dtype=np.float64)
+            K_out = np.empty((2,) + shape[1:], dtype=np.float64)
+            _check(self.L.grmhd_server_submit_electrons(
+                self.h, int(rid), ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
+                P_in.ctypes.data, K_in.ctypes.data, int(Pg is not None), out.ctypes.data,
+                K_out.ctypes.data, int(out_ghosts), int(nsteps), float(t_arrival)),
+                "grmhd_server_submit_electrons")
+            self._held[int(rid)] = (P_in, out, K_in, K_out)
+        else:
+            _check(self.L.grmhd_server_submit(self.h, int(rid), ctypes.byref(g), ctypes.byref(m),
+                                              ctypes.byref(p), P_in.ctypes.data, int(Pg is not None),
+                                              out.ctypes.data, int(out_ghosts), int(nsteps),
+                                              float(t_arrival)), "grmhd_server_submit")
+            self._held[int(rid)] = (P_in, out)
         return out
 
     def poll(self, max_results: int = 64, wait_ms: int = 0):
@@ -557,7 +573,8 @@ class Server:
             held = self._held.pop(int(r.id), (None, None))
             out.append({"id": r.id, "status": r.status, "zones": r.zones, "steps": r.steps,
                         "t_arrival": r.t_arrival, "t_admit": r.t_admit, "t_done": r.t_done,
-                        "stats": r.stats.as_dict(), "P": held[1]})
+                        "stats": r.stats.as_dict(), "P": held[1],
+                        "K": held[3] if len(held) > 3 else None})
         return out
 
     def drain(self, timeout_ms: int = -1) -> None:

@@ -13,7 +13,8 @@ oracle's electron thermodynamics.
   bar (3e-11) of the oracle, the FP32-flux modes within the mixed mode's
   (1e-5); batches mixing the modes stay bitwise.
 * Decomposed grids exchange the entropies: bitwise the whole grid's.
-* Serving refuses electrons.
+* Served requests carry them (grmhd_server_submit_electrons): bitwise the
+  simulation alone.
 """
 import dataclasses
 import math
@@ -255,6 +256,41 @@ def test_electron_refusals(grmhd):
     with pytest.raises(Exception):
         s.set_electrons(pr.K)
     s.close()
+    # the plain submission refuses electron requests: the entropies must travel
+    g, m, p = grmhd._structs(pr)
     with grmhd.Server() as srv:
-        with pytest.raises(Exception):
-            srv.submit(1, pr, 2)
+        out = np.empty_like(pr.P)
+        assert srv.L.grmhd_server_submit(srv.h, 1, grmhd.ctypes.byref(g), grmhd.ctypes.byref(m),
+                                         grmhd.ctypes.byref(p), pr.P.ctypes.data, 0,
+                                         out.ctypes.data, 0, 2, -1.0) == -1
+
+
+def test_electron_requests_are_served_bitwise(grmhd):
+    """Requests with electrons through the serving loop, batched with a
+    request without them: each result (primitives and entropies) is bitwise
+    the simulation's result alone."""
+    probs = [pb.with_electrons(pb.fm_torus(20, 16, 8), model=pb.ELEC_HOWES),
+             pb.fm_torus(16, 16, 4),
+             pb.with_electrons(pb.orszag_tang(24, recon=pb.RECON_WENO5), model=pb.ELEC_WERNER)]
+    steps = [3, 2, 4]
+    ref = []
+    for pr, n in zip(probs, steps):
+        s = grmhd.Sim(pr)
+        s.set_prims(pr.P)
+        if pr.electrons:
+            s.set_electrons(pr.K)
+        s.step(n)
+        ref.append((s.get_prims(), s.get_electrons() if pr.electrons else None))
+        s.close()
+    with grmhd.Server(quantum=2) as srv:
+        for q, (pr, n) in enumerate(zip(probs, steps)):
+            srv.submit(q, pr, n)
+        srv.drain()
+        res = {r["id"]: r for r in srv.poll(16)}
+    for q, (P, K) in enumerate(ref):
+        assert res[q]["status"] == 0
+        assert np.array_equal(res[q]["P"], P)
+        if K is not None:
+            assert np.array_equal(res[q]["K"], K)
+        else:
+            assert res[q]["K"] is None
