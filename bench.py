@@ -357,6 +357,20 @@ def variant_throughput(grmhd, pr, steps, warmup, stream, what):
             "kernel_ms_per_step": {k: v[0] / 2 for k, v in prof.items()}}
 
 
+def decomposed(grmhd, pr, steps, warmup, stream, nblocks=(2, 2, 2)):
+    """The FP64 workload split into blocks on one GPU (the paper's domain
+    decomposition; bitwise the whole grid): cycle time against the whole
+    grid's, i.e. the cost of the edge exchanges and the shared time step."""
+    d = grmhd.Decomp(pr, nblocks, stream=stream)
+    d.set_prims(pr.P)
+    d.step(warmup)
+    ms = _timed(stream, lambda: d.step(steps)) / steps
+    d.close()
+    z = pr.n[0] * pr.n[1] * pr.n[2]
+    return {"blocks": list(nblocks), "ms_per_step": ms, "value": z / (ms * 1e-3), "unit": UNIT,
+            "steps": steps}
+
+
 def small_single(grmhd, steps, stream):
     """The 64x64 fast mode (the accuracy workload, far too small to fill the
     GPU) stepped alone: one grmhd_step call of `steps` cycles (a graph
@@ -661,6 +675,7 @@ def main():
         extras["electrons"] = variant_throughput(grmhd, pr, max(args.steps // 2, 5), args.warmup,
                                                  stream, "electrons")
         extras["single_small"] = small_single(grmhd, 200, stream)
+        extras["decomposed"] = decomposed(grmhd, pr, max(args.steps // 5, 5), args.warmup, stream)
         extras["batched"] = batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, stream)
         extras["batched_small"] = batched_throughput(grmhd, args.steps, args.warmup, stream,
                                                      nmin=32, nmax=48)
