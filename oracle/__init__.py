@@ -118,6 +118,7 @@ def lib(counting: bool = False) -> ctypes.CDLL:
         L.oracle_elec_heat.argtypes = [d, d, d, d, d, d, d]
         L.oracle_elec_heat.restype = d
         L.oracle_recon.argtypes = [i, P(d), P(d)]
+        L.oracle_recon_faces.argtypes = [P(d), P(d)]
         L.oracle_op_counts.argtypes = [P(d), i]
         L.oracle_is_counting.restype = i
         _LIBS[counting] = L
@@ -324,6 +325,15 @@ def recon(kind, x):
     out = np.zeros(2)
     lib().oracle_recon(int(kind), _dp(x), _dp(out))
     return float(out[0]), float(out[1])
+
+
+def recon_faces(x):
+    """WENO5 (low, high) face values of the middle zone, each face from its
+    own smoothness indicators (the single-face form)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(2)
+    lib().oracle_recon_faces(_dp(x), _dp(out))
+    return out
 
 
 PHASES = ["flux", "ct", "update", "fixup", "other", "recon"]

@@ -436,6 +436,48 @@ static void recon_weno5(const real x[5], real *lout, real *rout) {
   *lout = weno5_right(x[4], x[3], x[2], x[1], x[0]);
 }
 
+/* Both WENO5 face values of the middle zone of x0..x4 from one set of
+ * smoothness indicators (the reconstruction step produces a zone's two
+ * interface values from the zone's own stencil).  The high face weighs the
+ * candidates (2x0 - 7x1 + 11x2)/6, (-x1 + 5x2 + 2x3)/6, (2x2 + 5x3 - x4)/6
+ * by 0.1, 0.6, 0.3 over (eps + beta_k)^2 with beta_0, beta_1, beta_2; the
+ * low face is its mirror image: candidates (2x4 - 7x3 + 11x2)/6,
+ * (-x3 + 5x2 + 2x1)/6, (2x2 + 5x1 - x0)/6 with beta_2, beta_1, beta_0 (a
+ * three-zone indicator reads the same in either direction).  The values
+ * are weno5_right's, each indicator formed once; every term is written in
+ * a mirror-symmetric order, so reversing the stencil swaps the two face
+ * values exactly. */
+static void weno5_zone(const real x[5], real *lout, real *rout) {
+  const real eps = 1.0e-26;
+  real t, s;
+  t = (x[0] + x[2]) - 2.0 * x[1];
+  s = (3.0 * x[2] - 4.0 * x[1]) + x[0];
+  real e0 = eps + ((13.0 / 12.0) * t * t + 0.25 * s * s);
+  t = (x[1] + x[3]) - 2.0 * x[2];
+  s = x[1] - x[3];
+  real e1 = eps + ((13.0 / 12.0) * t * t + 0.25 * s * s);
+  t = (x[2] + x[4]) - 2.0 * x[3];
+  s = (3.0 * x[2] - 4.0 * x[3]) + x[4];
+  real e2 = eps + ((13.0 / 12.0) * t * t + 0.25 * s * s);
+  e0 = e0 * e0;
+  e1 = e1 * e1;
+  e2 = e2 * e2;
+  /* high face */
+  real a0 = 0.1 / e0, a1 = 0.6 / e1, a2 = 0.3 / e2;
+  real q0 = (2.0 * x[0] - 7.0 * x[1] + 11.0 * x[2]) / 6.0;
+  real q1 = (-x[1] + 5.0 * x[2] + 2.0 * x[3]) / 6.0;
+  real q2 = (2.0 * x[2] + 5.0 * x[3] - x[4]) / 6.0;
+  *rout = (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  /* low face */
+  a0 = 0.1 / e2;
+  a1 = 0.6 / e1;
+  a2 = 0.3 / e0;
+  q0 = (2.0 * x[4] - 7.0 * x[3] + 11.0 * x[2]) / 6.0;
+  q1 = (-x[3] + 5.0 * x[2] + 2.0 * x[1]) / 6.0;
+  q2 = (2.0 * x[2] + 5.0 * x[1] - x[0]) / 6.0;
+  *lout = (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Simulation state                                                          */
 /* ------------------------------------------------------------------------ */
@@ -460,6 +502,7 @@ struct Sim {
   /* electrons: K = (kappa_tot, kappa_e) = (P_gas / rho^gamma, P_e / rho^gamma_e)
    * per zone, [s][k][j][i], and their fluxes; stage arrays as P, Ph */
   std::vector<real> K, Kh, FK[3];
+  std::vector<real> Lz, Rz, KLz, KRz; /* scratch: zones' face values along one direction */
   std::vector<real> emf[3];
   std::vector<int> pflag, fflag;
   real ctop_max[3];
@@ -617,24 +660,36 @@ static void load_prims(const Sim *S, const std::vector<real> &P, long id, real o
   for (int v = 0; v < NPRIM; v++) out[v] = P[v * S->ntot + id];
 }
 
-static void face_states(const Sim *S, const std::vector<real> &P, int d, int i, int j, int k,
-                        real PL[NPRIM], real PR[NPRIM]) {
+/* The two face values along d of every zone that the faces lo..hi need
+ * (zones lo[d]-1 .. hi[d] along d, the faces' transverse ranges), for the
+ * nvar variables of A: Lz at the zone's low face, Rz at its high face, each
+ * zone reconstructed once from its own stencil (MC slope or WENO5 pair). */
+static void zone_faces(const Sim *S, const std::vector<real> &A, int nvar, int d, const int lo[3],
+                       const int hi[3], std::vector<real> &Lz, std::vector<real> &Rz) {
+  const long N = S->ntot;
   int off[3] = {0, 0, 0};
   off[d] = 1;
-  for (int v = 0; v < NPRIM; v++) {
-    real x[6]; /* zones c-3 .. c+2 along d, face between c-1 and c */
-    for (int q = 0; q < 6; q++) {
-      int s = q - 3;
-      x[q] = P[v * S->ntot + IDX(S, i + s * off[0], j + s * off[1], k + s * off[2])];
-    }
-    if (S->recon == RECON_WENO5) {
-      PL[v] = weno5_right(x[0], x[1], x[2], x[3], x[4]); /* high face of zone c-1 */
-      PR[v] = weno5_right(x[5], x[4], x[3], x[2], x[1]); /* low face of zone c */
-    } else {
-      PL[v] = x[2] + 0.5 * mc_slope(x[1], x[2], x[3]);
-      PR[v] = x[3] - 0.5 * mc_slope(x[2], x[3], x[4]);
-    }
-  }
+  int zlo[3] = {lo[0], lo[1], lo[2]};
+  zlo[d] = lo[d] - 1;
+  for (int k = zlo[2]; k <= hi[2]; k++)
+    for (int j = zlo[1]; j <= hi[1]; j++)
+      for (int i = zlo[0]; i <= hi[0]; i++) {
+        long c = IDX(S, i, j, k);
+        for (int v = 0; v < nvar; v++) {
+          real x[5]; /* zones c-2 .. c+2 along d */
+          for (int q = 0; q < 5; q++) {
+            int sft = q - 2;
+            x[q] = A[v * N + IDX(S, i + sft * off[0], j + sft * off[1], k + sft * off[2])];
+          }
+          real l, r;
+          if (S->recon == RECON_WENO5)
+            weno5_zone(x, &l, &r);
+          else
+            recon_mc(x[1], x[2], x[3], &l, &r);
+          Lz[v * N + c] = l;
+          Rz[v * N + c] = r;
+        }
+      }
 }
 
 /* Local Lax-Friedrichs flux at one face; returns ctop. */
@@ -659,44 +714,20 @@ static real llf_face(const Sim *S, const GeomPt &g, int d, const real PL[NPRIM],
   return ctop;
 }
 
-/* Reconstructed values of the scalar field A (one variable of ntot) on both
- * sides of the face between zones c-1 and c along d, as face_states does
- * for the primitives. */
-static void recon_scalar(const Sim *S, const std::vector<real> &A, long base, int d, int i, int j,
-                         int k, real *L, real *R) {
-  int off[3] = {0, 0, 0};
-  off[d] = 1;
-  real x[6];
-  for (int q = 0; q < 6; q++) {
-    int s = q - 3;
-    x[q] = A[base + IDX(S, i + s * off[0], j + s * off[1], k + s * off[2])];
-  }
-  if (S->recon == RECON_WENO5) {
-    *L = weno5_right(x[0], x[1], x[2], x[3], x[4]);
-    *R = weno5_right(x[5], x[4], x[3], x[2], x[1]);
-  } else {
-    *L = x[2] + 0.5 * mc_slope(x[1], x[2], x[3]);
-    *R = x[3] - 0.5 * mc_slope(x[2], x[3], x[4]);
-  }
-}
-
 /* Fluxes of the electron entropies (Ressler et al. 2015): kappa_tot and
  * kappa_e are carried with the mass, conserved density sqrt(-g) rho u^t K
  * and flux sqrt(-g) rho u^d K, combined as the other fluxes are (local
- * Lax-Friedrichs with the face's ctop) from K reconstructed on each side. */
-static void elec_face(const Sim *S, const std::vector<real> &K, const GeomPt &g, int d, int i,
-                      int j, int k, const real PL[NPRIM], const real PR[NPRIM], real ctop,
-                      real FK[2]) {
+ * Lax-Friedrichs with the face's ctop) from K reconstructed on each side
+ * (KL[q], KR[q]). */
+static void elec_face(const GeomPt &g, int d, const real PL[NPRIM], const real PR[NPRIM],
+                      real ctop, const real KL[2], const real KR[2], real FK[2]) {
   FluidState sL, sR;
   get_state(PL, g, sL);
   get_state(PR, g, sR);
   real mL = PL[RHO] * sL.ucon[d + 1], mR = PR[RHO] * sR.ucon[d + 1]; /* rho u^d */
   real dL = PL[RHO] * sL.ucon[0], dR = PR[RHO] * sR.ucon[0];         /* rho u^t */
-  for (int q = 0; q < 2; q++) {
-    real KL, KR;
-    recon_scalar(S, K, (long)q * S->ntot, d, i, j, k, &KL, &KR);
-    FK[q] = 0.5 * g.gdet * (mL * KL + mR * KR - ctop * (dR * KR - dL * KL));
-  }
+  for (int q = 0; q < 2; q++)
+    FK[q] = 0.5 * g.gdet * (mL * KL[q] + mR * KR[q] - ctop * (dR * KR[q] - dL * KL[q]));
 }
 
 static void get_fluxes(Sim *S, const std::vector<real> &P, const std::vector<real> &K) {
@@ -708,25 +739,37 @@ static void get_fluxes(Sim *S, const std::vector<real> &P, const std::vector<rea
     lo[d] = NG;
     hi[d] = S->n[d] + NG;
     int loc = (d == 0) ? LOC_FACE1 : (d == 1) ? LOC_FACE2 : LOC_CENT;
+    /* every zone's two face values along d, then the faces */
+#ifdef ORACLE_COUNT
+    int saved = g_phase;
+    g_phase = 5;
+#endif
+    zone_faces(S, P, NPRIM, d, lo, hi, S->Lz, S->Rz);
+    if (S->elec) zone_faces(S, K, 2, d, lo, hi, S->KLz, S->KRz);
+#ifdef ORACLE_COUNT
+    g_phase = saved;
+#endif
+    const long st = (d == 0) ? 1 : (d == 1) ? S->s[0] : (long)S->s[0] * S->s[1];
     for (int k = lo[2]; k <= hi[2]; k++)
       for (int j = lo[1]; j <= hi[1]; j++)
         for (int i = lo[0]; i <= hi[0]; i++) {
           real PL[NPRIM], PR[NPRIM], Fo[NPRIM];
-#ifdef ORACLE_COUNT
-          int saved = g_phase;
-          g_phase = 5;
-#endif
-          face_states(S, P, d, i, j, k, PL, PR);
-#ifdef ORACLE_COUNT
-          g_phase = saved;
-#endif
+          const long c = IDX(S, i, j, k);
+          for (int v = 0; v < NPRIM; v++) {
+            PL[v] = S->Rz[v * N + c - st]; /* high face of the zone below the face */
+            PR[v] = S->Lz[v * N + c];      /* low face of the zone above it */
+          }
           const GeomPt &g = S->geom[loc][IJ(S, i, j)];
           real ctop = llf_face(S, g, d, PL, PR, Fo);
           long id = IDX(S, i, j, k);
           for (int v = 0; v < NPRIM; v++) S->F[d][v * N + id] = Fo[v];
           if (S->elec) {
-            real FK[2];
-            elec_face(S, K, g, d, i, j, k, PL, PR, ctop, FK);
+            real KL[2], KR[2], FK[2];
+            for (int q = 0; q < 2; q++) {
+              KL[q] = S->KRz[q * N + c - st];
+              KR[q] = S->KLz[q * N + c];
+            }
+            elec_face(g, d, PL, PR, ctop, KL, KR, FK);
             for (int q = 0; q < 2; q++) S->FK[d][q * N + id] = FK[q];
           }
           /* dt uses the faces of interior zones only */
@@ -1414,6 +1457,8 @@ void *oracle_create(const int n[3], const double xmin[3], const double xmax[3], 
   build_geometry(S);
   S->P.assign(NPRIM * S->ntot, real(0.0));
   S->Ph.assign(NPRIM * S->ntot, real(0.0));
+  S->Lz.assign(NPRIM * S->ntot, real(0.0));
+  S->Rz.assign(NPRIM * S->ntot, real(0.0));
   for (int d = 0; d < 3; d++) {
     S->F[d].assign(NPRIM * S->ntot, real(0.0));
     S->emf[d].assign(S->ntot, real(0.0));
@@ -1449,6 +1494,8 @@ void oracle_set_electrons(void *h, int model, double game, double gamp, double f
   if (model) {
     S->K.assign(2 * S->ntot, real(0.0));
     S->Kh.assign(2 * S->ntot, real(0.0));
+    S->KLz.assign(2 * S->ntot, real(0.0));
+    S->KRz.assign(2 * S->ntot, real(0.0));
     for (int d = 0; d < 3; d++) S->FK[d].assign(2 * S->ntot, real(0.0));
   } else {
     S->K.clear();
@@ -1774,15 +1821,26 @@ int oracle_floors_drift_at(int kind, double a, double h, const double X[4], doub
   return fl;
 }
 
+/* the step's reconstruction of one zone: out = (low face, high face) */
 void oracle_recon(int kind, const double *x, double out[2]) {
   real l, r;
   if (kind == RECON_WENO5) {
     real xx[5];
     for (int q = 0; q < 5; q++) xx[q] = x[q];
-    recon_weno5(xx, &l, &r);
+    weno5_zone(xx, &l, &r);
   } else {
     recon_mc(x[0], x[1], x[2], &l, &r);
   }
+  out[0] = val(l);
+  out[1] = val(r);
+}
+
+/* the single-face textbook form: out = (low face, high face), each from
+ * its own indicators */
+void oracle_recon_faces(const double *x, double out[2]) {
+  real xx[5], l, r;
+  for (int q = 0; q < 5; q++) xx[q] = x[q];
+  recon_weno5(xx, &l, &r);
   out[0] = val(l);
   out[1] = val(r);
 }

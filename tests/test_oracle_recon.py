@@ -68,3 +68,19 @@ def test_weno5_nonoscillatory_at_jump():
     l, r = oracle.recon(1, [0.0, 0.0, 0.0, 1.0, 1.0])
     assert -1e-6 <= l <= 1e-6 and 0.0 <= r <= 1.0
     assert r < 0.1
+
+
+def test_weno5_zone_pair_equals_single_face_form():
+    """The step reconstructs each zone's two faces from one set of
+    smoothness indicators; each value equals the single-face form (each
+    face from its own indicators, the mirrored stencil for the low face)
+    to rounding, on smooth data, steps, extrema and constants."""
+    rng = np.random.default_rng(11)
+    cases = [rng.normal(size=5) for _ in range(300)]
+    cases += [np.where(np.arange(5) < k, 1.0, 0.0) * rng.uniform(1, 10) for k in range(1, 5)]
+    cases += [np.full(5, 3.0), np.array([0, 1, 4, 1, 0.0]), np.array([1e-30, 2e-30, 0, 5e-31, 1e-30])]
+    for x in cases:
+        z = oracle.recon(oracle.RECON_WENO5 if hasattr(oracle, "RECON_WENO5") else 1, x)
+        f = oracle.recon_faces(x)
+        scale = np.abs(x).max()
+        assert np.abs(z - f).max() <= 1e-14 * max(scale, 1e-300), (x, z, f)
