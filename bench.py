@@ -750,10 +750,11 @@ def main():
                         "avg_launch_ms": kd["avg_launch_ms"], "hbm_frac": kd["hbm_frac"],
                         "algorithmic_bytes": kd["algorithmic_bytes"], "traffic": kd["traffic"],
                         "fp64_pipe_ncu": kd["fp64_pipe_ncu"],
-                        "note": "algorithmic flops are the oracle's (the method as defined: WENO "
-                                "smoothness indicators formed per face); the kernel forms them once "
-                                "per zone for both faces, so frac can exceed 1; fp64_pipe_ncu is the "
-                                "FP64 pipe's busy fraction in the ncu capture",
+                        "note": "algorithmic flops are the counting oracle's (adds, multiplies, "
+                                "divisions and square roots counted as one each); the kernel spends "
+                                "several FP64 instructions on each division and square root, so its "
+                                "FP64 pipe (fp64_pipe_ncu, the busy fraction in the ncu capture) "
+                                "runs above frac",
                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one "
                                           "launch, profiles/%s_fm_torus_128.md" % kd["kernel"].split()[0]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
