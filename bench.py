@@ -432,8 +432,8 @@ def batched_throughput(grmhd, steps, warmup, stream, nmin=32, nmax=256):
 
 def serving_run(grmhd, nreq, zone_cap, quantum, policy=0):
     """The serving workload: the first `nreq` requests of the 200-request
-    Poisson stream (4/s; 60% tori a ~ U[0, 0.98], N ~ U{64..192}; 40% 2D
-    Bondi, N ~ U{96..160}; 20..200 cycles; FP64 / mixed 50/50) submitted to
+    Poisson stream (4/s; 60% tori a ~ U[0, 0.98], N^3, N ~ U{64..192}; 40%
+    Bondi, N^3, N ~ U{96..160}; 20..200 cycles; FP64 / mixed 50/50) submitted to
     the serving loop at their arrival times.  Time-to-result runs from the
     scheduled arrival to the result in host memory."""
     import numpy as np
@@ -467,7 +467,7 @@ def serving_run(grmhd, nreq, zone_cap, quantum, policy=0):
     span = stream[-1]["t_arrival"]
     ok = sum(1 for r in results if r["status"] in (0, -4))
     return {"workload": "first %d of 200 Poisson requests at 4/s (seed 0): 60%% FM tori (a ~ U[0, 0.98], "
-                        "N^3, N ~ U{64..192}), 40%% 2D Bondi (N ~ U{96..160}), 20..200 cycles, "
+                        "N^3, N ~ U{64..192}), 40%% Bondi (N^3, N ~ U{96..160}), 20..200 cycles, "
                         "FP64/mixed 50/50" % nreq,
             "requests": len(stream), "completed": ok,
             "failed_zones_reported": sum(1 for r in results if r["status"] == -4),

@@ -297,7 +297,7 @@ def batch_2d(ngrid: int = 64, nmin: int = 32, nmax: int = 256, seed: int = 0,
 def serving_stream(nreq: int = 200, rate: float = 4.0, seed: int = 0) -> list:
     """``nreq`` requests arriving as a Poisson process of ``rate`` per second:
     60% Fishbone-Moncrief tori (spin a uniform in [0, 0.98], cubic N uniform
-    in {64..192}), 40% 2D Bondi inflows (N x N, N uniform in {96..160}); each
+    in {64..192}), 40% Bondi inflows (cubic N, N uniform in {96..160}); each
     asks for a number of cycles uniform in {20..200} and runs in FP64 or in
     the mixed mode with probability 1/2.  Returns dicts (id, t_arrival,
     kind, n, a, steps, precision); ``serving_problem`` builds a request's
@@ -326,7 +326,7 @@ def serving_problem(req: dict) -> "Problem":
         n = req["n"]
         pr = fm_torus(n, n, n, a=req["a"], seed=req["id"])
     else:
-        pr = bondi(req["n"], req["n"])
+        pr = bondi(req["n"], req["n"], n3=req["n"])
     pr.precision = req["precision"]
     pr.name = "req%03d_%s" % (req["id"], pr.name)
     return pr

@@ -158,4 +158,4 @@ def test_serving_stream_recipe():
     assert 0.35 < np.mean([r["precision"] for r in st]) < 0.65
     small = pb.serving_problem({"id": 3, "kind": "bondi", "n": 96, "a": 0.0, "steps": 20,
                                 "precision": 1, "t_arrival": 0.0})
-    assert small.n == (96, 96, 1) and small.precision == 1
+    assert small.n == (96, 96, 96) and small.precision == 1
