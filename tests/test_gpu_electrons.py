@@ -294,3 +294,16 @@ def test_electron_requests_are_served_bitwise(grmhd):
             assert np.array_equal(res[q]["K"], K)
         else:
             assert res[q]["K"] is None
+
+
+def test_electron_full_size_torus_one_step(grmhd):
+    """The bench's electron workload, the 128^3 WENO5 torus with Kawazura
+    heating: one step, every zone's primitives and entropies against the
+    oracle at the FP64 bar."""
+    pr = pb.with_electrons(pb.fm_torus(128, 128, 128), model=pb.ELEC_KAWAZURA)
+    o, s = _pair(pr, grmhd)
+    o.step(1)
+    s.step(1)
+    compare(s.get_prims(), o.get_prims(), what="128^3 electrons")
+    compare_K(s.get_electrons(), o.get_K(), what="128^3 electrons")
+    assert np.array_equal(s.flags()[0], o.flags()[0])

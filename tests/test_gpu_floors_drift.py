@@ -139,3 +139,14 @@ def test_drift_batch_and_decomp_bitwise(grmhd):
 def test_drift_frame_validated(grmhd):
     with pytest.raises(Exception):
         grmhd.Sim(dataclasses.replace(pb.fm_torus(8, 8, 4), floor_frame=2))
+
+
+def test_drift_full_size_torus_one_step(grmhd):
+    """The bench's drift-frame workload, the 128^3 WENO5 torus: one step,
+    every zone against the oracle at the FP64 bar."""
+    pr = _drift(pb.fm_torus(128, 128, 128))
+    o, s = _pair(pr, grmhd)
+    o.step(1)
+    s.step(1)
+    compare(s.get_prims(), o.get_prims(), what="128^3 drift")
+    assert np.array_equal(s.flags()[0], o.flags()[0])
