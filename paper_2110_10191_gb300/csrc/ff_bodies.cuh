@@ -630,13 +630,24 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
     }
     const double idx1 = A.idx[0], idx2 = A.idx[1], idx3 = A.idx[2];
     const ff dtpf = ff_from(dtp);
+    // The field is updated in FP64, sqrt(-g) B (P^n) - dt' div F_B, as the
+    // FP64 update does: flux-CT's divergence-free increments then keep div B
+    // at FP64 round-off; the inversion reads the result's words.
+    const double gdd = __ldg(A.geom + (long long)G_GDET * D.n2d + ij);
+    const double igdd = __ldg(A.geom + (long long)G_IGDET * D.n2d + ij);
+    double UB[3];
     ff Un[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       const long long o = v * N + c;
       const double div = (F1[o + 1] - F1[o]) * idx1 + (F2[o + D.s[0]] - F2[o]) * idx2 +
                          (F3[o + D.n2d] - F3[o]) * idx3;
-      ff rhs = ff_neg(ff_from(div * (double)(v < B1 ? sc.is : sc.irs)));
+      if (v >= B1) {
+        UB[v - B1] = gdd * Pi[o] + dtp * (0.0 - div);
+        Un[v] = ff_from(UB[v - B1] * (double)sc.irs);
+        continue;
+      }
+      ff rhs = ff_neg(ff_from(div * (double)sc.is));
       if (v >= UU && v <= U3) rhs = ff_add(rhs, S[v - UU]);
       Un[v] = ff_add(Ui[v], ff_mul(dtpf, rhs));
     }
@@ -644,11 +655,12 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
     pf = invert_1dw_ff(Un, G, gam, igam, gf, pi, pn, bsq_n, lor_n);
     double pd[NV];
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
+    for (int v = 0; v < B1; v++) {
       pd[v] = ff_to(pn[v]);
       if (v == RHO || v == UU) pd[v] *= sc.s;
-      if (v >= B1) pd[v] *= sc.rs;
     }
+#pragma unroll
+    for (int q = 0; q < 3; q++) pd[B1 + q] = UB[q] * igdd;
     if (pf == PF_OK && A.floors_on && !A.floor_drift && !A.elec) {
       const double rho_fl = __ldg(A.floors + ij), u_fl = __ldg(A.floors + D.n2d + ij);
       const double lor = ff_to(lor_n);
