@@ -329,13 +329,10 @@ def variant_throughput(grmhd, pr, steps, warmup, stream, what):
     """The FP64 workload with a variant switched on: the bounds in the drift
     frame ("drift") or electron entropies with the Kawazura heating model
     ("electrons"), with the device time of each kernel class."""
-    import dataclasses
-    from paper_2110_10191_gb300 import problems as pb
+    pv = apply_variant(pr, what)
     if what == "drift":
-        pv = dataclasses.replace(pr, floor_frame=1)
         desc = "bounds in the drift frame (floor parcel added in U and inverted)"
     else:
-        pv = pb.with_electrons(pr, model=pb.ELEC_KAWAZURA)
         desc = ("electron entropies carried with the mass, Kawazura et al. heating, "
                 "T_p/T_e in [1e-3, 1e3], P_gas/rho^gamma <= 3")
     s = grmhd.Sim(pv, stream=stream)
@@ -557,10 +554,25 @@ def mixed_accuracy(grmhd, steps, stream):
             "mixed_ff_primitives": norms(states[3][:, 3:-3, 3:-3, 3:-3])}
 
 
-def workload_config(name):
+def apply_variant(pr, variant):
+    """The workload with a variant of the step switched on: the bounds in the
+    drift frame, or electron entropies heated by the Kawazura et al. model
+    with T_p/T_e in [1e-3, 1e3] and P_gas/rho^gamma <= 3."""
+    import dataclasses
+    from paper_2110_10191_gb300 import problems as pb
+    if variant == "drift":
+        return dataclasses.replace(pr, floor_frame=1)
+    if variant == "electrons":
+        return pb.with_electrons(pr, model=pb.ELEC_KAWAZURA)
+    return pr
+
+
+def workload_config(name, variant="none"):
     w = WORKLOADS[name]
     cfg = {"workload": w["label"], "grid": list(w["n"]), "dtype": "fp64",
            "recon": "weno5" if w["recon"] == 1 else "mc"}
+    if variant != "none":
+        cfg["variant"] = variant
     if name.startswith("torus"):
         cfg.update({"metric": "kerr_mks", "a": 0.9375, "hslope": 0.3, "r_out": w["r_out"],
                     "r_in_torus": 6.0, "r_max_torus": 12.0, "beta": 100.0, "perturbation": 0.04,
@@ -579,6 +591,9 @@ def main():
     ap.add_argument("--config", default="torus128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff", "mixed_ff"],
                     help="arithmetic of the flux stage of the timed workload (fp64: the headline)")
+    ap.add_argument("--variant", default="none", choices=["none", "drift", "electrons"],
+                    help="run the timed workload with the bounds in the drift frame or with "
+                         "electron entropies (Kawazura heating); none: the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
@@ -611,12 +626,14 @@ def main():
         if world > 1:
             dist.barrier()
 
-    pr = make_problem(args.config)
+    pr = apply_variant(make_problem(args.config), args.variant)
     pr.precision = {"fp64": 0, "mixed": 1, "ff": 2, "mixed_ff": 3}[args.precision]
     zones = pr.n[0] * pr.n[1] * pr.n[2]
     stream = torch.cuda.current_stream()
     sim = grmhd.Sim(pr, stream=stream)
     sim.set_prims(pr.P)
+    if pr.electrons:
+        sim.set_electrons(pr.K)
     sim.step(args.warmup)
 
     # ---- timed region: K steps, device resident ----
@@ -649,6 +666,8 @@ def main():
         host_out = torch.empty_like(host_in).pin_memory()
         sim2 = grmhd.Sim(pr, stream=stream)
         sim2.set_prims(host_in)
+        if pr.electrons:
+            sim2.set_electrons(pr.K)
         sim2.step(1)
         barrier()
         torch.cuda.synchronize()
@@ -702,7 +721,8 @@ def main():
     launches = sum(v[1] for v in prof.values())
     roofline = None
     kernels = {}
-    if cpu is not None and pr.precision == 0:  # the FP64 kernels' algorithmic count
+    if cpu is not None and pr.precision == 0 and args.variant == "none":
+        # the FP64 kernels' algorithmic count
         faces = faces_per_launch(pr.n)
         hbm = 6791e9
         try:
@@ -761,7 +781,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if pr.precision == 0 else PREC_DTYPE[pr.precision],
-            "data": "synthetic", "config": workload_config(args.config),
+            "data": "synthetic", "config": workload_config(args.config, args.variant),
             "e2e": None if e2e_s is None else {
                 "value": job_value(zones, args.steps, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes / args.steps,
