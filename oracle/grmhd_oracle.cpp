@@ -1129,8 +1129,7 @@ static int apply_floors_drift(real P[NPRIM], const GeomPt &g, real rho_fl, real 
 /* 1)(u - u_e)/rho; the proton beta is beta_p = rho T_p/(b^2/2).             */
 /* READING: temperatures enter by magnitude, T_p/T_e is clamped to          */
 /* [1e-20, 1e20] and beta_p to [1e-20, 1e20] (1e20: an unmagnetised zone).  */
-/* Each
-/* model is the fit its paper publishes, with f_e = 1/(1 + Q_i/Q_e):          */
+/* Each model is the fit its paper publishes, with f_e = 1/(1 + Q_i/Q_e):     */
 /*  Kawazura et al. 2019  Q_i/Q_e = 35/(1 + (beta_p/15)^-1.4 e^(-0.1 T_e/T_p)) */
 /*  Werner et al. 2018    f_e = (1 + sqrt((s/5)/(2 + s/5)))/4, s = b^2/rho    */
 /*  Rowan et al. 2017     f_e = exp(-(1 - beta_p/beta_max)^3.3 /              */

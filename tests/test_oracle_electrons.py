@@ -8,7 +8,9 @@ models the paper lists, and the electron bounds.
   sqrt(T_e/T_p)); Werner et al. between 1/4 (unmagnetised) and 1/2 (sigma ->
   infinity); Rowan et al. 1/2 at beta = beta_max, e^-1/2 cold and
   unmagnetised -- electrons taking everything at low beta, monotonic trends,
-  and 0 <= f_e <= 1 on random states.
+  and 0 <= f_e <= 1 on random states; and each fit at interior points where
+  it reduces to a closed form by hand (Kawazura at beta_p = 15, Howes on each
+  branch of T_p/T_e, Werner at sigma = 10, Rowan at beta_p = beta_max/2).
 * One heating update gives the electrons the share f_e of the dissipated
   internal energy density.
 * With f_e = 0 the electron entropy is a passive scalar: its conserved
@@ -84,6 +86,54 @@ def test_rowan_limits():
     assert _fel(oracle.ELEC_ROWAN, 1.0, 1e-8, 1e-12, 0.0) == pytest.approx(0.5 / math.e, rel=1e-6)
     # cold and strongly magnetised: the exponent vanishes
     assert _fel(oracle.ELEC_ROWAN, 1.0, 1e-8, 1e-12, 1e12) == pytest.approx(0.5, rel=1e-6)
+
+
+def _state_for(beta, trat, rho=1.0, Te=1e-3, game=GAME, gamp=GAMP):
+    """(rho, u, kappa_e, b^2) of a zone with proton beta beta = rho T_p/(b^2/2)
+    and T_p/T_e = trat."""
+    kel = Te / rho ** (game - 1)
+    ue = rho * Te / (game - 1)
+    Tp = trat * Te
+    return rho, ue + rho * Tp / (gamp - 1), kel, 2 * rho * Tp / beta
+
+
+@pytest.mark.parametrize("model,beta,trat,expect", [
+    # Kawazura at beta_p = 15, where the beta term is 1, and where it is 2
+    ("KAWAZURA", 15.0, 0.1, 1 / (1 + 35 / (1 + math.exp(-1)))),
+    ("KAWAZURA", 15.0 * 2 ** (-1 / 1.4), 0.1, 1 / (1 + 35 / (1 + 2 * math.exp(-1)))),
+    # Howes on each branch of T_p/T_e: x = 2 at T_p = T_e; c2 = 0.16, c3 = 23
+    # at T_p = 10 T_e; c2 = 12, c3 = 18 at T_p = T_e/10 (beta_p = 1: beta^x = 1)
+    ("HOWES", 3.0, 1.0, 1 / (1 + 0.92 * (1.44 + 9) / (324 + 9) * math.sqrt(MP_ME) * math.exp(-1 / 3))),
+    ("HOWES", 1.0, 10.0, 1 / (1 + 0.92 * (0.0256 + 1) / (529 + 1) * math.sqrt(10 * MP_ME) * math.exp(-1))),
+    ("HOWES", 1.0, 0.1, 1 / (1 + 0.92 * (144 + 1) / (324 + 1) * math.sqrt(0.1 * MP_ME) * math.exp(-1))),
+    # Sharma at T_p = 9 T_e: Q_e/Q_i = 0.33/3
+    ("SHARMA", 0.3, 9.0, 0.11 / 1.11),
+])
+def test_fits_at_special_points(model, beta, trat, expect):
+    """Each fit at a point where it reduces to a closed form by hand: a
+    swapped temperature ratio, a wrong exponent or normalisation, or the
+    wrong branch each moves the value."""
+    rho, u, kel, bsq = _state_for(beta, trat)
+    assert _fel(getattr(oracle, "ELEC_" + model), rho, u, kel, bsq) == pytest.approx(expect, rel=1e-12)
+
+
+def test_werner_and_rowan_at_special_points():
+    """Werner at sigma = b^2/rho = 10: (1 + sqrt(1/2))/4.  Rowan at
+    sigma_w = b^2/(rho + gamma u) = 1 and beta_p = beta_max/2 = 1/8:
+    exp(-(1/2)^3.3/2.2)/2."""
+    rho, u, kel, _ = _state_for(1.0, 1.0)
+    assert _fel(oracle.ELEC_WERNER, rho, u, kel, 10.0 * rho) == pytest.approx(
+        (1 + math.sqrt(0.5)) / 4, rel=1e-14)
+    # sigma_w = 1 and 2 rho T_p / b^2 = 1/8 with u = u_e + rho T_p/(gamma_p - 1)
+    Te, rho = 1e-6, 1.0
+    ue = rho * Te / (GAME - 1)
+    Tp = 0.0625 * (rho + GAM * ue) / (1 - 0.0625 * GAM / (GAMP - 1))
+    u = ue + rho * Tp / (GAMP - 1)
+    bsq = rho + GAM * u
+    assert 2 * rho * Tp / bsq == pytest.approx(0.125, rel=1e-14)
+    kel = Te / rho ** (GAME - 1)
+    assert _fel(oracle.ELEC_ROWAN, rho, u, kel, bsq) == pytest.approx(
+        0.5 * math.exp(-0.5 ** 3.3 / 2.2), rel=1e-12)
 
 
 def test_fractions_bounded():
