@@ -158,3 +158,43 @@ def test_mixed_ff_divb_and_orszag_tang(grmhd):
     a, b = sm.get_prims(), s64.get_prims()
     sc = _scales(b)
     assert max(np.abs(a[v] - b[v]).max() / sc[v] for v in range(8)) < 1e-4
+
+
+def test_torus_288_all_modes_vs_oracle(grmhd):
+    """The largest workload, the 288x128x128 torus reaching R_out = 1000,
+    one step of every precision mode against one FP64 oracle step on the
+    same geometry: FP64 within 1e-12 of each group's scale (and 1e-9 per
+    zone), float-float within 3e-11, the two FP32-flux modes within 1e-5;
+    div B at round-off in all four."""
+    def problem(prec):
+        pr = pb.fm_torus(288, 128, 128, recon=pb.RECON_WENO5, r_out=1000.0)
+        pr.precision = prec
+        return pr
+
+    pr = problem(0)
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.step(1)
+    b = o.get_prims()
+    sc = _scales(b)
+    geom = [o.geom(loc) for loc in range(4)]
+    gdet = geom[0][32]
+    dx = [(pr.xmax[d] - pr.xmin[d]) / pr.n[d] for d in range(3)]
+    bars = {0: 1e-12, 2: 3e-11, 1: 1e-5, 3: 1e-5}
+    for prec, bar in bars.items():
+        pm = problem(prec)
+        s = grmhd.Sim(pm)
+        for loc in range(4):
+            s.set_geom(loc, geom[loc])
+        s.set_prims(pm.P)
+        s.step(1)
+        a = s.get_prims()
+        err = [np.abs(a[v] - b[v]).max() / sc[v] for v in range(8)]
+        assert max(err) <= bar, (prec, err)
+        if prec == 0:
+            for v in range(8):
+                bad = np.abs(a[v] - b[v]) > 1e-9 * np.abs(b[v]) + 1e-12 * sc[v]
+                assert not bad.any(), (v, int(bad.sum()))
+        d, scale = corner_divb(s.get_prims(True), gdet, dx, pm.n)
+        assert d <= 1e-12 * scale, (prec, d / scale)
+        s.close()
