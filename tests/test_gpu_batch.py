@@ -306,3 +306,31 @@ def test_sim_autotune_keeps_bits(grmhd):
     got = s.step(2)
     assert np.array_equal(s.get_prims(with_ghosts=True), ref)
     assert got["t"] == st["t"] and got["floor_hits"] == st["floor_hits"]
+
+
+def test_full_batch_oracle_parity(grmhd):
+    """The batch the benchmark times -- 64 uneven 2D grids, 32^2 to 256^2
+    (seed 0), autotuned and stepped through its CUDA graph -- one step,
+    every grid against the oracle at the single-grid FP64 rule."""
+    probs = pb.batch_2d(ngrid=64, nmin=32, nmax=256, seed=0)
+    sims, oracles = [], []
+    for pr in probs:
+        o = oracle.Oracle(pr)
+        o.set_prims(pr.P)
+        s = grmhd.Sim(pr)
+        for loc in range(4):
+            s.set_geom(loc, o.geom(loc))
+        s.set_prims(pr.P)
+        sims.append(s)
+        oracles.append(o)
+    b = grmhd.Batch(sims)
+    b.autotune(trials=1)
+    b.step(1, graph=True, sync=True)
+    assert b.info()["tuned"] == 1 and b.info()["graph"] == 1
+    for s, o, pr in zip(sims, oracles, probs):
+        o.step(1)
+        compare(s.get_prims(), o.get_prims(), what=pr.name)
+        o.close()
+    b.close()
+    for s in sims:
+        s.close()
