@@ -52,18 +52,19 @@ enum {
 enum { PF_OK = 0, PF_NOCONV = 1, PF_W = 2, PF_VSQ = 3, PF_RHO = 4, PF_U = 5, PF_D = 6 };
 
 // Reciprocal without the IEEE division sequence: the hardware approximation
-// (PTX rcp.approx.ftz.f64) refined by two Newton-Raphson steps for 1/x,
-// r <- r + r (1 - x r), each of which doubles the correct bits; the result is
-// within a few ulp of 1/x for normal x.  Used where the quotient feeds
-// further arithmetic (WENO weights, signal speeds, the Newton iteration of
-// the inversion); decisions compared against constants keep IEEE division.
+// (PTX rcp.approx.ftz.f64, about 20 correct bits) refined by one third-order
+// step of the geometric series 1/x = r/(1 - e) = r (1 + e + e^2 + ...),
+// e = 1 - x r: r <- r + r (e + e^2), which leaves a relative error of about
+// e^3 ~ 2^-60 before the final rounding (three FMAs; two Newton-Raphson
+// steps, r <- r + r e twice, take four for the same result).  Within a few
+// ulp of 1/x for normal x.  Used where the quotient feeds further arithmetic
+// (WENO weights, signal speeds, the Newton iteration of the inversion);
+// decisions compared against constants keep IEEE division.
 __device__ __forceinline__ double rcp_nr(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 struct Dims {
@@ -256,23 +257,27 @@ __device__ __forceinline__ double weno5_hi(double a, double b, double c, double 
 // Both WENO5 face values of the middle zone of a..e (zones c-2..c+2), written
 // in the stencil's first differences (dm2 = b-a, dm1 = c-b, dp1 = d-c,
 // dp2 = e-d) and second differences (D0 = a-2b+c, D1 = b-2c+d, D2 = c-2d+e):
-//   12 beta_0 = 13 D0^2 + 3 (D0 + 2 dm1)^2
-//   12 beta_1 = 13 D1^2 + 3 (dm1 + dp1)^2
-//   12 beta_2 = 13 D2^2 + 3 (D2 - 2 dp1)^2
+//   4 beta_0 = (13/3) D0^2 + (D0 + 2 dm1)^2
+//   4 beta_1 = (13/3) D1^2 + (dm1 + dp1)^2
+//   4 beta_2 = (13/3) D2^2 + (D2 - 2 dp1)^2
 //   6 (q_0 - c) = 2 D0 + 3 dm1,  6 (q_1 - c) = dm1 + 2 dp1,  6 (q_2 - c) = 3 dp1 - D2
 // (q_k the candidate values at the high face), the low face by mirroring.
 // The weights d_k/(eps + beta_k)^2 are taken over the common denominator
-// q0 q1 q2 of the squared (12 eps + 12 beta_k) and scaled by 10, which
-// leaves their ratios unchanged, and one reciprocal serves both faces.
+// q0 q1 q2 of the squared (4 eps + 4 beta_k) and scaled by 10, which
+// leaves their ratios unchanged (4 eps + 4 beta_k costs one multiply and two
+// FMAs), and one reciprocal serves both faces, with the 1/6 of the
+// candidate differences folded into it.  The terms pair up under the mirror
+// a <-> e, b <-> d, so a mirrored stencil gives the same two values swapped,
+// bit for bit.
 __device__ __forceinline__ void weno5_pair(double a, double b, double c, double d, double e,
                                            double &lo, double &hi) {
-  const double eps12 = 12.0e-26;
+  const double eps4 = 4.0e-26, c13 = 13.0 / 3.0;
   const double dm2 = b - a, dm1 = c - b, dp1 = d - c, dp2 = e - d;
   const double D0 = dm1 - dm2, D1 = dp1 - dm1, D2 = dp2 - dp1;
   const double s0 = D0 + 2.0 * dm1, s1 = dm1 + dp1, s2 = D2 - 2.0 * dp1;
-  const double e0 = eps12 + (13.0 * D0 * D0 + 3.0 * s0 * s0);
-  const double e1 = eps12 + (13.0 * D1 * D1 + 3.0 * s1 * s1);
-  const double e2 = eps12 + (13.0 * D2 * D2 + 3.0 * s2 * s2);
+  const double e0 = fma(c13 * D0, D0, fma(s0, s0, eps4));
+  const double e1 = fma(c13 * D1, D1, fma(s1, s1, eps4));
+  const double e2 = fma(c13 * D2, D2, fma(s2, s2, eps4));
   const double q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
   // linear weights in the ratio 1 : 6 : 3 (only ratios enter)
   const double q12 = q1 * q2, q02 = 6.0 * (q0 * q2), q01 = q0 * q1;
@@ -280,11 +285,11 @@ __device__ __forceinline__ void weno5_pair(double a, double b, double c, double 
   const double m3 = 3.0 * dm1, p3 = 3.0 * dp1;
   // high face: weights q12, 6 q02, 3 q01
   const double nh = q12 * (2.0 * D0 + m3) + q02 * (dm1 + 2.0 * dp1) + t01 * (p3 - D2);
-  const double H = 6.0 * (q12 + q02 + t01);
+  const double H = q12 + q02 + t01;
   // low face (mirrored stencil): weights q01, 6 q02, 3 q12
   const double nl = q01 * (2.0 * D2 - p3) - q02 * (dp1 + 2.0 * dm1) - t12 * (m3 + D0);
-  const double L = 6.0 * (q01 + q02 + t12);
-  const double r = rcp_nr(H * L);
+  const double L = q01 + q02 + t12;
+  const double r = rcp_nr(H * L) * (1.0 / 6.0);
   hi = c + nh * (L * r);
   lo = c + nl * (H * r);
 }
