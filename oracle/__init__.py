@@ -71,12 +71,17 @@ def _ip(a):
 
 
 def lib(counting: bool = False) -> ctypes.CDLL:
+    """The oracle library.  ORACLE_LIB, when set, names another build of the
+    plain (non-counting) oracle to load instead: the mutation tests point it
+    at copies of the source with a planted mistake."""
     with _LOCK:
         if counting in _LIBS:
             return _LIBS[counting]
-        path = _lib_path(counting)
-        if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
-            build()
+        path = os.environ.get("ORACLE_LIB") if not counting else None
+        if not path:
+            path = _lib_path(counting)
+            if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+                build()
         L = ctypes.CDLL(path)
         vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         P = ctypes.POINTER

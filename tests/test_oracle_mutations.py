@@ -1,0 +1,114 @@
+"""Planted mistakes in the oracle, each of which a pin must catch.
+
+A pin that no plausible mistake can fail proves nothing about the oracle.
+Each case copies oracle/grmhd_oracle.cpp, plants one mistake of the kinds a
+transcription makes (a dropped term, a wrong sign, a transposed index, a
+wrong constant or branch), builds the copy with the oracle's own compiler
+flags and runs the pins named beside it against that build (ORACLE_LIB).
+The case passes when those pins fail.  CPU only; the oracle's own build is
+not touched.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "grmhd_oracle.cpp")
+
+SCHEME = "tests/test_oracle_scheme.py"
+PHYSICS = "tests/test_oracle_physics.py"
+GEOMETRY = "tests/test_oracle_geometry.py"
+RECON = "tests/test_oracle_recon.py"
+DRIFT = "tests/test_oracle_floors_drift.py"
+ELEC = "tests/test_oracle_electrons.py"
+
+# (name, text in the oracle source (exactly once), planted replacement, pins)
+MUTATIONS = [
+    # local Lax-Friedrichs: the dissipation added instead of subtracted
+    ("llf_dissipation_sign", "FL[v] + FR[v] - ctop * (UR[v] - UL[v])",
+     "FL[v] + FR[v] + ctop * (UR[v] - UL[v])", [SCHEME]),
+    # stress-energy: magnetic pressure dropped from the total pressure
+    ("ptot_without_bsq", "real ptot = pgas + 0.5 * s.bsq;", "real ptot = pgas;", [PHYSICS]),
+    # energy flux: the rest mass subtracted twice instead of removed
+    ("rest_mass_sign", "F[UU] = T[0] + F[RHO];", "F[UU] = T[0] - F[RHO];", [PHYSICS]),
+    # fast speed: c_ms^2 = cs^2 + va^2 - cs^2 va^2 with the wrong sign
+    ("fast_speed_sign", "real cms2 = cs2 + va2 - cs2 * va2;",
+     "real cms2 = cs2 + va2 + cs2 * va2;", [PHYSICS]),
+    # MC limiter: the factor 2 of the one-sided slopes dropped
+    ("mc_factor", "rabs(2.0 * dm)", "rabs(dm)", [RECON]),
+    # WENO5: the linear weights of the high face swapped
+    ("weno5_linear_weights", "real a0 = 0.1 / e0, a1 = 0.6 / e1, a2 = 0.3 / e2;",
+     "real a0 = 0.3 / e0, a1 = 0.6 / e1, a2 = 0.1 / e2;", [RECON]),
+    # flux-CT: one of the four EMF terms with the wrong sign
+    ("emf_term_sign", "- F2[B1 * N + c] - F2[B1 * N + im]);",
+     "- F2[B1 * N + c] + F2[B1 * N + im]);", [SCHEME]),
+    # geometric source: the connection's upper and a lower index transposed
+    ("connection_index", "conn[(la * 4 + nu) * 4 + ka]", "conn[(nu * 4 + la) * 4 + ka]",
+     [SCHEME + "::test_torus_equilibrium_residual_second_order"]),
+    # geometric source with the wrong sign
+    ("source_sign", "dU[UU + nu] = acc * g.gdet;", "dU[UU + nu] = -acc * g.gdet;",
+     [SCHEME + "::test_torus_equilibrium_residual_second_order"]),
+    # 1D_W: v^2(W) with (B^2 + W) for (B^2 + 2W)
+    ("inversion_vsq", "q.QdB * q.QdB * (q.Bsq + 2.0 * W)) / (BW * BW * W2)",
+     "q.QdB * q.QdB * (q.Bsq + W)) / (BW * BW * W2)", [PHYSICS]),
+    # 1D_W: the spatial projection of Q with the wrong sign
+    ("inversion_projection", "(g.gcon[i][j] - g.gcon[i][0] * g.gcon[j][0] / g.gcon[0][0])",
+     "(g.gcon[i][j] + g.gcon[i][0] * g.gcon[j][0] / g.gcon[0][0])", [PHYSICS]),
+    # Kerr-Schild metric: g_tr with the wrong sign
+    ("kerr_schild_gtr_sign", "ks[0][1] = 2.0 * r / sig;", "ks[0][1] = -2.0 * r / sig;", [GEOMETRY]),
+    # modified Kerr-Schild theta(X2) with h for 1 - h
+    ("mks_theta_map", "double th = M_PI * X[2] + 0.5 * (1.0 - h) * std::sin(2.0 * M_PI * X[2]);",
+     "double th = M_PI * X[2] + 0.5 * (1.0 + h) * std::sin(2.0 * M_PI * X[2]);", [GEOMETRY]),
+    # predictor-corrector: the predictor takes the full step
+    ("predictor_full_step", "PHASE(2);\n  int bad = advance_stage(S, S->P, S->P, S->Ph, 0.5 * dt,",
+     "PHASE(2);\n  int bad = advance_stage(S, S->P, S->P, S->Ph, dt,",
+     [SCHEME + "::test_linear_mode_second_order"]),
+    # bounds: the beta bound's u without the factor 2 of P_b = b^2/2
+    ("beta_bound_factor", "BETA_MIN * s.bsq / (2.0 * (gam - 1.0))",
+     "BETA_MIN * s.bsq / (gam - 1.0)", [PHYSICS]),
+    # drift-frame bounds: the field-aligned part added instead of removed
+    ("drift_projection_sign", "(Pc[U1 + i] - (udB / Bsq) * Pc[B1 + i])",
+     "(Pc[U1 + i] + (udB / Bsq) * Pc[B1 + i])", [DRIFT]),
+    # electron entropy flux: the LLF term with the wrong sign
+    ("electron_llf_sign", "- ctop * (dR * KR[q] - dL * KL[q])",
+     "+ ctop * (dR * KR[q] - dL * KL[q])", [ELEC]),
+    # electron heating with the wrong sign
+    ("heating_sign", "(ktot_new - ktot_adv);", "(ktot_adv - ktot_new);", [ELEC]),
+    # Kawazura: the exponential taken in T_p/T_e instead of T_e/T_p
+    ("kawazura_temperature_ratio", "rexp(-0.1 / trat)", "rexp(-0.1 * trat)", [ELEC]),
+    # Howes: c3 with the wrong sign of its log term
+    ("howes_c3_sign", "18.0 + 5.0 * lt", "18.0 - 5.0 * lt", [ELEC]),
+]
+
+
+def _source():
+    with open(SRC) as f:
+        return f.read()
+
+
+def test_every_mutation_applies_once():
+    src = _source()
+    names = [m[0] for m in MUTATIONS]
+    assert len(set(names)) == len(names)
+    for name, old, _new, _pins in MUTATIONS:
+        assert src.count(old) == 1, name
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new, pins):
+    src = _source()
+    assert src.count(old) == 1, name
+    cpp = tmp_path / (name + ".cpp")
+    so = tmp_path / ("lib" + name + ".so")
+    cpp.write_text(src.replace(old, new))
+    subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-o", str(so), str(cpp)], check=True)
+    env = dict(os.environ, ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "-m", "not gpu", *pins], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    # exit code 1: tests ran and failed (2-5 would be an error of the run itself)
+    assert r.returncode == 1, "no pin caught %s:\n%s" % (name, r.stdout[-2000:] + r.stderr[-2000:])
+    assert " failed" in r.stdout

@@ -286,7 +286,9 @@ def _golden_floors():
 
 
 def test_floors_bounds_hold():
-    """After the floors every bound of the paper's list holds at once."""
+    """After the floors every bound of the paper's list holds at once, and
+    each bound that acted leaves its variable on the bound: rho and u end at
+    the largest of their lower bounds."""
     gv = _golden_floors()
     gam = 4.0 / 3.0
     rng, Xs = _kerr_points(500, 8)
@@ -312,6 +314,14 @@ def test_floors_bounds_hold():
             assert np.array_equal(P2, P)
         if fl & 1:
             assert lor == pytest.approx(gv["gamma_max"], rel=1e-12)
+        # the bounds add the least material: u and rho end at the largest of
+        # their lower bounds (b^2 depends on neither, only on the capped
+        # velocity and the field)
+        u_min = max(P[1], gv["u_floor_coef"] * k ** gam, gv["beta_min"] * bsq / (2 * (gam - 1)))
+        assert P2[1] == pytest.approx(u_min, rel=1e-12)
+        rho_min = max(P[0], gv["rho_floor_coef"] * k, bsq / gv["sigma_max"],
+                      P2[1] / gv["u_over_rho_max"])
+        assert P2[0] == pytest.approx(rho_min, rel=1e-12)
     assert hits > 100
 
 
