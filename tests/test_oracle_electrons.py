@@ -257,8 +257,49 @@ def test_electrons_leave_the_fluid_alone_and_bounds_hold():
     kt = (GAM - 1) * u / rho ** GAM
     assert np.all(kt <= _golden_ktot_max() * (1 + 1e-14))
     assert np.allclose(K[0], kt, rtol=1e-14, atol=0)
+
     Te = K[1] * rho ** (e["game"] - 1)
     ue = K[1] * rho ** e["game"] / (e["game"] - 1)
     Tp = (e["gamp"] - 1) * (u - ue) / rho
     r = Tp / Te
     assert np.all(r >= e["tpte_min"] * (1 - 1e-12)) and np.all(r <= e["tpte_max"] * (1 + 1e-12))
+
+
+def test_uniform_electron_entropy_survives_a_fixup():
+    """Zones planted with u < 0 fail the inversion and take the mean of
+    their neighbours; with no heating a uniform kappa_e stays uniform through
+    that, as it does through the flow."""
+    pr = _ot(32, model=oracle.ELEC_CONSTANT, fel=0.0, tpte_min=0.0, tpte_max=math.inf)
+    P = pr.P.copy()
+    u0 = np.abs(P[1]).mean()
+    for (j, i) in ((5, 7), (20, 11), (13, 27)):
+        P[1, 0, j, i] = -u0
+    o = oracle.Oracle(pr)
+    o.set_prims(P)
+    o.set_K(pr.K)
+    o.step(1)
+    assert o.counters()["inv_failures"] > 0
+    k = o.get_K()[1]
+    assert np.abs(k - pr.K[1]).max() <= 1e-13 * np.abs(pr.K[1]).max()
+
+
+def test_entropy_bound_lowers_u_only_to_the_bound():
+    """Hot zones (u = 50 rho, P_gas/rho^gamma far above 3) come out of a
+    stage with P_gas/rho^gamma exactly at the bound: the bound takes no more
+    internal energy than it must."""
+    el = pb.with_electrons(pb.fm_torus(24, 20, 8), model=oracle.ELEC_KAWAZURA)
+    P = el.P.copy()
+    body = np.argwhere(P[0] > 0.2)  # inside the torus, where no floor acts
+    hot = [tuple(body[q]) for q in (0, len(body) // 2, len(body) - 1)]
+    for (k, j, i) in hot:
+        P[1, k, j, i] = 50.0 * P[0, k, j, i]
+    o = oracle.Oracle(el)
+    o.set_prims(P)
+    o.set_K(el.K)
+    o.predictor()
+    _pf, ff = o.flags()
+    P1 = o.get_prims()
+    kt = (GAM - 1) * P1[1] / P1[0] ** GAM
+    hit = (ff & oracle.FF_KTOT) != 0
+    assert all(hit[z] for z in hot)
+    assert np.allclose(kt[hit], _golden_ktot_max(), rtol=1e-13, atol=0)

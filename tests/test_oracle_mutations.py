@@ -23,6 +23,7 @@ GEOMETRY = "tests/test_oracle_geometry.py"
 RECON = "tests/test_oracle_recon.py"
 DRIFT = "tests/test_oracle_floors_drift.py"
 ELEC = "tests/test_oracle_electrons.py"
+BOUNDARIES = "tests/test_oracle_boundaries.py"
 
 # (name, text in the oracle source (exactly once), planted replacement, pins)
 MUTATIONS = [
@@ -80,6 +81,68 @@ MUTATIONS = [
     ("kawazura_temperature_ratio", "rexp(-0.1 / trat)", "rexp(-0.1 * trat)", [ELEC]),
     # Howes: c3 with the wrong sign of its log term
     ("howes_c3_sign", "18.0 + 5.0 * lt", "18.0 - 5.0 * lt", [ELEC]),
+    # Werner: (s/5)/(1 + s/5) for (s/5)/(2 + s/5)
+    ("werner_constant", "(s / 5.0) / (2.0 + s / 5.0)", "(s / 5.0) / (1.0 + s / 5.0)", [ELEC]),
+    # Rowan: the exponent 3.3 rounded to 3
+    ("rowan_exponent", "rpow(1.0 - r, 3.3)", "rpow(1.0 - r, 3.0)", [ELEC]),
+    # electron bounds: T_p/T_e's lower and upper limits swapped
+    ("electron_bounds_swapped", "real kmax = kk / (a + e.tpte_min * b);",
+     "real kmax = kk / (a + e.tpte_max * b);", [ELEC]),
+    # entropy bound: u set with (gamma - 1) multiplied instead of divided
+    ("entropy_bound_formula", "P[UU] = KTOT_MAX * rpow(P[RHO], e.gam) / (e.gam - 1.0);",
+     "P[UU] = KTOT_MAX * rpow(P[RHO], e.gam) * (e.gam - 1.0);", [ELEC]),
+    # electron fixup: the neighbours' kappa_tot averaged instead of kappa_e
+    ("electron_fixup_index", "if (S->elec) sumk += Kout[N + nb];", "if (S->elec) sumk += Kout[nb];",
+     [ELEC]),
+    # 4-velocity: u^t = gamma alpha for gamma/alpha
+    ("ut_lapse", "ucon[0] = gamma / g.alpha;", "ucon[0] = gamma * g.alpha;", [PHYSICS]),
+    # b^i = (B^i + b^t u^i)/u^t with the wrong sign
+    ("bcon_sign", "s.bcon[i] = (P[B1 + i - 1] + s.bcon[0] * s.ucon[i]) / s.ucon[0];",
+     "s.bcon[i] = (P[B1 + i - 1] - s.bcon[0] * s.ucon[i]) / s.ucon[0];", [PHYSICS]),
+    # induction flux b^j u^d - b^d u^j transposed
+    ("induction_flux_order", "s.bcon[j] * s.ucon[dir] - s.bcon[dir] * s.ucon[j]",
+     "s.bcon[dir] * s.ucon[j] - s.bcon[j] * s.ucon[dir]", [PHYSICS]),
+    # signal speeds: the wrong sign of b in one root
+    ("vchar_root", "real v1 = (-qb + disc) / (2.0 * qa);", "real v1 = (qb + disc) / (2.0 * qa);",
+     [PHYSICS]),
+    # 1D_W: the rest-mass term of w - rho with the wrong sign
+    ("w_minus_rho_sign", "return Wp * (1.0 - vsq) - q.D * vsq * sq / (1.0 + sq);",
+     "return Wp * (1.0 - vsq) + q.D * vsq * sq / (1.0 + sq);", [PHYSICS]),
+    # Kerr-Schild g_phiphi without its factor 2
+    ("kerr_schild_gphiphi", "ks[3][3] = s2 * (sig + a * a * s2 * (1.0 + 2.0 * r / sig));",
+     "ks[3][3] = s2 * (sig + a * a * s2 * (1.0 + r / sig));", [GEOMETRY]),
+    # bounds: sigma's limit multiplied instead of divided
+    ("sigma_bound", "real rmin_sig = s.bsq / BSQ_OVER_RHO_MAX;",
+     "real rmin_sig = s.bsq * BSQ_OVER_RHO_MAX;", [PHYSICS]),
+    # drift-frame bounds: the drift Lorentz factor inverted
+    ("drift_lorentz_factor", "real f = 1.0 / rsqrt_(1.0 + upar2);", "real f = rsqrt_(1.0 + upar2);",
+     [DRIFT]),
+    # CFL: the per-direction limits combined by a maximum instead of a sum
+    ("cfl_combination", "inv += 1.0 / ndt;", "inv = (1.0 / ndt > inv) ? 1.0 / ndt : inv;",
+     [SCHEME + "::test_uniform_dt_closed_form"]),
+    # fixup: failed neighbours included in the mean
+    ("fixup_uses_failed_zones",
+     "if (S->pflag[nb] != INV_OK) continue;\n              for (int v = 0; v < 5; v++)",
+     "for (int v = 0; v < 5; v++)", [SCHEME + "::test_torus_equatorial_symmetry"]),
+    # polar ghosts: B^2 not turned over
+    ("polar_b2_not_flipped",
+     "copy_zone(S, P, K, d, IDX(S, i, NG + g, k));\n          P[U2 * N + d] = -P[U2 * N + d];\n"
+     "          P[B2 * N + d] = -P[B2 * N + d];",
+     "copy_zone(S, P, K, d, IDX(S, i, NG + g, k));\n          P[U2 * N + d] = -P[U2 * N + d];",
+     [BOUNDARIES]),
+    # polar ghosts mirrored one zone off
+    ("polar_mirror_offset", "copy_zone(S, P, K, d, IDX(S, i, NG + g, k));",
+     "copy_zone(S, P, K, d, IDX(S, i, NG + g + 1, k));", [BOUNDARIES]),
+    # outflow ghosts: the inflow check with the wrong sign
+    ("outflow_ghost_inflow_sign", "if (P[U1 * N + d] > 0.0) P[U1 * N + d] = 0.0;",
+     "if (P[U1 * N + d] < 0.0) P[U1 * N + d] = 0.0;", [BOUNDARIES]),
+    # outflow faces: outflow zeroed instead of inflow
+    ("outflow_face_inflow_sign", "if (S->F[0][RHO * N + id] > 0.0) {",
+     "if (S->F[0][RHO * N + id] < 0.0) {", [BOUNDARIES]),
+    # outflow ghosts: B copied without the sqrt(-g) rescaling
+    ("outflow_b_not_rescaled",
+     "for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;\n          if (P[U1 * N + d] > 0.0)",
+     "(void)rescale;\n          if (P[U1 * N + d] > 0.0)", [BOUNDARIES]),
 ]
 
 
