@@ -139,6 +139,17 @@ MUTATIONS = [
     # outflow faces: outflow zeroed instead of inflow
     ("outflow_face_inflow_sign", "if (S->F[0][RHO * N + id] > 0.0) {",
      "if (S->F[0][RHO * N + id] < 0.0) {", [BOUNDARIES]),
+    # predictor-corrector: the corrector's geometric source at P^n, not P^(n+1/2)
+    ("corrector_source_state", "bad += advance_stage(S, S->P, S->Ph, S->P, dt,",
+     "bad += advance_stage(S, S->P, S->P, S->P, dt,",
+     [SCHEME + "::test_time_integration_second_order_in_curved_space"]),
+    # periodic X3 ghosts filled from the first zone instead of the last
+    ("x3_periodic_not_wrapped",
+     "copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, wrap_index(kg, n3)));\n"
+     "        else if (S->bc[2][0] == BC_OUTFLOW)",
+     "copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, NG));\n"
+     "        else if (S->bc[2][0] == BC_OUTFLOW)",
+     [SCHEME + "::test_conservation_periodic_flat_3d"]),
     # outflow ghosts: B copied without the sqrt(-g) rescaling
     ("outflow_b_not_rescaled",
      "for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;\n          if (P[U1 * N + d] > 0.0)",

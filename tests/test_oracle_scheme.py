@@ -14,6 +14,9 @@
 * Restart from a checkpoint is bitwise identical to an uninterrupted run
   (the paper's restart identity test, "Tests" section).
 * The time step on a uniform state has the closed form of the CFL rule.
+* A 3D periodic flat domain conserves everything across all three seams.
+* The predictor-corrector is second order in time on a non-stationary
+  flow in curved space (the stage state of the geometric source enters).
 """
 import math
 
@@ -90,6 +93,32 @@ def test_conservation_periodic_flat():
     assert o.counters()["inv_failures"] == 0
     U1 = _zone_U(pr, o.get_prims()).sum(axis=(1, 2, 3))
     scale = np.abs(_zone_U(pr, pr.P)).sum(axis=(1, 2, 3)) + 1.0
+    assert np.all(np.abs(U1 - U0) <= 1e-13 * scale), (U1 - U0) / scale
+
+
+def test_conservation_periodic_flat_3d():
+    """The same in three dimensions, with the state varying along every
+    axis, so that each periodic seam carries flux."""
+    n = (12, 10, 8)
+    x = [(np.arange(m) + 0.5) / m for m in n]
+    Z, Y, X = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    P0 = np.array([1.0, 0.6, 0.1, -0.05, 0.08, 0.3, 0.2, -0.1])
+    P = np.empty((8,) + n[::-1])
+    for v in range(8):
+        ph = 0.7 * v
+        P[v] = P0[v] + 0.05 * (np.sin(2 * math.pi * X + ph) + np.cos(2 * math.pi * Y - ph)
+                               + np.sin(2 * math.pi * Z + 2 * ph))
+    pr = _uniform_problem(n=n, P0=P0)
+    pr.P = P
+    o = oracle.Oracle(pr)
+    o.set_prims(P)
+    U0 = _zone_U(pr, P).sum(axis=(1, 2, 3))
+    o.step(3)
+    assert o.counters()["inv_failures"] == 0
+    P1 = o.get_prims()
+    assert not np.allclose(P1, P, rtol=1e-6, atol=0)
+    U1 = _zone_U(pr, P1).sum(axis=(1, 2, 3))
+    scale = np.abs(_zone_U(pr, P)).sum(axis=(1, 2, 3)) + 1.0
     assert np.all(np.abs(U1 - U0) <= 1e-13 * scale), (U1 - U0) / scale
 
 
@@ -294,3 +323,32 @@ def test_bondi_stationary_second_order():
     orders = np.log2(e[:-1] / e[1:])
     assert np.all(orders > 1.7), (e, orders)
     assert e[-1] < 1e-4
+
+
+def _bondi_perturbed(cfl, n=16, t_final=2.0):
+    """Michel inflow with a smooth 10% bump in rho and u: a flow in curved
+    space that is not stationary, run to t_final on one grid."""
+    pr = pb.bondi(n, n, t_final=t_final, r_in=1.5, recon=pb.RECON_WENO5, cfl=cfl)
+    Pg = pr.info["P_ghost"].copy()
+    s3, s2, s1 = Pg.shape[1:]
+    X1, X2 = np.meshgrid((np.arange(s1) - NG + 0.5) / n, (np.arange(s2) - NG + 0.5) / n)
+    bump = np.exp(-((X1 - 0.5) ** 2 + (X2 - 0.5) ** 2) / 0.02)
+    Pg[0] *= (1 + 0.1 * bump)[None]
+    Pg[1] *= (1 + 0.1 * bump)[None]
+    o = oracle.Oracle(pr)
+    o.set_prims(Pg)
+    assert o.step(100000) == 0
+    assert o.time()[0] == t_final
+    return o.get_prims()
+
+
+def test_time_integration_second_order_in_curved_space():
+    """The predictor-corrector is second order in time: on one grid, the
+    difference between runs at CFL 0.4 and 0.2 is 4x that between 0.2 and
+    0.1.  The flow is non-stationary and the metric curved, so the
+    geometric source's stage state enters (flat or stationary tests cannot
+    see it)."""
+    P4, P2, P1 = (_bondi_perturbed(c) for c in (0.4, 0.2, 0.1))
+    e1 = np.abs(P4 - P2).mean(axis=(1, 2, 3))[:4]
+    e2 = np.abs(P2 - P1).mean(axis=(1, 2, 3))[:4]
+    assert np.all(e1 / e2 > 3.3), (e1, e2)
