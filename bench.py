@@ -582,6 +582,90 @@ def workload_config(name, variant="none"):
     return cfg
 
 
+# FP64 peak from the unit counts and clock: 152 SMs, 2 DFMA per SM per clock
+# (ncu sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304
+# per GPU), 2 flops per DFMA, 2070 MHz maximum SM clock
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2070e6
+
+
+def build_roofline(prof, cpu, pr, zones, peak_fp64, config, variant="none"):
+    """Roofline of the FP64-bound kernel classes from the live per-class
+    device times (prof: class -> (total ms, launches)), the counting
+    oracle's algorithmic flops (cpu) and the derived FP64 peak; the
+    measured DFMA probe (peak_fp64) is reported beside it.  Returns
+    (roofline of the dominant class, per-class figures, algorithmic flops
+    per zone-cycle of this grid)."""
+    flops_zc = None
+    if cpu is not None and variant == "none" and pr.precision == 0:
+        # the oracle counts on a thin slab, whose extended-range faces weigh
+        # more per zone than the workload grid's: scale the per-unit counts
+        flops_zc = 2 * ((cpu["_face_flops_per_face"] + cpu["_recon_flops_per_face"]) *
+                        sum(faces_per_launch(pr.n)) +
+                        cpu["_update_flops_per_zone_stage"] * zones) / zones
+    roofline = None
+    kernels = {}
+    if cpu is not None and pr.precision == 0 and variant == "none":
+        # the FP64 kernels' algorithmic count
+        faces = faces_per_launch(pr.n)
+        hbm = 6791e9
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                hbm = float(json.load(f)["hbm_gbs"]) * 1e9
+        except (OSError, KeyError, ValueError):
+            pass
+        # algorithmic work and bytes per launch of each FP64-bound kernel class:
+        # face: two states in, one flux out (24 doubles per face); recon: the
+        # primitives in, two face values out (24 doubles per zone of the
+        # extended range); update: predictor 48, corrector 56 doubles per zone
+        work = {
+            "flux": ("kp_face (LLF face fluxes from reconstructed states)",
+                     cpu["_face_flops_per_face"] * sum(faces) / 3.0, 24 * 8 * sum(faces) / 3.0),
+            "recon": ("kp_recon (WENO5 face states, both faces of every zone)",
+                      cpu["_recon_flops_per_face"] * sum(faces) / 3.0,
+                      24 * 8 * (pr.n[0] + 2) * (pr.n[1] + 2) * (pr.n[2] + 2)),
+            "update": ("kp_update (conserved update + 1D_W inversion + bounds)",
+                       cpu["_update_flops_per_zone_stage"] * zones, 52 * 8 * zones),
+        }
+        same_src = kernel_source_hash() == NCU_TRAFFIC["src_hash"]
+        traffic = NCU_TRAFFIC.get(config) if same_src else None
+        pipe = NCU_FP64_PIPE.get(config) if same_src else None
+        for cls, (label, flops, nbytes) in work.items():
+            ms_c, n_c = prof[cls]
+            if not n_c:
+                continue
+            avg = ms_c / n_c
+            kernels[cls] = {"kernel": label, "avg_launch_ms": avg, "launches": n_c,
+                            "achieved_tflops": flops / (avg * 1e-3) / 1e12,
+                            "frac": flops / (avg * 1e-3) / FP64_PEAK_DERIVED,
+                            "frac_of_measured_probe": flops / (avg * 1e-3) / peak_fp64,
+                            "hbm_frac": nbytes / (avg * 1e-3) / hbm,
+                            "algorithmic_bytes": nbytes,
+                            "traffic": None if traffic is None else traffic.get(cls),
+                            "fp64_pipe_ncu": None if pipe is None else pipe.get(cls)}
+        dom = max(kernels, key=lambda k: prof[k][0]) if kernels else None
+        if dom:
+            kd = kernels[dom]
+            roofline = {"bound": "alu", "kernel": kd["kernel"],
+                        "achieved": kd["achieved_tflops"], "peak": FP64_PEAK_DERIVED / 1e12,
+                        "unit": "TFLOP/s", "frac": kd["frac"],
+                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                        "measured_probe_peak": peak_fp64 / 1e12,
+                        "frac_of_measured_probe": kd["frac_of_measured_probe"],
+                        "measured_probe": "dependency-free DFMA kernel (grmhd_fp64_peak), this run",
+                        "work": "algorithmic FP64 flops of the oracle's counting build",
+                        "avg_launch_ms": kd["avg_launch_ms"], "hbm_frac": kd["hbm_frac"],
+                        "algorithmic_bytes": kd["algorithmic_bytes"], "traffic": kd["traffic"],
+                        "fp64_pipe_ncu": kd["fp64_pipe_ncu"],
+                        "note": "algorithmic flops are the counting oracle's (adds, multiplies, "
+                                "divisions and square roots counted as one each); the kernel spends "
+                                "several FP64 instructions on each division and square root, so its "
+                                "FP64 pipe (fp64_pipe_ncu, the busy fraction in the ncu capture) "
+                                "runs above frac",
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one "
+                                          "launch, profiles/%s_fm_torus_128.md" % kd["kernel"].split()[0]}
+    return roofline, kernels, flops_zc
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -719,71 +803,8 @@ def main():
             cpu_all = cpu_oracle_all_cores(args.config, steps=2)
 
     launches = sum(v[1] for v in prof.values())
-    flops_zc = None
-    if cpu is not None and args.variant == "none" and pr.precision == 0:
-        # the oracle counts on a thin slab, whose extended-range faces weigh
-        # more per zone than the workload grid's: scale the per-unit counts
-        flops_zc = 2 * ((cpu["_face_flops_per_face"] + cpu["_recon_flops_per_face"]) *
-                        sum(faces_per_launch(pr.n)) +
-                        cpu["_update_flops_per_zone_stage"] * zones) / zones
-    roofline = None
-    kernels = {}
-    if cpu is not None and pr.precision == 0 and args.variant == "none":
-        # the FP64 kernels' algorithmic count
-        faces = faces_per_launch(pr.n)
-        hbm = 6791e9
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                hbm = float(json.load(f)["hbm_gbs"]) * 1e9
-        except (OSError, KeyError, ValueError):
-            pass
-        # algorithmic work and bytes per launch of each FP64-bound kernel class:
-        # face: two states in, one flux out (24 doubles per face); recon: the
-        # primitives in, two face values out (24 doubles per zone of the
-        # extended range); update: predictor 48, corrector 56 doubles per zone
-        work = {
-            "flux": ("kp_face (LLF face fluxes from reconstructed states)",
-                     cpu["_face_flops_per_face"] * sum(faces) / 3.0, 24 * 8 * sum(faces) / 3.0),
-            "recon": ("kp_recon (WENO5 face states, both faces of every zone)",
-                      cpu["_recon_flops_per_face"] * sum(faces) / 3.0,
-                      24 * 8 * (pr.n[0] + 2) * (pr.n[1] + 2) * (pr.n[2] + 2)),
-            "update": ("kp_update (conserved update + 1D_W inversion + bounds)",
-                       cpu["_update_flops_per_zone_stage"] * zones, 52 * 8 * zones),
-        }
-        same_src = kernel_source_hash() == NCU_TRAFFIC["src_hash"]
-        traffic = NCU_TRAFFIC.get(args.config) if same_src else None
-        pipe = NCU_FP64_PIPE.get(args.config) if same_src else None
-        for cls, (label, flops, nbytes) in work.items():
-            ms_c, n_c = prof[cls]
-            if not n_c:
-                continue
-            avg = ms_c / n_c
-            kernels[cls] = {"kernel": label, "avg_launch_ms": avg, "launches": n_c,
-                            "achieved_tflops": flops / (avg * 1e-3) / 1e12,
-                            "frac": flops / (avg * 1e-3) / peak_fp64,
-                            "hbm_frac": nbytes / (avg * 1e-3) / hbm,
-                            "algorithmic_bytes": nbytes,
-                            "traffic": None if traffic is None else traffic.get(cls),
-                            "fp64_pipe_ncu": None if pipe is None else pipe.get(cls)}
-        dom = max(kernels, key=lambda k: prof[k][0]) if kernels else None
-        if dom:
-            kd = kernels[dom]
-            roofline = {"bound": "alu", "kernel": kd["kernel"],
-                        "achieved": kd["achieved_tflops"], "peak": peak_fp64 / 1e12,
-                        "unit": "TFLOP/s", "frac": kd["frac"],
-                        "peak_source": "measured FP64 FMA throughput (grmhd_fp64_peak, this run); "
-                                       "nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz = 1.259",
-                        "work": "algorithmic FP64 flops of the oracle's counting build",
-                        "avg_launch_ms": kd["avg_launch_ms"], "hbm_frac": kd["hbm_frac"],
-                        "algorithmic_bytes": kd["algorithmic_bytes"], "traffic": kd["traffic"],
-                        "fp64_pipe_ncu": kd["fp64_pipe_ncu"],
-                        "note": "algorithmic flops are the counting oracle's (adds, multiplies, "
-                                "divisions and square roots counted as one each); the kernel spends "
-                                "several FP64 instructions on each division and square root, so its "
-                                "FP64 pipe (fp64_pipe_ncu, the busy fraction in the ncu capture) "
-                                "runs above frac",
-                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one "
-                                          "launch, profiles/%s_fm_torus_128.md" % kd["kernel"].split()[0]}
+    roofline, kernels, flops_zc = build_roofline(prof, cpu, pr, zones, peak_fp64, args.config,
+                                                 args.variant)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -803,8 +824,10 @@ def main():
             "cpu_baseline_all_cores": cpu_all,
             "algorithmic_fp64_flops_per_zone_cycle": flops_zc,
             "fp64_ceiling": None if flops_zc is None else {
-                "value": peak_fp64 / flops_zc, "unit": UNIT, "frac": value * flops_zc / peak_fp64,
-                "note": "measured FP64 peak / algorithmic FP64 flops per zone-cycle of this grid "
+                "value": FP64_PEAK_DERIVED / flops_zc, "unit": UNIT,
+                "frac": value * flops_zc / FP64_PEAK_DERIVED,
+                "frac_of_measured_probe": value * flops_zc / peak_fp64,
+                "note": "derived FP64 peak / algorithmic FP64 flops per zone-cycle of this grid "
                         "(the oracle's counts per face and per zone-stage, scaled to its faces and "
                         "zones)"},
             "clocks": clk,
