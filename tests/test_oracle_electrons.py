@@ -106,8 +106,11 @@ def _state_for(beta, trat, rho=1.0, Te=1e-3, game=GAME, gamp=GAMP):
     ("HOWES", 3.0, 1.0, 1 / (1 + 0.92 * (1.44 + 9) / (324 + 9) * math.sqrt(MP_ME) * math.exp(-1 / 3))),
     ("HOWES", 1.0, 10.0, 1 / (1 + 0.92 * (0.0256 + 1) / (529 + 1) * math.sqrt(10 * MP_ME) * math.exp(-1))),
     ("HOWES", 1.0, 0.1, 1 / (1 + 0.92 * (144 + 1) / (324 + 1) * math.sqrt(0.1 * MP_ME) * math.exp(-1))),
-    # Sharma at T_p = 9 T_e: Q_e/Q_i = 0.33/3
+    # Sharma at T_p = 9 T_e: Q_e/Q_i = 0.33/3; and at both ends of the range
+    # the default T_p/T_e bounds allow, where the fit applies unclamped
     ("SHARMA", 0.3, 9.0, 0.11 / 1.11),
+    ("SHARMA", 0.3, 1e3, (0.33 / math.sqrt(1e3)) / (1 + 0.33 / math.sqrt(1e3))),
+    ("SHARMA", 0.3, 1e-3, (0.33 * math.sqrt(1e3)) / (1 + 0.33 * math.sqrt(1e3))),
 ])
 def test_fits_at_special_points(model, beta, trat, expect):
     """Each fit at a point where it reduces to a closed form by hand: a

@@ -150,6 +150,30 @@ MUTATIONS = [
      "copy_zone(S, P, K, IDX(S, i, j, kg), IDX(S, i, j, NG));\n"
      "        else if (S->bc[2][0] == BC_OUTFLOW)",
      [SCHEME + "::test_conservation_periodic_flat_3d"]),
+    # WENO5: a smoothness indicator's second term with 1/2 for 1/4
+    ("weno5_indicator_coefficient", "  real e0 = eps + ((13.0 / 12.0) * t * t + 0.25 * s * s);",
+     "  real e0 = eps + ((13.0 / 12.0) * t * t + 0.5 * s * s);", [RECON]),
+    # LLF: the left state's face value taken from the wrong side of its zone
+    ("face_states_swapped", "PL[v] = S->Rz[v * N + c - st];", "PL[v] = S->Lz[v * N + c - st];",
+     [SCHEME + "::test_linear_mode_second_order"]),
+    # LLF: the left-going speeds' sign in c_max
+    ("llf_cmin_sign", "real cmin = rmax(rmax(real(0.0), -vminL), -vminR);",
+     "real cmin = rmax(rmax(real(0.0), vminL), vminR);",
+     [SCHEME + "::test_torus_equilibrium_residual_second_order"]),
+    # CFL: the Courant factor dropped
+    ("cfl_factor_missing", "double ndt = S->cfl * S->dx[d] / ct;", "double ndt = S->dx[d] / ct;",
+     [SCHEME + "::test_uniform_dt_closed_form"]),
+    # flux-CT: emf1 averaged over the wrong neighbour
+    ("emf1_neighbour",
+     "e1[c] = 0.25 * (F2[B3 * N + c] + F2[B3 * N + km] - F3[B2 * N + c] - F3[B2 * N + jm]);",
+     "e1[c] = 0.25 * (F2[B3 * N + c] + F2[B3 * N + jm] - F3[B2 * N + c] - F3[B2 * N + jm]);",
+     [SCHEME]),
+    # electron fluxes: the two sides' densities swapped in the LLF term
+    ("electron_densities_swapped", "real dL = PL[RHO] * sL.ucon[0], dR = PR[RHO] * sR.ucon[0];",
+     "real dR = PL[RHO] * sL.ucon[0], dL = PR[RHO] * sR.ucon[0];", [ELEC]),
+    # heating fits: T_p/T_e clamped inside the range the bounds allow
+    ("temperature_ratio_clamp", "trat = rmin(rmax(trat, real(1.0e-20)), real(1.0e20));",
+     "trat = rmin(rmax(trat, real(1.0e-2)), real(1.0e2));", [ELEC]),
     # outflow ghosts: B copied without the sqrt(-g) rescaling
     ("outflow_b_not_rescaled",
      "for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;\n          if (P[U1 * N + d] > 0.0)",
