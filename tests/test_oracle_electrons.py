@@ -209,6 +209,30 @@ def test_passive_electron_entropy_is_conserved():
     assert not np.allclose(o.get_K()[1], K[1], rtol=1e-6, atol=0)
 
 
+def test_passive_electron_entropy_is_conserved_in_compressive_flow():
+    """A fast mode of amplitude 1e-2 compresses the gas; kappa_e is made to
+    vary with div(rho u), so any stage that carries kappa_e with the wrong
+    state's mass would change the total sum(rho u^t kappa_e)."""
+    pr = pb.with_electrons(pb.linear_mode(32, kind="fast", amp=1e-2), model=oracle.ELEC_CONSTANT,
+                           fel=0.0, tpte_min=0.0, tpte_max=math.inf)
+    P = pr.P
+    n1, n2 = pr.n[0], pr.n[1]
+    fx, fy = P[0] * P[2], P[0] * P[3]
+    div = ((np.roll(fx, -1, axis=2) - np.roll(fx, 1, axis=2)) * n1 / 2 +
+           (np.roll(fy, -1, axis=1) - np.roll(fy, 1, axis=1)) * n2 / 2)
+    K = pr.K.copy()
+    K[1] *= 1 + 0.5 * div / np.abs(div).max()
+    o = oracle.Oracle(pr)
+    o.set_prims(P)
+    o.set_K(K)
+    k0, m0 = _conserved_kel(o, pr)
+    o.step(4)
+    k1, m1 = _conserved_kel(o, pr)
+    assert m1 == pytest.approx(m0, rel=1e-13)
+    assert k1 == pytest.approx(k0, rel=1e-13)
+    assert not np.allclose(o.get_K()[1], K[1], rtol=1e-6, atol=0)
+
+
 def test_uniform_electron_entropy_stays_uniform():
     """The entropies ride with the mass: a uniform kappa_e (f_e = 0) stays
     uniform while the flow compresses and shears it."""

@@ -174,6 +174,10 @@ MUTATIONS = [
     # heating fits: T_p/T_e clamped inside the range the bounds allow
     ("temperature_ratio_clamp", "trat = rmin(rmax(trat, real(1.0e-20)), real(1.0e20));",
      "trat = rmin(rmax(trat, real(1.0e-2)), real(1.0e2));", [ELEC]),
+    # electron entropies carried from the source stage's kappa, not kappa^n
+    ("electron_advection_state", "real Uk = Ui[RHO] * Ki[o + c] + dtp * (0.0 - divk);",
+     "real Uk = Ui[RHO] * Ks[o + c] + dtp * (0.0 - divk);",
+     [ELEC + "::test_passive_electron_entropy_is_conserved_in_compressive_flow"]),
     # outflow ghosts: B copied without the sqrt(-g) rescaling
     ("outflow_b_not_rescaled",
      "for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;\n          if (P[U1 * N + d] > 0.0)",
