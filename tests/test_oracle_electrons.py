@@ -246,6 +246,23 @@ def test_uniform_electron_entropy_stays_uniform():
     assert not np.allclose(o.get_prims()[0], pr.P[0], rtol=1e-6, atol=0)
 
 
+def test_uniform_electron_entropy_stays_uniform_on_the_torus():
+    """The same on the Kerr torus, whose polar and outflow boundaries zero
+    the mass flux on some faces and whose bounds add mass: with kappa_e
+    uniform its flux is kappa_e times the mass flux, so kappa_e stays
+    uniform only if every boundary treats both alike."""
+    pr = pb.with_electrons(pb.fm_torus(16, 16, 4), model=oracle.ELEC_CONSTANT, fel=0.0,
+                           tpte_min=0.0, tpte_max=math.inf)
+    K = pr.K.copy()
+    K[1] = 1e-6
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.set_K(K)
+    o.step(2)
+    assert o.counters()["floor_hits"] > 0
+    assert np.abs(o.get_K()[1] - 1e-6).max() <= 1e-13 * 1e-6
+
+
 def test_electrons_carry_all_entropy_when_they_take_all_the_heat():
     pr = pb.orszag_tang(24, recon=pb.RECON_WENO5)
     pr = pb.with_electrons(pr, model=oracle.ELEC_CONSTANT, fel=1.0, game=pr.gamma, tpte_min=0.0,

@@ -178,6 +178,12 @@ MUTATIONS = [
     ("electron_advection_state", "real Uk = Ui[RHO] * Ki[o + c] + dtp * (0.0 - divk);",
      "real Uk = Ui[RHO] * Ks[o + c] + dtp * (0.0 - divk);",
      [ELEC + "::test_passive_electron_entropy_is_conserved_in_compressive_flow"]),
+    # outer boundary: the mass inflow zeroed but the entropies' flux kept
+    ("outflow_electron_flux_kept",
+     "          if (S->F[0][RHO * N + id] < 0.0) {\n            S->F[0][RHO * N + id] = 0.0;\n"
+     "            if (S->elec)\n              for (int q = 0; q < 2; q++) S->FK[0][q * N + id] = 0.0;",
+     "          if (S->F[0][RHO * N + id] < 0.0) {\n            S->F[0][RHO * N + id] = 0.0;",
+     [ELEC + "::test_uniform_electron_entropy_stays_uniform_on_the_torus"]),
     # outflow ghosts: B copied without the sqrt(-g) rescaling
     ("outflow_b_not_rescaled",
      "for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;\n          if (P[U1 * N + d] > 0.0)",
