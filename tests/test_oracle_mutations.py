@@ -11,6 +11,7 @@ not touched.
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -204,19 +205,37 @@ def test_every_mutation_applies_once():
         assert src.count(old) == 1, name
 
 
-@pytest.mark.parametrize("name,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, name, old, new, pins):
+def _run_mutation(workdir, name, old, new, pins):
+    """Build the oracle with one planted mistake and run its pins against
+    it; returns the pins' pytest exit code and output."""
     src = _source()
     assert src.count(old) == 1, name
-    cpp = tmp_path / (name + ".cpp")
-    so = tmp_path / ("lib" + name + ".so")
-    cpp.write_text(src.replace(old, new))
+    cpp = os.path.join(workdir, name + ".cpp")
+    so = os.path.join(workdir, "lib" + name + ".so")
+    with open(cpp, "w") as f:
+        f.write(src.replace(old, new))
     subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                    "-o", str(so), str(cpp)], check=True)
-    env = dict(os.environ, ORACLE_LIB=str(so))
+                    "-o", so, cpp], check=True)
+    env = dict(os.environ, ORACLE_LIB=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         "-m", "not gpu", *pins], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every case built and run at once (independent processes)."""
+    workdir = str(tmp_path_factory.mktemp("mutations"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futures = {m[0]: ex.submit(_run_mutation, workdir, *m) for m in MUTATIONS}
+        return {name: f.result() for name, f in futures.items()}
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(outcomes, name):
+    rc, out = outcomes[name]
     # exit code 1: tests ran and failed (2-5 would be an error of the run itself)
-    assert r.returncode == 1, "no pin caught %s:\n%s" % (name, r.stdout[-2000:] + r.stderr[-2000:])
-    assert " failed" in r.stdout
+    assert rc == 1, "no pin caught %s:\n%s" % (name, out)
+    assert " failed" in out
