@@ -185,6 +185,23 @@ MUTATIONS = [
      "            if (S->elec)\n              for (int q = 0; q < 2; q++) S->FK[0][q * N + id] = 0.0;",
      "          if (S->F[0][RHO * N + id] < 0.0) {\n            S->F[0][RHO * N + id] = 0.0;",
      [ELEC + "::test_uniform_electron_entropy_stays_uniform_on_the_torus"]),
+    # bounds: the density floor reported as the internal-energy floor
+    ("floor_flag_swapped",
+     "if (P[RHO] < rho_fl) { P[RHO] = rho_fl; flags |= FF_RHO_GEOM; }",
+     "if (P[RHO] < rho_fl) { P[RHO] = rho_fl; flags |= FF_U_GEOM; }", [PHYSICS]),
+    # ghost fill: the electron entropies not copied into the ghosts
+    ("electron_ghosts_not_filled",
+     "    for (int q = 0; q < 2; q++) K[q * S->ntot + dst] = K[q * S->ntot + src];", "    (void)K;",
+     [ELEC]),
+    # electrons: kappa_tot reset from u/rho instead of u/rho^gamma
+    ("ktot_reset_formula", "  K[0] = (e.gam - 1.0) * P[UU] / rpow(P[RHO], e.gam);",
+     "  K[0] = (e.gam - 1.0) * P[UU] / P[RHO];", [ELEC]),
+    # 1D_W: a negative u reported as success
+    ("negative_u_accepted", "  if (uu < 0.0) return INV_U_NEG;", "  if (uu < 0.0) return INV_OK;",
+     [ELEC]),
+    # b^2 without its time component
+    ("bsq_without_time_part", "for (int m = 0; m < 4; m++) s.bsq += s.bcon[m] * s.bcov[m];",
+     "for (int m = 1; m < 4; m++) s.bsq += s.bcon[m] * s.bcov[m];", [PHYSICS]),
     # outflow ghosts: B copied without the sqrt(-g) rescaling
     ("outflow_b_not_rescaled",
      "for (int b = B1; b <= B3; b++) P[b * N + d] *= rescale;\n          if (P[U1 * N + d] > 0.0)",

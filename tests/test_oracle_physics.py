@@ -314,6 +314,10 @@ def test_floors_bounds_hold():
             assert np.array_equal(P2, P)
         if fl & 1:
             assert lor == pytest.approx(gv["gamma_max"], rel=1e-12)
+        # each geometric-floor flag names its own bound: set exactly when the
+        # variable came in below that floor
+        assert bool(fl & oracle.FF_RHO_GEOM) == bool(P[0] < gv["rho_floor_coef"] * k)
+        assert bool(fl & oracle.FF_U_GEOM) == bool(P[1] < gv["u_floor_coef"] * k ** gam)
         # the bounds add the least material: u and rho end at the largest of
         # their lower bounds (b^2 depends on neither, only on the capped
         # velocity and the field)
