@@ -25,6 +25,7 @@ RECON = "tests/test_oracle_recon.py"
 DRIFT = "tests/test_oracle_floors_drift.py"
 ELEC = "tests/test_oracle_electrons.py"
 BOUNDARIES = "tests/test_oracle_boundaries.py"
+FIXUP_DT = "tests/test_oracle_fixup_dt.py"
 
 # (name, text in the oracle source (exactly once), planted replacement, pins)
 MUTATIONS = [
@@ -125,6 +126,17 @@ MUTATIONS = [
     ("fixup_uses_failed_zones",
      "if (S->pflag[nb] != INV_OK) continue;\n              for (int v = 0; v < 5; v++)",
      "for (int v = 0; v < 5; v++)", [SCHEME + "::test_torus_equatorial_symmetry"]),
+    # fixup: only the six face neighbours averaged
+    ("fixup_six_face_neighbours", "if (di == 0 && dj == 0 && dk == 0) continue;",
+     "if (di * di + dj * dj + dk * dk != 1) continue;", [FIXUP_DT]),
+    # fixup: the failed zone's own values counted in the mean
+    ("fixup_mean_includes_centre", "if (di == 0 && dj == 0 && dk == 0) continue;",
+     "if (di == 0 && dj == 0 && dk == 0) {\n                for (int v = 0; v < 5; v++) "
+     "sum[v] += Pout[v * N + c];\n                cnt++;\n                continue;\n"
+     "              }", [FIXUP_DT]),
+    # time step: the growth limit 2 instead of 1.3
+    ("dt_growth_limit", "dt > 1.3 * S->dt_prev) dt = 1.3 * S->dt_prev;",
+     "dt > 2.0 * S->dt_prev) dt = 2.0 * S->dt_prev;", [FIXUP_DT]),
     # polar ghosts: B^2 not turned over
     ("polar_b2_not_flipped",
      "copy_zone(S, P, K, d, IDX(S, i, NG + g, k));\n          P[U2 * N + d] = -P[U2 * N + d];\n"
