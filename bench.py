@@ -47,10 +47,10 @@ WORKLOADS = {
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each FP64-bound kernel class on the 128^3 torus, from the ncu captures whose
-# summaries are under profiles/ (kp_recon<0>, kp_face<0>, kp_update).  The
-# figures hold while the kernel sources hash to SRC_HASH; otherwise the
-# bench reports the traffic as unknown (null).
+# each FP64-bound kernel class on the 128^3 torus, from an ncu capture of one
+# launch of each (kp_recon<0>, kp_face<0>, kp_update).  The figures hold
+# while the kernel sources hash to src_hash; otherwise the bench reports the
+# traffic as unknown (null).
 NCU_TRAFFIC = {"src_hash": "8f586f76c0bbb338",
                "torus128": {"recon": 152264192 + 229483264, "flux": 297974016 + 113205504,
                             "update": 594006016 + 271203840}}
@@ -554,6 +554,92 @@ def mixed_accuracy(grmhd, steps, stream):
             "mixed_ff_primitives": norms(states[3][:, 3:-3, 3:-3, 3:-3])}
 
 
+def mode_accuracy(grmhd, stream):
+    """The 64x64 fast mode (MC, CFL 0.9) run for one period on the GPU and on
+    the oracle: per-primitive L1 of the difference from the analytic
+    eigenmode at t_final (mean over zones of |P - P_exact|), their sum, and
+    the sum relative to the mode's amplitude (1e-4)."""
+    import numpy as np
+    import oracle
+    pr = make_problem("mode64")
+    ex = pr.exact(pr.t_final)
+    s = grmhd.Sim(pr, stream=stream)
+    s.set_prims(pr.P)
+    st = s.step(100000)
+    Pg = s.get_prims()
+    s.close()
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    o.step(100000)
+    Po = o.get_prims()
+    t_o, _, n_o = o.time()
+    o.close()
+    names = ["rho", "u", "u1", "u2", "u3", "B1", "B2", "B3"]
+    eg = np.abs(Pg - ex).mean(axis=(1, 2, 3))
+    eo = np.abs(Po - ex).mean(axis=(1, 2, 3))
+    amp = pr.info["amp"]
+    return {"workload": WORKLOADS["mode64"]["label"] + "_one_period",
+            "t_final": pr.t_final, "cycles_gpu": st["steps"], "cycles_oracle": n_o,
+            "l1_gpu": {nm: float(v) for nm, v in zip(names, eg)},
+            "l1_oracle": {nm: float(v) for nm, v in zip(names, eo)},
+            "l1_sum_gpu": float(eg.sum()), "l1_sum_oracle": float(eo.sum()),
+            "l1_sum_over_amplitude_gpu": float(eg.sum() / amp),
+            "l1_sum_over_amplitude_oracle": float(eo.sum() / amp),
+            "gpu_vs_oracle_rel": float(abs(eg.sum() - eo.sum()) / eo.sum()),
+            "norm": "mean over the 64x64 zones of |P_v - P_exact,v| at t = one period; "
+                    "amplitude 1e-4 of the eigenvector (unit norm)"}
+
+
+def mixed_vs_oracle(grmhd, steps, stream):
+    """The 288x128x128 torus (R_out = 1000) advanced `steps` cycles by the
+    oracle (FP64, one host core) and on the GPU in FP64, in the mixed mode
+    and in the mixed mode with the float-float update, every GPU run on the
+    oracle's geometry: per-primitive L1 and Linf of each GPU state's
+    difference from the oracle's, relative to the oracle state's mean and
+    largest magnitude, over all interior zones and over the torus (rho >
+    1e-2), and the corner divergence of each."""
+    import dataclasses
+    import numpy as np
+    import oracle
+    pr = make_problem("torus288")
+    t0 = time.perf_counter()
+    o = oracle.Oracle(pr)
+    o.set_prims(pr.P)
+    geoms = [o.geom(loc) for loc in range(4)]
+    o.step(steps)
+    ref = o.get_prims()
+    o.close()
+    oracle_s = time.perf_counter() - t0
+    names = ["rho", "u", "u1", "u2", "u3", "B1", "B2", "B3"]
+    body = ref[0] > 1e-2
+    dx = [(pr.xmax[d] - pr.xmin[d]) / pr.n[d] for d in range(3)]
+    out = {"workload": WORKLOADS["torus288"]["label"].replace("_fp64", ""), "steps": steps,
+           "reference": "the oracle (FP64, CPU), same geometry", "oracle_seconds": oracle_s}
+    for prec, key in ((0, "fp64"), (1, "mixed"), (3, "mixed_ff")):
+        p = dataclasses.replace(pr, precision=prec)
+        s = grmhd.Sim(p, stream=stream)
+        for loc in range(4):
+            s.set_geom(loc, geoms[loc])
+        s.set_prims(p.P)
+        s.step(steps)
+        a = s.get_prims()
+        Pgh = s.get_prims(with_ghosts=True)
+        s.close()
+        res = {}
+        for v, nm in enumerate(names):
+            d = np.abs(a[v] - ref[v])
+            res[nm] = {"l1_rel": float(d.mean() / max(np.abs(ref[v]).mean(), 1e-300)),
+                       "linf_rel": float(d.max() / max(np.abs(ref[v]).max(), 1e-300)),
+                       "torus_l1_rel": float(d[body].mean() / max(np.abs(ref[v][body]).mean(), 1e-300)),
+                       "torus_linf_rel": float(d[body].max() / max(np.abs(ref[v][body]).max(), 1e-300))}
+        m, sc = corner_divb(Pgh, geoms[0][32], dx, pr.n)
+        res["divb_rel"] = m / sc
+        out[key] = res
+    out["norms"] = ("l1_rel: mean |gpu - oracle| / mean |oracle| of the component; linf_rel: max / "
+                    "max; over all interior zones; torus_*: over zones with rho > 1e-2")
+    return out
+
+
 def apply_variant(pr, variant):
     """The workload with a variant of the step switched on: the bounds in the
     drift frame, or electron entropies heated by the Kawazura et al. model
@@ -661,8 +747,9 @@ def build_roofline(prof, cpu, pr, zones, peak_fp64, config, variant="none"):
                                 "several FP64 instructions on each division and square root, so its "
                                 "FP64 pipe (fp64_pipe_ncu, the busy fraction in the ncu capture) "
                                 "runs above frac",
-                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one "
-                                          "launch, profiles/%s_fm_torus_128.md" % kd["kernel"].split()[0]}
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                          "capture of one launch of %s on this workload"
+                                          % kd["kernel"].split()[0]}
     return roofline, kernels, flops_zc
 
 
@@ -683,6 +770,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision, batched and accuracy legs")
     ap.add_argument("--accuracy-steps", type=int, default=100)
+    ap.add_argument("--oracle-steps", type=int, default=2,
+                    help="cycles of the 288x128x128 torus run by the oracle for the precision "
+                         "modes' error against it (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the 200-request serving stream to run (0: skip)")
     ap.add_argument("--serve-zone-cap", type=int, default=1 << 22)
@@ -795,12 +885,17 @@ def main():
             dist.destroy_process_group()
         return
 
+    # the oracle leg: the CPU baseline, and the accuracy of the GPU path and
+    # of the oracle itself against the analytic mode and against each other
     cpu = None
     cpu_all = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_sample(args.config, steps=2)
         if not args.no_extras:
             cpu_all = cpu_oracle_all_cores(args.config, steps=2)
+            extras["mode_accuracy"] = mode_accuracy(grmhd, stream)
+            if args.oracle_steps > 0:
+                extras["mixed_vs_oracle"] = mixed_vs_oracle(grmhd, args.oracle_steps, stream)
 
     launches = sum(v[1] for v in prof.values())
     roofline, kernels, flops_zc = build_roofline(prof, cpu, pr, zones, peak_fp64, args.config,

@@ -172,24 +172,34 @@ typedef struct {
 
 /* Allocate a simulation on the current CUDA device and build its geometry
  * (metric, inverse, sqrt(-g), lapse at zone centres and faces, numerical
- * connection at centres).  stream: a cudaStream_t (NULL = legacy default
+ * connection at centres).  The problem it states is the paper's
+ * ("Functionality and Purpose": ideal GRMHD in a stationary spacetime on a
+ * logically Cartesian mesh in arbitrary coordinates); the metric quantities
+ * are evaluated numerically from the analytic line element ("Implementation
+ * Notes", second paragraph).  stream: a cudaStream_t (NULL = legacy default
  * stream) on which every later call of this simulation is ordered.
  * n1, n2, n3 >= 1 and (n1+6)(n2+6)(n3+6) < 2^31.  *out is set on success. */
 int grmhd_create(const grmhd_grid *grid, const grmhd_metric *metric,
                  const grmhd_params *params, void *stream, grmhd_sim **out);
 
-/* Free every device buffer.  NULL is accepted. */
+/* Free every device buffer.  NULL is accepted.  (The end of the
+ * simulation's lifetime; the paper has no separate passage for it.) */
 int grmhd_destroy(grmhd_sim *sim);
 
 /* Set the interior primitives ([8][n3][n2][n1]) and fill the ghosts by the
- * boundary conditions. */
+ * boundary conditions.  The primitive variables (density, internal energy,
+ * velocity; "Implementation Notes", third paragraph) and the field are the
+ * state the scheme evolves ("Functionality and Purpose"). */
 int grmhd_set_prims(grmhd_sim *sim, const double *P, int on_device);
 
 /* Set primitives including ghosts ([8][n3+6][n2+6][n1+6]); the boundary
  * conditions then refill every non-FIXED ghost region. */
 int grmhd_set_prims_ghost(grmhd_sim *sim, const double *P, int on_device);
 
-/* Read the primitives, interior ([8][n3][n2][n1]) or with ghosts. */
+/* Read the primitives, interior ([8][n3][n2][n1]) or with ghosts: the
+ * state after the steps taken, recovered from the conserved variables by
+ * the 1D_W inversion and bounded ("Implementation Notes", third paragraph
+ * and list of bounds). */
 int grmhd_get_prims(grmhd_sim *sim, double *P, int with_ghosts, int on_device);
 
 /* The electron entropies (kappa_tot, kappa_e) of a simulation created with
@@ -200,7 +210,13 @@ int grmhd_get_prims(grmhd_sim *sim, double *P, int with_ghosts, int on_device);
 int grmhd_set_electrons(grmhd_sim *sim, const double *K, int with_ghosts, int on_device);
 int grmhd_get_electrons(grmhd_sim *sim, double *K, int with_ghosts, int on_device);
 
-/* Advance nsteps full predictor-corrector steps, enqueued on the stream.
+/* Advance nsteps full predictor-corrector steps, enqueued on the stream:
+ * the conservative HARM update ("Functionality and Purpose") with flux-CT
+ * ("Implementation Notes", first paragraph), the 1D_W inversion (third
+ * paragraph) and the bounds at the end of each stage (list of bounds); the
+ * predictor-corrector, reconstruction, LLF fluxes and fixup are the HARM
+ * method of Gammie et al. (2003), which the paper builds on and does not
+ * print.
  * stats == NULL: returns after enqueueing (errors of this call surface at
  * the next synchronising call).  stats != NULL: synchronises, fills *stats
  * and returns GRMHD_ERR_INVERSION if any failed zone had no valid neighbour
@@ -243,7 +259,10 @@ int grmhd_get_flags(grmhd_sim *sim, int *pflag, int *fflag);
 int grmhd_get_geometry(grmhd_sim *sim, int loc, double *out);
 
 /* Replace the geometry at location loc with caller-supplied values, in the
- * layout grmhd_get_geometry() returns (host memory; loc 0..2: g_{mu nu},
+ * spirit of the paper's numerically evaluated metric ("Implementation
+ * Notes", second paragraph: any stationary spacetime whose metric is known
+ * runs on the same scheme), in the layout grmhd_get_geometry() returns
+ * (host memory; loc 0..2: g_{mu nu},
  * g^{mu nu}, sqrt(-g), lapse; loc 3: the connection).  Only the upper
  * triangle (m <= n) of each symmetric index pair is read.  This runs the
  * step on a tabulated metric (any stationary, X3-independent spacetime
@@ -304,6 +323,18 @@ int grmhd_autotune(grmhd_sim *sim, int trials, double *ms_before, double *ms_aft
  * the FP64-bound kernels. */
 int grmhd_fp64_peak(long long iters, double *flops);
 
+/* The reciprocal that the step uses inside its arithmetic (WENO5 weights,
+ * signal speeds, the Newton iteration of the 1D_W inversion; the paper's
+ * "Implementation Notes" name the inversion, the HARM method the rest): the
+ * hardware approximation refined by one third-order step, within 2 ulp of
+ * the IEEE quotient 1/x for |x| in [2^-1022, 2^1022].  Outside that range
+ * the approximation flushes subnormal inputs and results to zero: a zero or
+ * subnormal x gives NaN, |x| > 2^1022 gives a zero of x's sign (the IEEE
+ * results there are infinite, huge or subnormal).  x, out:
+ * n device doubles (out[i] = rcp(x[i])), enqueued on stream; for
+ * verification of the step's arithmetic. */
+int grmhd_rcp(const double *x, double *out, long long n, void *stream);
+
 /* Face-flux stage without any device allocation (no counterpart in the
  * paper: it exists for callers of this library that cannot allocate).
  * Serving processes that have reserved all device memory up front, code
@@ -317,16 +348,24 @@ int grmhd_fp64_peak(long long iters, double *flops);
  *         fills it (entries outside the computed face ranges are zeroed).
  *   ctop: host double[3] for the interior signal-speed maxima, or NULL;
  *         when given, the call synchronises the stream to read them.
+ * grid, metric and params are checked as grmhd_create checks them; the
+ * fluxes are FP64 whatever params->precision says (fields the flux stage
+ * does not read are ignored).
  * Every intermediate (metric at centres and faces, EMFs, signal-speed
  * maxima) lives in one file-scope device array of 64 MiB that every GPU
- * loading this library holds until exit; the call rejects a grid needing
- * more, i.e. 8 * (3 (n1+6)(n2+6)(n3+6) + 108 (n1+6)(n2+6)) bytes beyond
- * 64 MiB, with GRMHD_ERR_INVALID.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the
- * array and it keeps the last call's contents: calls that overlap on the
- * GPU race and must be serialised. */
+ * loading this library holds until exit.  A grid needs 24 N + 936 A bytes
+ * of it plus at most 1 KiB of alignment, N = (n1+6)(n2+6)(n3+6) and
+ * A = (n1+6)(n2+6) (3 EMFs per zone; 117 doubles of geometry, connection
+ * and bound thresholds per (i, j)): cubes up to 123^3 fit, and a grid that
+ * does not is refused with GRMHD_ERR_INVALID.  The call makes no
+ * cudaMalloc, cudaFree or allocating library call.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it (behind a lock: calls may come from
+ * several threads); make that first call before any stream capture.  A
+ * call that meets a CUDA error forgets the address, so that after a device
+ * reset the next call looks it up again.  All calls share the array and it
+ * keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised. */
 int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *metric,
                          const grmhd_params *params, const double *P, double *F,
                          double *ctop, void *stream);
@@ -550,7 +589,8 @@ int grmhd_decomp_step(grmhd_decomp *dc, int nsteps, grmhd_stats *stats);
  * grmhd_step does, GRMHD_ERR_INVERSION / GRMHD_ERR_DT since the last check. */
 int grmhd_decomp_get_stats(grmhd_decomp *dc, grmhd_stats *stats, int check);
 
-/* Name of an error code. */
+/* Name of an error code (the error convention of this interface; the
+ * paper has no counterpart). */
 const char *grmhd_strerror(int code);
 
 #ifdef __cplusplus

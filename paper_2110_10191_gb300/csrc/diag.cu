@@ -6,7 +6,9 @@
 //          corner along d - the same over the 4 on the - side] / (4 dX_d)
 // over directions with more than one zone; corners between interior zones
 // only (a direction with one zone takes its single layer and the ghost copy
-// below it).
+// below it).  Also the step's reciprocal on an array (grmhd_rcp), so that
+// its accuracy can be checked on the device.
+#include "../../include/grmhd.h"
 #include "grmhd_dev.cuh"
 #include "grmhd_impl.h"
 #include "step_bodies.cuh"
@@ -56,3 +58,25 @@ void launch_divb(const StepArgs &A, const double *P, unsigned long long *out, cu
 }
 
 }  // namespace grmhd
+
+// ---------------------------------------------------------------------------
+// The step's reciprocal (rcp_nr) on an array, so that its accuracy can be
+// checked against IEEE division on the device.
+// ---------------------------------------------------------------------------
+namespace grmhd {
+
+__global__ void k_rcp(const double *__restrict__ x, double *__restrict__ out, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = rcp_nr(x[t]);
+}
+
+}  // namespace grmhd
+
+extern "C" int grmhd_rcp(const double *x, double *out, long long n, void *stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return GRMHD_ERR_INVALID;
+  if (n == 0) return GRMHD_OK;
+  const long long nb = (n + grmhd::BS - 1) / grmhd::BS;
+  if (nb >= (1ll << 31)) return GRMHD_ERR_INVALID;
+  grmhd::k_rcp<<<(unsigned)nb, grmhd::BS, 0, (cudaStream_t)stream>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}

@@ -18,10 +18,12 @@
 // host threads) race on it; serialise them.
 #include <cstddef>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/grmhd.h"
 #include "grmhd_dev.cuh"
 #include "grmhd_impl.h"
+#include "sim_impl.h"
 
 using namespace grmhd;
 
@@ -34,22 +36,46 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES]
 
 // Device address of g_noalloc_scratch per device, looked up once per device
 // (with that device current).  In host code the symbol itself is only a
-// host-side stand-in, never a device address.
+// host-side stand-in, never a device address.  The table is guarded by a
+// mutex: calls may come from several host threads.  An entry is dropped
+// when a call on its device meets a CUDA error, so that after a device
+// reset (which reloads the module, possibly at another address) the next
+// call looks the address up again.
 unsigned char *g_scratch_ptr[MAX_DEVICES];
+std::mutex g_scratch_mu;
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-int scratch_for_current_device(unsigned char **out) {
+int scratch_for_current_device(int *dev_out, unsigned char **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GRMHD_ERR_CUDA;
   if (dev < 0 || dev >= MAX_DEVICES) return GRMHD_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GRMHD_ERR_CUDA;
     g_scratch_ptr[dev] = (unsigned char *)p;
   }
+  *dev_out = dev;
   *out = g_scratch_ptr[dev];
   return GRMHD_OK;
+}
+
+void forget_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  g_scratch_ptr[dev] = nullptr;
+}
+
+// Byte offsets of the pieces carved from the scratch for a grid of
+// dimensions D: clock, geometry (3 locations), connection, bound
+// thresholds, EMFs; off[5] is the total need.
+void carve(const Dims &D, size_t off[6]) {
+  off[0] = 0;
+  off[1] = align_up(off[0] + sizeof(Clock));
+  off[2] = align_up(off[1] + sizeof(double) * NLOC * G_NCOMP * (size_t)D.n2d);
+  off[3] = align_up(off[2] + sizeof(double) * C_NCOMP * (size_t)D.n2d);
+  off[4] = align_up(off[3] + sizeof(double) * 2 * (size_t)D.n2d);
+  off[5] = align_up(off[4] + sizeof(double) * 3 * (size_t)D.ntot);
 }
 
 }  // namespace
@@ -57,40 +83,22 @@ int scratch_for_current_device(unsigned char **out) {
 extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *metric,
                                     const grmhd_params *params, const double *P, double *F,
                                     double *ctop, void *stream) {
-  if (!grid || !metric || !params || !P || !F) return GRMHD_ERR_INVALID;
+  if (!P || !F) return GRMHD_ERR_INVALID;
+  Dims D;
+  int rc = validate_problem(grid, metric, params, &D);  // the checks of grmhd_create
+  if (rc != GRMHD_OK) return rc;
   const int n[3] = {grid->n1, grid->n2, grid->n3};
   const double xmin[3] = {grid->x1min, grid->x2min, grid->x3min};
   const double xmax[3] = {grid->x1max, grid->x2max, grid->x3max};
-  Dims D;
-  long long tot = 1;
-  for (int d = 0; d < 3; d++) {
-    if (n[d] < 1 || n[d] > (1 << 20) || !(xmax[d] > xmin[d])) return GRMHD_ERR_INVALID;
-    D.n[d] = n[d];
-    D.s[d] = n[d] + 2 * NG;
-    tot *= D.s[d];
-  }
-  if (tot >= (1ll << 31)) return GRMHD_ERR_INVALID;
-  D.ntot = tot;
-  D.n2d = (long long)D.s[0] * D.s[1];
-  if (metric->kind != GRMHD_METRIC_MINKOWSKI && metric->kind != GRMHD_METRIC_MKS_KERR)
-    return GRMHD_ERR_INVALID;
-  if (params->recon != GRMHD_RECON_MC && params->recon != GRMHD_RECON_WENO5) return GRMHD_ERR_INVALID;
-  if (!(params->gamma > 1.0)) return GRMHD_ERR_INVALID;
-  for (int d = 0; d < 3; d++)
-    for (int sd = 0; sd < 2; sd++)
-      if (params->bc[d][sd] < 0 || params->bc[d][sd] > 3) return GRMHD_ERR_INVALID;
+  size_t off[6];
+  carve(D, off);
+  if (off[5] > NOALLOC_SCRATCH_BYTES) return GRMHD_ERR_INVALID;  // grid too large for the scratch
+  const size_t off_clk = off[0], off_geom = off[1], off_conn = off[2], off_floors = off[3],
+               off_emf = off[4];
 
-  // carve the scratch: clock, geometry (3 locations), connection, floors, EMFs
-  const size_t off_clk = 0;
-  const size_t off_geom = align_up(off_clk + sizeof(Clock));
-  const size_t off_conn = align_up(off_geom + sizeof(double) * NLOC * G_NCOMP * (size_t)D.n2d);
-  const size_t off_floors = align_up(off_conn + sizeof(double) * C_NCOMP * (size_t)D.n2d);
-  const size_t off_emf = align_up(off_floors + sizeof(double) * 2 * (size_t)D.n2d);
-  const size_t need = align_up(off_emf + sizeof(double) * 3 * (size_t)D.ntot);
-  if (need > NOALLOC_SCRATCH_BYTES) return GRMHD_ERR_INVALID;  // grid too large for the scratch
-
+  int dev = 0;
   unsigned char *base = nullptr;
-  int rc = scratch_for_current_device(&base);
+  rc = scratch_for_current_device(&dev, &base);
   if (rc != GRMHD_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   Clock *clk = (Clock *)(base + off_clk);
@@ -132,19 +140,27 @@ extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *
 
   // faces outside the computed ranges read as zero, as in grmhd_get_fluxes
   const size_t fbytes = sizeof(double) * NV * (size_t)D.ntot;
-  if (cudaMemsetAsync(F, 0, 3 * fbytes, st) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaMemsetAsync(F, 0, 3 * fbytes, st) != cudaSuccess) {
+    forget_scratch(dev);
+    return GRMHD_ERR_CUDA;
+  }
   launch_geometry(G, st);
   launch_ctop_reset(A, st);
   double *Fd[3] = {F, F + NV * D.ntot, F + 2 * NV * D.ntot};
   launch_fluxes(A, P, Fd, st);
   launch_fix_ct(A, Fd, (double *)(base + off_emf), st);
-  if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) {
+    forget_scratch(dev);
+    return GRMHD_ERR_CUDA;
+  }
   if (ctop) {
     unsigned long long bits[3];
     const void *src = (const unsigned char *)clk + offsetof(Clock, ctop_bits);
-    if (cudaMemcpyAsync(bits, src, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cudaMemcpyAsync(bits, src, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      forget_scratch(dev);
       return GRMHD_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return GRMHD_ERR_CUDA;
+    }
     for (int d = 0; d < 3; d++) memcpy(&ctop[d], &bits[d], sizeof(double));
   }
   return GRMHD_OK;

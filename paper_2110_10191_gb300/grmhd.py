@@ -120,7 +120,7 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_decomp_set_prims", "grmhd_decomp_get_prims", "grmhd_decomp_step",
            "grmhd_decomp_get_stats", "grmhd_set_electrons", "grmhd_get_electrons",
            "grmhd_decomp_set_electrons", "grmhd_decomp_get_electrons",
-           "grmhd_server_submit_electrons",
+           "grmhd_server_submit_electrons", "grmhd_rcp",
            "grmhd_strerror"]
 
 
@@ -160,6 +160,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_fluxes_noalloc.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params), vp,
                                            vp, vp, vp]
         L.grmhd_profile.argtypes = [vp, i]
+        L.grmhd_rcp.argtypes = [vp, vp, ctypes.c_longlong, vp]
         L.grmhd_get_profile.argtypes = [vp, P(grmhd_profile_data), i]
         L.grmhd_fp64_peak.argtypes = [ctypes.c_longlong, P(d)]
         L.grmhd_batch_create.argtypes = [P(vp), i, P(vp)]
@@ -269,6 +270,20 @@ def fluxes_noalloc(problem, P, F, stream=None):
                                        ct.ctypes.data, ctypes.c_void_p(stream or 0)),
            "grmhd_fluxes_noalloc")
     return ct
+
+
+def rcp(x, out, stream=None):
+    """The step's reciprocal of every element of the device tensor x into
+    out (float64, same size; see grmhd_rcp in include/grmhd.h)."""
+    xp, xdev = _ptr(x)
+    op, odev = _ptr(out)
+    if not (xdev and odev):
+        raise ValueError("x and out must be device tensors")
+    if x.numel() != out.numel():
+        raise ValueError("x and out differ in size")
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load().grmhd_rcp(xp, op, int(x.numel()), ctypes.c_void_p(stream or 0)), "grmhd_rcp")
 
 
 class Sim:

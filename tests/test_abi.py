@@ -57,3 +57,21 @@ def test_buffers_must_be_contiguous_float64():
     with pytest.raises(ValueError):
         grmhd._ptr(torch.zeros(3, dtype=torch.float32))
     assert grmhd._ptr(torch.zeros(3, dtype=torch.float64))[1] == 0
+
+
+def test_fluxes_noalloc_checks_arguments_as_create_does():
+    """The allocation-free flux stage refuses, before any CUDA call, what
+    grmhd_create refuses: a Kerr spin |a| >= 1, an unpaired periodic side,
+    outflow off X1 (the pointers are never read on these paths)."""
+    import dataclasses
+    from paper_2110_10191_gb300 import grmhd, problems as pb
+    L = grmhd.load()
+    dummy = ctypes.c_void_p(256)
+    cases = [dataclasses.replace(pb.fm_torus(8, 8, 4), a=1.0),
+             dataclasses.replace(pb.linear_mode(8), bc=((0, 1), (0, 0), (0, 0))),
+             dataclasses.replace(pb.linear_mode(8), bc=((0, 0), (1, 1), (0, 0)))]
+    for pr in cases:
+        g, m, p = grmhd._structs(pr)
+        rc = L.grmhd_fluxes_noalloc(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p), dummy, dummy,
+                                    None, None)
+        assert rc == -1, pr.name

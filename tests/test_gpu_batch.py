@@ -140,7 +140,7 @@ def test_batch_oracle_parity(grmhd):
     b.step(1, sync=True)
     for s, o, pr in zip(sims, oracles, probs):
         o.step(1)
-        compare(s.get_prims(), o.get_prims(), what=pr.name)
+        compare(s.get_prims(), o.get_prims(), what=pr.name, ref=o)
     b.close()
 
 
@@ -329,7 +329,7 @@ def test_full_batch_oracle_parity(grmhd):
     assert b.info()["tuned"] == 1 and b.info()["graph"] == 1
     for s, o, pr in zip(sims, oracles, probs):
         o.step(1)
-        compare(s.get_prims(), o.get_prims(), what=pr.name)
+        compare(s.get_prims(), o.get_prims(), what=pr.name, ref=o)
         o.close()
     b.close()
     for s in sims:

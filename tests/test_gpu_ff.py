@@ -55,7 +55,7 @@ def test_ff_step_parity_torus(grmhd, shape, recon):
     o, s = _pair(pr, grmhd)
     o.step(1)
     s.step(1)
-    compare(s.get_prims(), o.get_prims(), tol_norm=TOL_FF, what="ff %s" % (shape,))
+    compare(s.get_prims(), o.get_prims(), tol=TOL_FF, what="ff %s" % (shape,), rule="group")
     pfo, _ = o.flags()
     pfg, _ = s.flags()
     assert np.array_equal(pfg, pfo)
@@ -72,7 +72,7 @@ def test_ff_step_parity_flat(grmhd, prob):
     o, s = _pair(pr, grmhd)
     o.step(n)
     s.step(n)
-    compare(s.get_prims(), o.get_prims(), tol_norm=TOL_FF, what="ff " + prob)
+    compare(s.get_prims(), o.get_prims(), tol=TOL_FF, what="ff " + prob, rule="group")
 
 
 @pytest.mark.parametrize("recon", [pb.RECON_MC, pb.RECON_WENO5])
@@ -152,4 +152,4 @@ def test_ff_full_size_torus_vs_fp64(grmhd):
         s.step(1)
         out.append(s.get_prims())
         s.close()
-    compare(out[1], out[0], tol_norm=TOL_FF, what="ff 128^3")
+    compare(out[1], out[0], tol=TOL_FF, what="ff 128^3", rule="group")

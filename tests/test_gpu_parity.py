@@ -1,15 +1,27 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerance.  FP64 rounding (1.1e-16) through the step's ~12k operations per
-zone-cycle, with condition growth of at most rho/u ~ 1e3 in the energy
-recovery, stays far below 1e-12; the measured differences are <= 4e-14.
-After one full predictor-corrector step in FP64, for each primitive group -- rho; u;
-utilde^1..3; B^1..3 -- the largest zone difference is <= 1e-12 of the
-group's scale, and every zone agrees to 1e-9 relative (plus that floor).
-The group scale is the group's largest magnitude, except that velocities
-are measured in units of c (scale max(max|utilde|, 1)): the update adds flux
-differences of O(p) quantities, so a velocity carries an absolute rounding
-error of order machine epsilon whatever its own size.
+Tolerance.  After one full predictor-corrector step in FP64 every zone is
+held to 1e-12 relative, per primitive (compare(), rule "zone"):
+  rho  |a - b| <= 1e-12 max(|b|, 1e-12 max|b|);
+  u    the same in every zone where that is coarser than the rounding the
+       energy variable carries; in cold zones (u < 3.6e-3 rho) |a - b| <=
+       32 eps rho: the energy density and its face fluxes are differences
+       of O(rho) terms (rest mass), so two FP64 implementations' u differ
+       by a few eps rho however small u is (measured: <= 13 eps rho);
+  B^i  |a - b| sqrt(g_ii) <= 1e-12 of the field strength sqrt(g_ij B^i
+       B^j) over the zone's domain of dependence of one step (zones within
+       6): a component is built from EMF differences of the reconstructed
+       states around it, so it carries rounding of that field strength even
+       where it crosses zero or sits in a field-free zone beside a
+       magnetised one;
+  utilde^i  |a - b| <= 1e-12 max(max|utilde|, 1) (units of c: the update
+       adds flux differences of O(p) quantities, so a velocity carries an
+       absolute rounding of order eps whatever its own size).
+FP64 rounding (1.1e-16) through the step's ~12k operations per zone-cycle
+stays far below these bars: measured <= 4.4e-13 (rho), 3.1e-13 (u, warm
+zones), 5.4e-16 (B), 5.3e-15 (utilde).  Reduced-precision modes and
+several-step runs use rule "group" (each variable against its group's
+largest magnitude).
 
 Both sides take the same decisions (MC/minmod branches, Newton stopping,
 bounds, failures) in FP64; the differences are rounding (FMA contraction on
@@ -21,7 +33,9 @@ oracle's, loaded through grmhd_set_geometry), the GPU's own geometry is
 compared with the oracle's separately, and a step on the GPU's own geometry
 is held to 1e-9.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -32,8 +46,19 @@ from paper_2110_10191_gb300 import problems as pb
 pytestmark = pytest.mark.gpu
 
 GROUPS = [(0,), (1,), (2, 3, 4), (5, 6, 7)]
-TOL_NORM = 1e-12
-TOL_ZONE = 1e-9
+NAMES = ["rho", "u", "u1", "u2", "u3", "B1", "B2", "B3"]
+TOL = 1e-12          # the one-step FP64 bar
+ZONE_FLOOR = 1e-12   # denominator floor, as a fraction of the largest magnitude over zones
+EPS = 2.0 ** -53     # FP64 unit roundoff
+# The energy variable's rest-mass cancellation: each side forms the energy
+# density and the six face fluxes of energy (with the Lax-Friedrichs term
+# c U) from pairs of O(rho) terms (T^d_t + rho u^d), each rounding to about
+# 2 eps rho, so two implementations' u may differ by up to 2 x 8 x 2 eps rho
+# whatever u is.
+U_REST_MASS = 32 * EPS
+# One full step reads the zones within 3 of a zone per stage: its domain of
+# dependence is the cube of zones within 6.
+REACH = 6
 
 
 @pytest.fixture(scope="module")
@@ -52,20 +77,123 @@ def group_scales(b):
     return sc
 
 
-def compare(a, b, tol_norm=TOL_NORM, tol_zone=TOL_ZONE, what=""):
-    """Group-scaled and zone-wise comparison of primitive arrays [8,...]."""
-    report = {}
-    for grp, scale in zip(GROUPS, group_scales(b)):
+def zone_rel(a, b):
+    """|a - b| / max(|b|, 1e-12 max|b|) per zone (zero where both vanish)."""
+    m = np.abs(b).max()
+    if m == 0.0:
+        return np.where(a == b, 0.0, np.inf)
+    return np.abs(a - b) / np.maximum(np.abs(b), ZONE_FLOOR * m)
+
+
+def _report(what, rep):
+    """With GRMHD_PARITY_REPORT set to a path, append the measured figures of
+    one comparison as a JSON line (before any assertion), so that a run
+    records every comparison's figures, passing or not."""
+    path = os.environ.get("GRMHD_PARITY_REPORT")
+    if not path:
+        return
+    rec = {"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "what": what}
+    rec.update(rep)
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")
+
+
+def _spatial_metric(ref, shape):
+    """g_ij (i, j = 1..3) at the interior zone centres, broadcast to the
+    primitive shape [n3, n2, n1]; the identity without a reference."""
+    g = np.zeros((3, 3) + tuple(shape))
+    if ref is None:
+        for i in range(3):
+            g[i, i] = 1.0
+        return g
+    gc = ref.geom(0)[:16, 3:-3, 3:-3]
+    for i in range(3):
+        for j in range(3):
+            g[i, j] = gc[4 * (i + 1) + (j + 1)][None]
+    return g
+
+
+def _reach_max(x):
+    """The largest value of x over each zone's domain of dependence of one
+    step (the zones within REACH along every axis, clipped at the grid)."""
+    from scipy.ndimage import maximum_filter
+    return maximum_filter(x, size=2 * REACH + 1, mode="nearest")
+
+
+def compare(a, b, tol=TOL, what="", ref=None, rule="zone"):
+    """Primitive arrays a (CUDA path) against b (oracle), [8, n3, n2, n1].
+
+    rule="zone", the one-step FP64 bar, zone by zone:
+      rho:   |a - b| / max(|b|, 1e-12 max|b|) <= tol;
+      u:     the same, except in cold zones, where it is finer than the
+             rest-mass cancellation of the energy variable allows (32 eps
+             rho > 1e-12 u): there |a - b| <= 32 eps rho (U_REST_MASS),
+             scaled by tol / 1e-12;
+      B^i:   |a - b| sqrt(g_ii) <= tol max(|B|_reach, 1e-12 max|B|), with
+             |B| = sqrt(g_ij B^i B^j) the field strength and |B|_reach its
+             largest value over the zone's domain of dependence of one step:
+             the induction update forms each component from EMF differences
+             of b^i u^j - b^j u^i of reconstructed states, so a component
+             carries rounding of the field strength around it, whatever its
+             own size (it may cross zero, or sit in a field-free zone beside
+             a magnetised one);
+      utilde^i: |a - b| <= tol max(max|utilde|, 1) (units of c: the update
+             adds flux differences of O(p) quantities, so a velocity carries
+             an absolute rounding of order eps whatever its own size).
+    ref (the oracle holding b): its centre metric for |B| (identity without
+    it) and its last stage's bound flags, which split the figures into
+    bound-held zones and the others.  rule="group" (reduced precision,
+    several steps): every variable to tol times its group's largest
+    magnitude.  Returns {variable: largest measured figure}."""
+    shape = b.shape[1:]
+    held = None if ref is None else (ref.flags()[1] != 0)
+    scales = group_scales(b)
+    figs, classes, worst, extra = {}, {}, {}, {}
+    bad = []
+    if rule == "zone":
+        g = _spatial_metric(ref, shape)
+        Bv = b[5:8]
+        bmag = np.sqrt(np.maximum(np.einsum("i...,ij...,j...->...", Bv, g, Bv), 0.0))
+        bden = np.maximum(_reach_max(bmag), ZONE_FLOOR * bmag.max()) if bmag.max() > 0 else None
+        cold = U_REST_MASS * np.abs(b[0]) > TOL * np.abs(b[1])
+        extra["u_cold_zones"] = int(cold.sum())
+    for q, grp in enumerate(GROUPS):
         for v in grp:
             d = np.abs(a[v] - b[v])
-            if scale == 0.0:
-                assert d.max() == 0.0, (what, v)
-                continue
-            report[v] = d.max() / scale
-            assert d.max() <= tol_norm * scale, (what, v, d.max() / scale)
-            bad = d > tol_zone * np.abs(b[v]) + tol_norm * scale
-            assert not bad.any(), (what, v, int(bad.sum()))
-    return report
+            if rule == "zone" and v == 0:
+                r = zone_rel(a[v], b[v])
+            elif rule == "zone" and v == 1:
+                r = zone_rel(a[v], b[v])
+                extra["u_hot_max"] = float(r[~cold].max()) if (~cold).any() else 0.0
+                if cold.any():
+                    rc = d / (U_REST_MASS * (tol / TOL) * np.maximum(np.abs(b[0]), 1e-300)) * tol
+                    extra["u_cold_max_over_eps_rho"] = float((d / (EPS * np.abs(b[0])))[cold].max())
+                    extra["u_cold_max_rel"] = float(r[cold].max())
+                    r = np.where(cold, rc, r)
+            elif rule == "zone" and v >= 5:
+                if bden is None:
+                    r = np.where(a[v] == b[v], 0.0, np.inf)
+                else:
+                    r = d * np.sqrt(g[v - 5, v - 5]) / bden
+                    # the same against the zone's own field strength, for the record
+                    own = d * np.sqrt(g[v - 5, v - 5]) / np.maximum(bmag, ZONE_FLOOR * bmag.max())
+                    extra["%s_vs_own_field" % NAMES[v]] = float(own.max())
+            else:
+                r = d / scales[q] if scales[q] > 0 else np.where(a[v] == b[v], 0.0, np.inf)
+            figs[NAMES[v]] = float(r.max())
+            if held is not None:
+                classes[NAMES[v]] = {"bound_held": float(r[held].max()) if held.any() else 0.0,
+                                     "free": float(r[~held].max()) if (~held).any() else 0.0}
+            if r.max() > 0:
+                iz = np.unravel_index(int(np.argmax(r)), r.shape)
+                worst[NAMES[v]] = {"zone": [int(x) for x in iz], "b": float(b[v][iz]),
+                                   "rho": float(b[0][iz]), "u": float(b[1][iz])}
+            if not r.max() <= tol:
+                bad.append((NAMES[v], figs[NAMES[v]], int((r > tol).sum())))
+    _report(what, {"rule": rule, "tol": tol, "max": figs, "classes": classes, "worst": worst,
+                   "extra": extra})
+    assert not bad, (what, rule, tol, bad)
+    return figs
 
 
 def compare_fluxes(Fg, Fo, Ub_scale, tol=1e-12):
@@ -139,7 +267,7 @@ def test_step_parity_own_geometry(grmhd):
     o, s = _pair(pr, grmhd, same_geometry=False)
     o.step(1)
     s.step(1)
-    compare(s.get_prims(), o.get_prims(), tol_norm=1e-9, tol_zone=1e-7, what="own geometry")
+    compare(s.get_prims(), o.get_prims(), tol=1e-9, what="own geometry", ref=o)
 
 
 def test_ghost_fill_parity(grmhd):
@@ -173,7 +301,7 @@ def test_step_parity_linear_mode(grmhd):
     o, s = _pair(pr, grmhd)
     o.step(1)
     s.step(1)
-    rep = compare(s.get_prims(), o.get_prims(), what="mode")
+    rep = compare(s.get_prims(), o.get_prims(), what="mode", ref=o)
     assert s.stats()["t"] == pytest.approx(o.time()[0], rel=1e-14)
 
 
@@ -190,7 +318,7 @@ def test_linear_mode_full_period(grmhd):
     eg = np.abs(Pg - ex).mean(axis=(1, 2, 3)).sum()
     eo = np.abs(Po - ex).mean(axis=(1, 2, 3)).sum()
     assert eg == pytest.approx(eo, rel=1e-6)
-    compare(Pg, Po, tol_norm=1e-10, tol_zone=1e-6, what="mode period")
+    compare(Pg, Po, tol=1e-10, what="mode period", rule="group")
 
 
 @pytest.mark.parametrize("shape,recon", [((32, 32, 16), pb.RECON_WENO5),
@@ -204,8 +332,8 @@ def test_step_parity_torus(grmhd, shape, recon):
     o, s = _pair(pr, grmhd)
     o.step(1)
     st = s.step(1)
-    compare(s.get_prims(), o.get_prims(), what=str(shape))
     pfo, ffo = o.flags()
+    compare(s.get_prims(), o.get_prims(), what=str(shape), ref=o)
     pfg, ffg = s.flags()
     assert np.array_equal(pfg, pfo)
     mism = ffg != ffo
@@ -229,7 +357,7 @@ def test_bondi_fixed_boundary_parity(grmhd):
     s.set_prims(pr.info["P_ghost"])
     o.step(3)
     s.step(3)
-    compare(s.get_prims(), o.get_prims(), tol_norm=1e-11, what="bondi")
+    compare(s.get_prims(), o.get_prims(), tol=1e-11, what="bondi", ref=o)
     assert np.array_equal(s.get_prims(True)[:, :, :, :3], o.get_prims(True)[:, :, :, :3])
 
 
@@ -238,7 +366,7 @@ def test_predictor_parity(grmhd):
     o, s = _pair(pr, grmhd)
     o.predictor()
     s.predictor()
-    compare(s.get_prims(), o.get_prims(), what="predictor")
+    compare(s.get_prims(), o.get_prims(), what="predictor", ref=o)
 
 
 def test_orszag_tang_parity(grmhd):
@@ -246,7 +374,7 @@ def test_orszag_tang_parity(grmhd):
     o, s = _pair(pr, grmhd)
     o.step(2)
     s.step(2)
-    compare(s.get_prims(), o.get_prims(), tol_norm=1e-11, what="OT")
+    compare(s.get_prims(), o.get_prims(), tol=1e-11, what="OT", ref=o)
 
 
 def test_multi_step_torus_drift(grmhd):
@@ -267,7 +395,7 @@ def test_full_size_torus_one_step(grmhd):
     o, s = _pair(pr, grmhd)
     o.step(1)
     s.step(1)
-    compare(s.get_prims(), o.get_prims(), what="128^3")
+    compare(s.get_prims(), o.get_prims(), what="128^3", ref=o)
 
 
 def test_restart_bitwise_gpu(grmhd):

@@ -41,12 +41,28 @@ def test_fluxes_noalloc_matches_regular_path_twice():
         sim.close()
 
 
-def test_fluxes_noalloc_rejects_grid_beyond_scratch():
+def test_fluxes_noalloc_scratch_limit():
+    """The largest cube the fixed scratch holds (123^3: 24 N + 936 A bytes
+    plus alignment within 64 MiB) runs and matches the regular path; the
+    next one (124^3) and far larger grids are refused."""
     import torch
     from paper_2110_10191_gb300 import grmhd
-    pr = pb.linear_mode(8)
-    pr.n = (400, 400, 400)  # needs far more than the fixed scratch
+    pr = pb.fm_torus(123, 123, 123, recon=pb.RECON_WENO5)
+    sim = grmhd.Sim(pr)
+    sim.set_prims(pr.P)
+    Pg = torch.from_numpy(sim.get_prims(with_ghosts=True)).cuda()
+    F_ref, ct_ref = sim.fluxes()
+    sim.close()
+    F = torch.empty((3, 8) + tuple(Pg.shape[1:]), dtype=torch.float64, device="cuda")
+    ct = grmhd.fluxes_noalloc(pr, Pg, F)
+    torch.cuda.synchronize()
+    _check_close(F.cpu().numpy(), F_ref)
+    assert np.allclose(ct, ct_ref, rtol=1e-13, atol=0)
+    del F, Pg
     P = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(grmhd.GrmhdError) as e:
-        grmhd.fluxes_noalloc(pr, P, P)
-    assert e.value.code == -1
+    for n in ((124, 124, 124), (400, 400, 400)):
+        big = pb.linear_mode(8)
+        big.n = n
+        with pytest.raises(grmhd.GrmhdError) as e:
+            grmhd.fluxes_noalloc(big, P, P)
+        assert e.value.code == -1, n
