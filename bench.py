@@ -668,19 +668,43 @@ def workload_config(name, variant="none"):
     return cfg
 
 
-# FP64 peak from the unit counts and clock: 152 SMs, 2 DFMA per SM per clock
-# (ncu sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304
-# per GPU), 2 flops per DFMA, 2070 MHz maximum SM clock
-FP64_PEAK_DERIVED = 152 * 2 * 2 * 2070e6
+# FP64 peak from the nominal unit counts and clock: 152 SMs, 2 DFMA per SM
+# per clock (ncu sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained
+# = 304 per GPU), 2 flops per DFMA, 2070 MHz maximum SM clock
+FP64_PEAK_NOMINAL = 152 * 2 * 2 * 2070e6
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
 
 
-def build_roofline(prof, cpu, pr, zones, peak_fp64, config, variant="none"):
+def fp64_peak_sustained(rate_per_sm_clock, nsm=SM_COUNT, mhz=SM_MAX_MHZ):
+    """FP64 peak from the unit count and clock, with the FP64 issue rate per
+    SM per clock measured (grmhd_fp64_probe) instead of the nominal 2: nsm x
+    rate x 2 flops x the maximum SM clock."""
+    return nsm * rate_per_sm_clock * 2.0 * mhz * 1e6
+
+
+def fp64_issue_sweep(grmhd, iters=1 << 14):
+    """The FP64 issue rate per SM per clock (and the SM clock measured in
+    the kernel) for FMA with 1, 8 and 16 independent chains per thread on 1,
+    8 and 16 blocks per SM, and for add and multiply."""
+    out = []
+    for op, chains, bps in ((0, 8, 8), (0, 1, 1), (0, 1, 8), (0, 16, 16), (1, 8, 8), (2, 8, 8)):
+        r, mhz = grmhd.fp64_probe(op, chains, bps, iters)
+        out.append({"op": ("fma", "add", "mul")[op], "chains": chains, "blocks_per_sm": bps,
+                    "ops_per_sm_clock": r, "sm_mhz": mhz})
+    return out
+
+
+def build_roofline(prof, cpu, pr, zones, fp64, config, variant="none"):
     """Roofline of the FP64-bound kernel classes from the live per-class
     device times (prof: class -> (total ms, launches)), the counting
-    oracle's algorithmic flops (cpu) and the derived FP64 peak; the
-    measured DFMA probe (peak_fp64) is reported beside it.  Returns
-    (roofline of the dominant class, per-class figures, algorithmic flops
-    per zone-cycle of this grid)."""
+    oracle's algorithmic flops (cpu) and the FP64 peak fp64 = {"rate": FP64
+    instructions per SM per clock measured by the probe, "mhz": the SM clock
+    the probe measured}: the peak is the unit count (152 SMs) x that rate x
+    2 flops x the maximum SM clock; the nominal peak (2 per SM per clock) is
+    reported beside it.  Returns (roofline of the dominant class, per-class
+    figures, algorithmic flops per zone-cycle of this grid)."""
+    peak = fp64_peak_sustained(fp64["rate"])
     flops_zc = None
     if cpu is not None and variant == "none" and pr.precision == 0:
         # the oracle counts on a thin slab, whose extended-range faces weigh
@@ -722,8 +746,8 @@ def build_roofline(prof, cpu, pr, zones, peak_fp64, config, variant="none"):
             avg = ms_c / n_c
             kernels[cls] = {"kernel": label, "avg_launch_ms": avg, "launches": n_c,
                             "achieved_tflops": flops / (avg * 1e-3) / 1e12,
-                            "frac": flops / (avg * 1e-3) / FP64_PEAK_DERIVED,
-                            "frac_of_measured_probe": flops / (avg * 1e-3) / peak_fp64,
+                            "frac": flops / (avg * 1e-3) / peak,
+                            "frac_of_nominal": flops / (avg * 1e-3) / FP64_PEAK_NOMINAL,
                             "hbm_frac": nbytes / (avg * 1e-3) / hbm,
                             "algorithmic_bytes": nbytes,
                             "traffic": None if traffic is None else traffic.get(cls),
@@ -732,21 +756,25 @@ def build_roofline(prof, cpu, pr, zones, peak_fp64, config, variant="none"):
         if dom:
             kd = kernels[dom]
             roofline = {"bound": "alu", "kernel": kd["kernel"],
-                        "achieved": kd["achieved_tflops"], "peak": FP64_PEAK_DERIVED / 1e12,
+                        "achieved": kd["achieved_tflops"], "peak": peak / 1e12,
                         "unit": "TFLOP/s", "frac": kd["frac"],
-                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                        "measured_probe_peak": peak_fp64 / 1e12,
-                        "frac_of_measured_probe": kd["frac_of_measured_probe"],
-                        "measured_probe": "dependency-free DFMA kernel (grmhd_fp64_peak), this run",
+                        "peak_source": "derived: 152 SMs x %.3f FP64 instructions per SM per clock "
+                                       "(measured in this run by grmhd_fp64_probe, the same for any "
+                                       "number of chains, blocks and FP64 operation) x 2 flop x "
+                                       "2.07 GHz" % fp64["rate"],
+                        "peak_nominal": FP64_PEAK_NOMINAL / 1e12,
+                        "frac_of_nominal": kd["frac_of_nominal"],
+                        "nominal_source": "152 SMs x 2 DFMA/clk (ncu peak_sustained) x 2 flop x "
+                                          "2.07 GHz",
                         "work": "algorithmic FP64 flops of the oracle's counting build",
                         "avg_launch_ms": kd["avg_launch_ms"], "hbm_frac": kd["hbm_frac"],
                         "algorithmic_bytes": kd["algorithmic_bytes"], "traffic": kd["traffic"],
                         "fp64_pipe_ncu": kd["fp64_pipe_ncu"],
                         "note": "algorithmic flops are the counting oracle's (adds, multiplies, "
                                 "divisions and square roots counted as one each); the kernel spends "
-                                "several FP64 instructions on each division and square root, so its "
-                                "FP64 pipe (fp64_pipe_ncu, the busy fraction in the ncu capture) "
-                                "runs above frac",
+                                "several FP64 instructions on each division and square root, and a "
+                                "lone add or multiply takes an issue slot worth two flops, so a "
+                                "kernel whose FP64 pipe is saturated reads below 1",
                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                           "capture of one launch of %s on this workload"
                                           % kd["kernel"].split()[0]}
@@ -854,7 +882,8 @@ def main():
         e2e_s = reduce_max(e2e_s, world, "cuda")
         sim2.close()
 
-    peak_fp64 = grmhd.fp64_peak(1 << 16)
+    fp64_sweep = fp64_issue_sweep(grmhd)
+    fp64 = {"rate": fp64_sweep[0]["ops_per_sm_clock"], "mhz": fp64_sweep[0]["sm_mhz"]}
 
     extras = {}
     if not args.no_extras:
@@ -898,7 +927,7 @@ def main():
                 extras["mixed_vs_oracle"] = mixed_vs_oracle(grmhd, args.oracle_steps, stream)
 
     launches = sum(v[1] for v in prof.values())
-    roofline, kernels, flops_zc = build_roofline(prof, cpu, pr, zones, peak_fp64, args.config,
+    roofline, kernels, flops_zc = build_roofline(prof, cpu, pr, zones, fp64, args.config,
                                                  args.variant)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -919,12 +948,13 @@ def main():
             "cpu_baseline_all_cores": cpu_all,
             "algorithmic_fp64_flops_per_zone_cycle": flops_zc,
             "fp64_ceiling": None if flops_zc is None else {
-                "value": FP64_PEAK_DERIVED / flops_zc, "unit": UNIT,
-                "frac": value * flops_zc / FP64_PEAK_DERIVED,
-                "frac_of_measured_probe": value * flops_zc / peak_fp64,
-                "note": "derived FP64 peak / algorithmic FP64 flops per zone-cycle of this grid "
-                        "(the oracle's counts per face and per zone-stage, scaled to its faces and "
-                        "zones)"},
+                "value": fp64_peak_sustained(fp64["rate"]) / flops_zc, "unit": UNIT,
+                "frac": value * flops_zc / fp64_peak_sustained(fp64["rate"]),
+                "frac_of_nominal": value * flops_zc / FP64_PEAK_NOMINAL,
+                "note": "FP64 peak (measured issue rate) / algorithmic FP64 flops per zone-cycle "
+                        "of this grid (the oracle's counts per face and per zone-stage, scaled to "
+                        "its faces and zones)"},
+            "fp64_issue_rate": fp64_sweep,
             "clocks": clk,
             "sim": {"t": st["t"], "steps": st["steps"], "inv_failures": st["inv_failures"],
                     "floor_hits": st["floor_hits"]}}

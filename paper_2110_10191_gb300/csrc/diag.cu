@@ -6,8 +6,9 @@
 //          corner along d - the same over the 4 on the - side] / (4 dX_d)
 // over directions with more than one zone; corners between interior zones
 // only (a direction with one zone takes its single layer and the ghost copy
-// below it).  Also the step's reciprocal on an array (grmhd_rcp), so that
-// its accuracy can be checked on the device.
+// below it).  Also the step's reciprocal, reciprocal square root and square
+// root on an array (grmhd_arith), so that their accuracy can be checked on
+// the device.
 #include "../../include/grmhd.h"
 #include "grmhd_dev.cuh"
 #include "grmhd_impl.h"
@@ -60,23 +61,30 @@ void launch_divb(const StepArgs &A, const double *P, unsigned long long *out, cu
 }  // namespace grmhd
 
 // ---------------------------------------------------------------------------
-// The step's reciprocal (rcp_nr) on an array, so that its accuracy can be
-// checked against IEEE division on the device.
+// The step's reciprocal, reciprocal square root and square root (rcp_nr,
+// rsqrt_nr, sqrt_nr) on an array, so that their accuracy can be checked
+// against the IEEE operations on the device.
 // ---------------------------------------------------------------------------
 namespace grmhd {
 
-__global__ void k_rcp(const double *__restrict__ x, double *__restrict__ out, long long n) {
+template <int FN>
+__global__ void k_arith(const double *__restrict__ x, double *__restrict__ out, long long n) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < n) out[t] = rcp_nr(x[t]);
+  if (t >= n) return;
+  const double v = x[t];
+  out[t] = FN == 0 ? rcp_nr(v) : FN == 1 ? rsqrt_nr(v) : sqrt_nr(v);
 }
 
 }  // namespace grmhd
 
-extern "C" int grmhd_rcp(const double *x, double *out, long long n, void *stream) {
-  if (n < 0 || (n > 0 && (!x || !out))) return GRMHD_ERR_INVALID;
+extern "C" int grmhd_arith(int fn, const double *x, double *out, long long n, void *stream) {
+  if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !out))) return GRMHD_ERR_INVALID;
   if (n == 0) return GRMHD_OK;
   const long long nb = (n + grmhd::BS - 1) / grmhd::BS;
   if (nb >= (1ll << 31)) return GRMHD_ERR_INVALID;
-  grmhd::k_rcp<<<(unsigned)nb, grmhd::BS, 0, (cudaStream_t)stream>>>(x, out, n);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (fn == 0) grmhd::k_arith<0><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
+  if (fn == 1) grmhd::k_arith<1><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
+  if (fn == 2) grmhd::k_arith<2><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
   return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }

@@ -67,6 +67,27 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
+// Reciprocal square root without the IEEE sequence: the hardware
+// approximation (PTX rsqrt.approx.ftz.f64) refined by the binomial series
+// (1 - h)^(-1/2) = 1 + h/2 + 3h^2/8 + ... with h = 1 - x y^2, y the seed:
+// y <- y + y h (1/2 + 3h/8), which leaves about (5/16) h^3 of the seed's
+// relative error h before the final rounding (five FP64 instructions).
+// Within a few ulp of 1/sqrt(x) for normal positive x.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = fma(-(x * y), y, 1.0);
+  return fma(y * h, fma(0.375, h, 0.5), y);
+}
+
+// Square root of a positive normal x as x / sqrt(x) from rsqrt_nr (within a
+// few ulp); the callers send zero, negative and subnormal values to their
+// own branch.
+__device__ __forceinline__ double sqrt_nr(double x) { return x * rsqrt_nr(x); }
+
+// smallest positive normal double
+constexpr double DBL_NORMAL_MIN = 2.2250738585072014e-308;
+
 struct Dims {
   int n[3];   // interior zones
   int s[3];   // with ghosts
@@ -111,7 +132,7 @@ __device__ __forceinline__ void fluid_state(const double P[NV], const Geo &G, FS
   const double l3 = G.gcov[SY(1, 3)] * v1 + G.gcov[SY(2, 3)] * v2 + G.gcov[SY(3, 3)] * v3;
   // gamma and 1/gamma from one reciprocal square root
   const double g2 = 1.0 + (l1 * v1 + l2 * v2 + l3 * v3);
-  const double rg = rsqrt(g2);
+  const double rg = rsqrt_nr(g2);
   const double gam = g2 * rg;
   const double ga = gam * G.alpha;
   s.ucon[0] = gam * G.ialpha;
@@ -215,7 +236,7 @@ __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, c
   const double qb = -2.0 * (AuBu - (AB + AuBu) * cms2);
   const double qc = Au * Au - (Asq + Au * Au) * cms2;
   double disc = qb * qb - 4.0 * qa * qc;
-  disc = (disc > 0.0) ? sqrt(disc) : 0.0;
+  disc = (disc >= DBL_NORMAL_MIN) ? sqrt_nr(disc) : 0.0;  // a subnormal root is negligible
   const double i2a = 0.5 * rcp_nr(qa);
   const double v1 = (-qb + disc) * i2a;
   const double v2 = (-qb - disc) * i2a;
@@ -256,25 +277,27 @@ __device__ __forceinline__ double weno5_hi(double a, double b, double c, double 
 
 // Both WENO5 face values of the middle zone of a..e (zones c-2..c+2), written
 // in the stencil's first differences (dm2 = b-a, dm1 = c-b, dp1 = d-c,
-// dp2 = e-d) and second differences (D0 = a-2b+c, D1 = b-2c+d, D2 = c-2d+e):
-//   4 beta_0 = (13/3) D0^2 + (D0 + 2 dm1)^2
-//   4 beta_1 = (13/3) D1^2 + (dm1 + dp1)^2
-//   4 beta_2 = (13/3) D2^2 + (D2 - 2 dp1)^2
-//   6 (q_0 - c) = 2 D0 + 3 dm1,  6 (q_1 - c) = dm1 + 2 dp1,  6 (q_2 - c) = 3 dp1 - D2
-// (q_k the candidate values at the high face), the low face by mirroring.
-// The weights d_k/(eps + beta_k)^2 are taken over the common denominator
-// q0 q1 q2 of the squared (4 eps + 4 beta_k) and scaled by 10, which
-// leaves their ratios unchanged (4 eps + 4 beta_k costs one multiply and two
-// FMAs), and one reciprocal serves both faces, with the 1/6 of the
-// candidate differences folded into it.  The terms pair up under the mirror
-// a <-> e, b <-> d, so a mirrored stencil gives the same two values swapped,
-// bit for bit.
+// dp2 = e-d), second differences (D0 = a-2b+c, D1 = b-2c+d, D2 = c-2d+e) and
+// s0 = D0 + 2 dm1, s1 = dm1 + dp1, s2 = D2 - 2 dp1:
+//   4 beta_k = (13/3) D_k^2 + s_k^2,
+// and, with q_k the candidate values at the high face,
+//   6 (q_0 - c) = A = 2 D0 + 3 dm1 = Cl + D0,   Cl = D0 + 3 dm1 = s0 + dm1,
+//   6 (q_1 - c) = B = dm1 + 2 dp1  = s1 + dp1,
+//   6 (q_2 - c) = C = 3 dp1 - D2   = dp1 - s2,
+// the low face's by mirroring: Al = 2 D2 - 3 dp1 = D2 - C, Bl = dp1 + 2 dm1
+// = s1 + dm1, Cl.  The weights d_k/(eps + beta_k)^2 are taken over the
+// common denominator q0 q1 q2 of the squared (4 eps + 4 beta_k) and scaled
+// by 10, which leaves their ratios unchanged (4 eps + 4 beta_k costs one
+// multiply and two FMAs), and one reciprocal serves both faces, with the
+// 1/6 of the candidate differences folded into it.  The terms pair up under
+// the mirror a <-> e, b <-> d (A <-> Al, B <-> -Bl, C <-> -Cl), so a
+// mirrored stencil gives the same two values swapped, bit for bit.
 __device__ __forceinline__ void weno5_pair(double a, double b, double c, double d, double e,
                                            double &lo, double &hi) {
   const double eps4 = 4.0e-26, c13 = 13.0 / 3.0;
   const double dm2 = b - a, dm1 = c - b, dp1 = d - c, dp2 = e - d;
   const double D0 = dm1 - dm2, D1 = dp1 - dm1, D2 = dp2 - dp1;
-  const double s0 = D0 + 2.0 * dm1, s1 = dm1 + dp1, s2 = D2 - 2.0 * dp1;
+  const double s0 = fma(2.0, dm1, D0), s1 = dm1 + dp1, s2 = fma(-2.0, dp1, D2);
   const double e0 = fma(c13 * D0, D0, fma(s0, s0, eps4));
   const double e1 = fma(c13 * D1, D1, fma(s1, s1, eps4));
   const double e2 = fma(c13 * D2, D2, fma(s2, s2, eps4));
@@ -282,16 +305,17 @@ __device__ __forceinline__ void weno5_pair(double a, double b, double c, double 
   // linear weights in the ratio 1 : 6 : 3 (only ratios enter)
   const double q12 = q1 * q2, q02 = 6.0 * (q0 * q2), q01 = q0 * q1;
   const double t01 = 3.0 * q01, t12 = 3.0 * q12;
-  const double m3 = 3.0 * dm1, p3 = 3.0 * dp1;
+  const double Cl = s0 + dm1, A = Cl + D0, B = s1 + dp1, C = dp1 - s2;
+  const double Al = D2 - C, Bl = s1 + dm1;
   // high face: weights q12, 6 q02, 3 q01
-  const double nh = q12 * (2.0 * D0 + m3) + q02 * (dm1 + 2.0 * dp1) + t01 * (p3 - D2);
-  const double H = q12 + q02 + t01;
+  const double nh = fma(t01, C, fma(q02, B, q12 * A));
+  const double H = (q12 + q02) + t01;
   // low face (mirrored stencil): weights q01, 6 q02, 3 q12
-  const double nl = q01 * (2.0 * D2 - p3) - q02 * (dp1 + 2.0 * dm1) - t12 * (m3 + D0);
-  const double L = q01 + q02 + t12;
+  const double nl = fma(-t12, Cl, fma(-q02, Bl, q01 * Al));
+  const double L = (q01 + q02) + t12;
   const double r = rcp_nr(H * L) * (1.0 / 6.0);
-  hi = c + nh * (L * r);
-  lo = c + nl * (H * r);
+  hi = fma(nh, L * r, c);
+  lo = fma(nl, H * r, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,7 +395,7 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
     }
     if (vsq < 0.0) vsq = 0.0;
     const double omv = 1.0 - vsq;
-    const double rsq = rsqrt(omv);  // 1/sqrt(1 - v^2)
+    const double rsq = rsqrt_nr(omv);  // 1/sqrt(1 - v^2)
     const double sq = omv * rsq;
     const double wmr = Wp * omv - D * vsq * sq * rcp_nr(1.0 + sq);
     const double iW = BW * ix;
@@ -408,7 +432,7 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
   if (!(vsq < 1.0) || invalid) return PF_VSQ;
   if (vsq < 0.0) vsq = 0.0;
   const double omv = 1.0 - vsq;
-  const double rsq = rsqrt(omv);  // Lorentz factor
+  const double rsq = rsqrt_nr(omv);  // Lorentz factor
   const double sq = omv * rsq;
   const double rho = D * sq;
   const double uu = (Wp * omv - D * vsq * sq * rcp_nr(1.0 + sq)) * igam;

@@ -5,9 +5,23 @@
 // stay FP64.  Same formulas as grmhd_dev.cuh.
 #pragma once
 
+#include <cfloat>
+
 #include "grmhd_dev.cuh"
 
 namespace grmhd {
+
+// FP32 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32,
+// within one ulp of 1/x), one instruction against the IEEE sequence of
+// __frcp_rn; the FP32 flux stage rounds at that level anyway.  Every
+// caller passes a normal, non-zero argument (the WENO variation is at least
+// 1e-30, the smoothness indicators at least their epsilon, the signal-speed
+// denominators are sums of positive terms).
+__device__ __forceinline__ float rcp_f(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 struct GeoF {
   float gcov[10], gcon[10], gdet, alpha, ialpha, omalpha;
@@ -43,7 +57,7 @@ __device__ __forceinline__ void fluid_state_f(const float P[NV], const GeoF &G, 
   const float gam = g2 * rg;
   const float ga = gam * G.alpha;
   const float sh = G.gcov[SY(0, 1)] * v1 + G.gcov[SY(0, 2)] * v2 + G.gcov[SY(0, 3)] * v3;
-  s.opu_t = G.omalpha - G.alpha * qsq * __frcp_rn(1.0f + gam) + sh;
+  s.opu_t = G.omalpha - G.alpha * qsq * rcp_f(1.0f + gam) + sh;
   s.ucon[0] = gam * G.ialpha;
   s.ucon[1] = v1 - ga * G.gcon[SY(0, 1)];
   s.ucon[2] = v2 - ga * G.gcon[SY(0, 2)];
@@ -98,7 +112,7 @@ __device__ __forceinline__ void mhd_vchar_f(const float P[NV], const FStateF &s,
                                             float gam, int dir, float &vmax, float &vmin) {
   const float ef = P[RHO] + gam * P[UU];
   const float ee = s.bsq + ef;
-  const float iee = __frcp_rn(ef * ee);
+  const float iee = rcp_f(fmaxf(ef * ee, FLT_MIN));  // (densities below ~1e-19 stay normal)
   const float va2 = s.bsq * ef * iee;
   const float cs2 = gam * (gam - 1.0f) * P[UU] * ee * iee;
   const float cms2 = cs2 + va2 - cs2 * va2;
@@ -113,7 +127,7 @@ __device__ __forceinline__ void mhd_vchar_f(const float P[NV], const FStateF &s,
   const float qc = Au * Au - (Asq + Au * Au) * cms2;
   float disc = qb * qb - 4.0f * qa * qc;
   disc = (disc > 0.0f) ? sqrtf(disc) : 0.0f;
-  const float i2a = 0.5f * __frcp_rn(qa);
+  const float i2a = 0.5f * rcp_f(qa);
   const float v1 = (-qb + disc) * i2a;
   const float v2 = (-qb - disc) * i2a;
   vmax = fmaxf(v1, v2);
@@ -146,7 +160,7 @@ __device__ __forceinline__ void weno5_pair_f(float a, float b, float c, float d,
     hi = c;
     return;
   }
-  const float is = __frcp_rn(sc);
+  const float is = rcp_f(sc);
   dm2 *= is;
   dm1 *= is;
   dp1 *= is;
@@ -158,7 +172,7 @@ __device__ __forceinline__ void weno5_pair_f(float a, float b, float c, float d,
   const float e1 = eps + (13.0f * D1 * D1 + 3.0f * s1 * s1);
   const float e2 = eps + (13.0f * D2 * D2 + 3.0f * s2 * s2);
   const float emin = fminf(fminf(e0, e1), e2);
-  const float r0 = emin * __frcp_rn(e0), r1 = emin * __frcp_rn(e1), r2 = emin * __frcp_rn(e2);
+  const float r0 = emin * rcp_f(e0), r1 = emin * rcp_f(e1), r2 = emin * rcp_f(e2);
   const float w0 = r0 * r0, w1 = 6.0f * (r1 * r1), w2 = r2 * r2;
   const float m3 = 3.0f * dm1, p3 = 3.0f * dp1;
   // high face: linear weights 1 : 6 : 3 on stencils 0, 1, 2
@@ -167,8 +181,8 @@ __device__ __forceinline__ void weno5_pair_f(float a, float b, float c, float d,
   // low face: the mirrored stencils (2, 1, 0) with the same linear weights
   const float nl = w2 * (2.0f * D2 - p3) - w1 * (dp1 + 2.0f * dm1) - 3.0f * w0 * (m3 + D0);
   const float L = 6.0f * (w2 + w1 + 3.0f * w0);
-  hi = c + sc * (nh * __frcp_rn(H));
-  lo = c + sc * (nl * __frcp_rn(L));
+  hi = c + sc * (nh * rcp_f(H));
+  lo = c + sc * (nl * rcp_f(L));
 }
 
 }  // namespace grmhd

@@ -120,7 +120,7 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_decomp_set_prims", "grmhd_decomp_get_prims", "grmhd_decomp_step",
            "grmhd_decomp_get_stats", "grmhd_set_electrons", "grmhd_get_electrons",
            "grmhd_decomp_set_electrons", "grmhd_decomp_get_electrons",
-           "grmhd_server_submit_electrons", "grmhd_rcp",
+           "grmhd_server_submit_electrons", "grmhd_arith", "grmhd_fp64_probe",
            "grmhd_strerror"]
 
 
@@ -160,7 +160,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_fluxes_noalloc.argtypes = [P(grmhd_grid), P(grmhd_metric), P(grmhd_params), vp,
                                            vp, vp, vp]
         L.grmhd_profile.argtypes = [vp, i]
-        L.grmhd_rcp.argtypes = [vp, vp, ctypes.c_longlong, vp]
+        L.grmhd_arith.argtypes = [i, vp, vp, ctypes.c_longlong, vp]
+        L.grmhd_fp64_probe.argtypes = [i, i, i, ctypes.c_longlong, P(d), P(d)]
         L.grmhd_get_profile.argtypes = [vp, P(grmhd_profile_data), i]
         L.grmhd_fp64_peak.argtypes = [ctypes.c_longlong, P(d)]
         L.grmhd_batch_create.argtypes = [P(vp), i, P(vp)]
@@ -234,6 +235,17 @@ def fp64_peak(iters: int = 1 << 16) -> float:
     return out.value
 
 
+def fp64_probe(op: int = 0, chains: int = 8, blocks_per_sm: int = 8, iters: int = 1 << 14):
+    """(FP64 instructions per SM per clock cycle, SM MHz measured in the
+    kernel) of a loop of op (0 FMA, 1 add, 2 multiply) with `chains`
+    independent chains per thread on blocks_per_sm blocks of 128 threads
+    per SM."""
+    r, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(load().grmhd_fp64_probe(int(op), int(chains), int(blocks_per_sm), int(iters),
+                                   ctypes.byref(r), ctypes.byref(mhz)), "grmhd_fp64_probe")
+    return r.value, mhz.value
+
+
 def _structs(pr):
     g = grmhd_grid(int(pr.n[0]), int(pr.n[1]), int(pr.n[2]), pr.xmin[0], pr.xmax[0], pr.xmin[1],
                    pr.xmax[1], pr.xmin[2], pr.xmax[2])
@@ -272,9 +284,13 @@ def fluxes_noalloc(problem, P, F, stream=None):
     return ct
 
 
-def rcp(x, out, stream=None):
-    """The step's reciprocal of every element of the device tensor x into
-    out (float64, same size; see grmhd_rcp in include/grmhd.h)."""
+ARITH = {"rcp": 0, "rsqrt": 1, "sqrt": 2}
+
+
+def arith(fn, x, out, stream=None):
+    """The step's reciprocal ("rcp"), reciprocal square root ("rsqrt") or
+    square root ("sqrt") of every element of the device tensor x into out
+    (float64, same size; see grmhd_arith in include/grmhd.h)."""
     xp, xdev = _ptr(x)
     op, odev = _ptr(out)
     if not (xdev and odev):
@@ -283,7 +299,8 @@ def rcp(x, out, stream=None):
         raise ValueError("x and out differ in size")
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    _check(load().grmhd_rcp(xp, op, int(x.numel()), ctypes.c_void_p(stream or 0)), "grmhd_rcp")
+    _check(load().grmhd_arith(ARITH[fn], xp, op, int(x.numel()), ctypes.c_void_p(stream or 0)),
+           "grmhd_arith")
 
 
 class Sim:

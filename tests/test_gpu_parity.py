@@ -502,6 +502,22 @@ def test_fp64_peak_probe(grmhd):
     assert 1e11 < f < 1e14
 
 
+def test_fp64_issue_rate_probe(grmhd):
+    """The FP64 issue rate per SM per clock, with the clock measured in the
+    kernel: positive, at most the nominal 2 per SM per clock, and the same
+    (within 3%) with one chain per thread as with 8, and with one block per
+    SM as with 8."""
+    r8, mhz = grmhd.fp64_probe(0, 8, 8, 1 << 12)
+    r1, _ = grmhd.fp64_probe(0, 1, 8, 1 << 15)
+    rb, _ = grmhd.fp64_probe(0, 8, 1, 1 << 15)
+    assert abs(rb / r8 - 1.0) < 0.03
+    assert 300.0 < mhz < 4000.0
+    assert 0.5 < r8 <= 2.02 and 0.5 < r1 <= 2.02
+    assert abs(r1 / r8 - 1.0) < 0.03
+    with pytest.raises(grmhd.GrmhdError):
+        grmhd.fp64_probe(0, 3, 8, 16)
+
+
 def _divb_ref(P, gdet, dx, n):
     """Corner-centred divergence of sqrt(-g) B over the corners between
     interior zones, written out with numpy (the definition in grmhd.h)."""

@@ -1,12 +1,17 @@
-"""The reciprocal the step uses inside its arithmetic (WENO5 weights, signal
-speeds, the Newton iteration of the 1D_W inversion): the hardware
-approximation refined by one third-order step.  Against the IEEE quotient
-1/x computed on the same device, it must be within 2 ulp over the normal
-range it is specified for, on values spread log-uniformly over 1e-300 ..
-1e300 of both signs, on the magnitudes the WENO5 pair feeds it (products
-of two sums of squared smoothness indicators) and on exact powers of two.
-Outside [2^-1022, 2^1022] the approximation flushes (zero or subnormal
-x -> NaN, |x| > 2^1022 -> 0), as the header states."""
+"""The reciprocal, reciprocal square root and square root the step uses
+inside its arithmetic (WENO5 weights, fluid states, signal speeds, the
+Newton iteration of the 1D_W inversion): hardware approximations refined by
+one step of a series (the geometric series of 1/(1 - e) for the
+reciprocal, the binomial series of (1 - h)^(-1/2) for the reciprocal square
+root; the square root is x times the latter).  Against the IEEE results
+computed on the same device (torch's reciprocal, rsqrt and sqrt), each must
+be within 2 ulp over the normal range it is specified for: values spread
+log-uniformly over 1e-300 .. 1e300 (both signs for the reciprocal), the
+magnitudes the WENO5 pair feeds the reciprocal (products of two sums of
+squared smoothness indicators), 1 + q^2 and 1 - v^2 as the fluid state and
+the inversion form them, and exact powers of two.  Outside
+[2^-1022, 2^1022] the reciprocal flushes (zero or subnormal x -> NaN,
+|x| > 2^1022 -> 0), as the header states."""
 import numpy as np
 import pytest
 
@@ -47,27 +52,53 @@ def _weno_denominators(rng, n):
     return H * L
 
 
-def test_rcp_within_2_ulp_of_ieee_division(dev):
+def _run(dev, fn, xs):
     torch, grmhd = dev
+    x = torch.from_numpy(xs).cuda()
+    out = torch.empty_like(x)
+    grmhd.arith(fn, x, out)
+    ref = {"rcp": torch.reciprocal, "rsqrt": torch.rsqrt, "sqrt": torch.sqrt}[fn](x)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), ref.cpu().numpy()
+
+
+def _normal(xs):
+    return xs[np.isfinite(xs) & (np.abs(xs) >= 2.0 ** -1022) & (np.abs(xs) <= 2.0 ** 1022)]
+
+
+def test_rcp_within_2_ulp_of_ieee_division(dev):
     rng = np.random.default_rng(7)
     n = 1 << 20
     mag = 10.0 ** rng.uniform(-300, 300, n)
     sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
     pows = 2.0 ** np.arange(-1022, 1023, dtype=np.float64)
-    xs = np.concatenate([mag * sign, _weno_denominators(rng, n // 4), pows, -pows,
-                         np.nextafter(pows, 0.0)[1:], 1.0 + np.arange(1, 4096) * 2.0 ** -52])
-    xs = xs[np.isfinite(xs) & (np.abs(xs) >= 2.0 ** -1022) & (np.abs(xs) <= 2.0 ** 1022)]
-    x = torch.from_numpy(xs).cuda()
-    out = torch.empty_like(x)
-    grmhd.rcp(x, out)
-    ref = torch.reciprocal(x)  # IEEE division on the device
-    torch.cuda.synchronize()
-    a, b = out.cpu().numpy(), ref.cpu().numpy()
+    xs = _normal(np.concatenate([mag * sign, _weno_denominators(rng, n // 4), pows, -pows,
+                                 np.nextafter(pows, 0.0)[1:], 1.0 + np.arange(1, 4096) * 2.0 ** -52]))
+    a, b = _run(dev, "rcp", xs)
     assert np.all(np.sign(a) == np.sign(b))
     u = _ulps(a, b)
     assert u.max() <= 2, (int(u.max()), float(xs[int(np.argmax(u))]))
     # and most are exact: the third-order step leaves ~2^-60 before rounding
     assert (u == 0).mean() > 0.9
+
+
+@pytest.mark.parametrize("fn", ["rsqrt", "sqrt"])
+def test_rsqrt_and_sqrt_within_2_ulp_of_ieee(dev, fn):
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    mag = 10.0 ** rng.uniform(-300, 300, n)
+    pows = 2.0 ** np.arange(-1022, 1023, dtype=np.float64)
+    # 1 + q^2 of the fluid state (q up to a Lorentz factor of ~1e3) and
+    # 1 - v^2 of the inversion (down to its limit 1e-10)
+    lorentz = 1.0 + (10.0 ** rng.uniform(-12, 3, n // 4)) ** 2
+    omv = 1.0 - (1.0 - 10.0 ** rng.uniform(-10, 0, n // 4))
+    xs = _normal(np.concatenate([mag, _weno_denominators(rng, n // 8), lorentz, omv, pows,
+                                 np.nextafter(pows, np.inf)[:-1]]))
+    a, b = _run(dev, fn, xs)
+    assert np.all(a > 0)
+    u = _ulps(a, b)
+    assert u.max() <= 2, (int(u.max()), float(xs[int(np.argmax(u))]))
+    assert (u == 0).mean() > 0.5
 
 
 def test_rcp_outside_the_normal_range(dev):
@@ -76,11 +107,11 @@ def test_rcp_outside_the_normal_range(dev):
     2^1022 (a subnormal quotient) gives a zero of x's sign."""
     torch, grmhd = dev
     xs = np.array([2.0 ** -1074, -2.0 ** -1040, 0.0, 2.0 ** 1022 * 1.5, -(2.0 ** 1023)])
-    x = torch.from_numpy(xs).cuda()
-    out = torch.empty_like(x)
-    grmhd.rcp(x, out)
-    torch.cuda.synchronize()
-    a = out.cpu().numpy()
+    a, _ = _run(dev, "rcp", xs)
     assert np.all(np.isnan(a[:3]))
     assert a[3] == 0.0 and not np.signbit(a[3])
     assert a[4] == 0.0 and np.signbit(a[4])
+    with pytest.raises(grmhd.GrmhdError):
+        x = torch.zeros(4, dtype=torch.float64, device="cuda")
+        grmhd.load()
+        grmhd._check(grmhd.load().grmhd_arith(3, x.data_ptr(), x.data_ptr(), 4, None), "grmhd_arith")
