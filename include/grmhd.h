@@ -272,14 +272,16 @@ int grmhd_get_geometry(grmhd_sim *sim, int loc, double *out);
 int grmhd_set_geometry(grmhd_sim *sim, int loc, const double *in);
 
 /* Kernel classes of the step, for grmhd_get_profile(). */
-#define GRMHD_K_FLUX 0    /* LLF face fluxes from reconstructed states (3 launches a stage) */
+#define GRMHD_K_FLUX 0    /* LLF face fluxes from reconstructed states (3 launches a stage;
+                             in the FP32-flux modes with the reconstruction fused in) */
 #define GRMHD_K_DT 1      /* CFL time step */
 #define GRMHD_K_CT 2      /* boundary flux fixes + flux-CT */
 #define GRMHD_K_UPDATE 3  /* conserved update + 1D_W inversion + bounds */
 #define GRMHD_K_FIXUP 4   /* fixup of failed zones */
 #define GRMHD_K_BOUNDS 5  /* ghost fill */
 #define GRMHD_K_OTHER 6   /* clock advance, signal-speed reset */
-#define GRMHD_K_RECON 7   /* MC / WENO5 reconstruction of face states (3 launches a stage) */
+#define GRMHD_K_RECON 7   /* MC / WENO5 reconstruction of face states (3 launches a stage;
+                             in the FP32-flux modes the FP32 copy of the stage input) */
 #define GRMHD_NKCLASS 8
 
 typedef struct {
@@ -323,17 +325,32 @@ int grmhd_autotune(grmhd_sim *sim, int trials, double *ms_before, double *ms_aft
  * the FP64-bound kernels. */
 int grmhd_fp64_peak(long long iters, double *flops);
 
-/* The reciprocal that the step uses inside its arithmetic (WENO5 weights,
- * signal speeds, the Newton iteration of the 1D_W inversion; the paper's
- * "Implementation Notes" name the inversion, the HARM method the rest): the
- * hardware approximation refined by one third-order step, within 2 ulp of
- * the IEEE quotient 1/x for |x| in [2^-1022, 2^1022].  Outside that range
- * the approximation flushes subnormal inputs and results to zero: a zero or
- * subnormal x gives NaN, |x| > 2^1022 gives a zero of x's sign (the IEEE
- * results there are infinite, huge or subnormal).  x, out:
- * n device doubles (out[i] = rcp(x[i])), enqueued on stream; for
- * verification of the step's arithmetic. */
-int grmhd_rcp(const double *x, double *out, long long n, void *stream);
+/* The FP64 issue rate of the current device: thread-level FP64 instructions
+ * (op 0: fused multiply-add, 1: add, 2: multiply) per SM per SM clock
+ * cycle, from a loop of `chains` (1, 2, 4, 8 or 16) independent dependent
+ * chains per thread on blocks_per_sm (1..16) blocks of 128 threads per SM,
+ * about `iters` iterations per thread; the SM clock (*sm_mhz) is measured
+ * inside the kernel (SM cycle counter against the global nanosecond
+ * timer) and the time by CUDA events.  The FP64-bound kernels of the step
+ * are reported against the rate it finds. */
+int grmhd_fp64_probe(int op, int chains, int blocks_per_sm, long long iters,
+                     double *ops_per_sm_clock, double *sm_mhz);
+
+/* The reciprocal, reciprocal square root and square root that the step
+ * uses inside its arithmetic (WENO5 weights, fluid states, signal speeds,
+ * the Newton iteration of the 1D_W inversion; the paper's "Implementation
+ * Notes" name the inversion, the HARM method the rest), on n device doubles
+ * x into out, enqueued on stream; for verification of the step's
+ * arithmetic.  fn 0: 1/x, the hardware approximation refined by one
+ * third-order step of the geometric series; fn 1: 1/sqrt(x), the hardware
+ * approximation refined by the binomial series to second order; fn 2:
+ * sqrt(x) = x times fn 1.  Each is within 2 ulp of the IEEE result for
+ * normal x in [2^-1022, 2^1022] (positive for fn 1, 2).  Outside that range
+ * the approximations flush subnormal inputs and results to zero: for fn 0 a
+ * zero or subnormal x gives NaN and |x| > 2^1022 a zero of x's sign; the
+ * step sends zero and subnormal arguments of fn 2 to a branch of its own.
+ * GRMHD_ERR_INVALID: fn outside 0..2, n < 0, NULL pointers with n > 0. */
+int grmhd_arith(int fn, const double *x, double *out, long long n, void *stream);
 
 /* Face-flux stage without any device allocation (no counterpart in the
  * paper: it exists for callers of this library that cannot allocate).
