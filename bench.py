@@ -640,6 +640,47 @@ def mixed_vs_oracle(grmhd, steps, stream):
     return out
 
 
+def long_run_health(grmhd, cycles, stream):
+    """Health of long runs of the 128^3 torus: `cycles` cycles in each
+    precision mode and cycles/2 with each variant (bounds in the drift
+    frame; electrons with Kawazura heating), one grmhd_step call each:
+    unrecoverable zones, whether every primitive is finite, inversion
+    failures and bound hits per cycle, and the corner divergence of sqrt(-g)
+    B relative to max|sqrt(-g) B| / min dX."""
+    import dataclasses
+    import numpy as np
+    base = make_problem("torus128")
+    dx = min((base.xmax[d] - base.xmin[d]) / base.n[d] for d in range(3))
+    runs = [("fp64", dataclasses.replace(base, precision=0), cycles),
+            ("mixed", dataclasses.replace(base, precision=1), cycles),
+            ("float_float", dataclasses.replace(base, precision=2), cycles),
+            ("mixed_ff", dataclasses.replace(base, precision=3), cycles),
+            ("drift_frame", apply_variant(base, "drift"), cycles // 2),
+            ("electrons", apply_variant(base, "electrons"), cycles // 2)]
+    out = {}
+    for name, pr, n in runs:
+        s = grmhd.Sim(pr, stream=stream)
+        s.set_prims(pr.P)
+        if pr.electrons:
+            s.set_electrons(pr.K)
+        t0 = time.perf_counter()
+        s.step(n, sync=False)
+        st = s.stats()
+        sec = time.perf_counter() - t0
+        P = s.get_prims()
+        dv, gb = s.divb()
+        rec = {"cycles": st["steps"], "t": st["t"], "seconds": sec,
+               "unrecoverable": st["unrecoverable"], "all_finite": bool(np.isfinite(P).all()),
+               "inv_failures": st["inv_failures"], "floor_hits_per_stage": st["floor_hits"] / max(2 * n, 1),
+               "divb_rel": dv * dx / gb if gb > 0 else None}
+        if pr.electrons:
+            rec["electrons_finite"] = bool(np.isfinite(s.get_electrons()).all())
+        s.close()
+        out[name] = rec
+    return {"workload": WORKLOADS["torus128"]["label"].replace("_fp64", ""), "runs": out,
+            "note": "floor_hits_per_stage: zones in which a bound acted, per stage (two per cycle)"}
+
+
 def apply_variant(pr, variant):
     """The workload with a variant of the step switched on: the bounds in the
     drift frame, or electron entropies heated by the Kawazura et al. model
@@ -798,6 +839,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision, batched and accuracy legs")
     ap.add_argument("--accuracy-steps", type=int, default=100)
+    ap.add_argument("--long-run", type=int, default=0,
+                    help="instead of the benchmark, run this many cycles of the 128^3 torus in "
+                         "every precision mode (half as many with each variant) and print their "
+                         "health as one JSON line")
     ap.add_argument("--oracle-steps", type=int, default=2,
                     help="cycles of the 288x128x128 torus run by the oracle for the precision "
                          "modes' error against it (0: skip)")
@@ -827,6 +872,12 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.long_run > 0:
+        if rank == 0:
+            print(json.dumps({"long_run": long_run_health(grmhd, args.long_run,
+                                                         torch.cuda.current_stream())}))
+        return
 
     pr = apply_variant(make_problem(args.config), args.variant)
     pr.precision = {"fp64": 0, "mixed": 1, "ff": 2, "mixed_ff": 3}[args.precision]

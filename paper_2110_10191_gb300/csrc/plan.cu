@@ -78,26 +78,23 @@ __global__ void kp_to_f32(BView V, int in) {
   to_f32_body(arr(it, in), it.Pf, (long long)NV * it.A.D.ntot, block_tid(V, g));
 }
 
+// fused FP32 reconstruction + face fluxes (mixed-precision grids)
 template <int DIR>
-__global__ void __launch_bounds__(BS_MAX) kp_recon_f32(BView V) {
+__global__ void __launch_bounds__(BS_MAX) kp_flux_f32(BView V) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
-  float *Lf = (float *)it.Lf, *Rf = (float *)it.Rf;
-  if (it.A.recon == 1)
-    recon_f32_body<DIR, 1>(it.A, it.Pf, Lf, Rf, t);
-  else
-    recon_f32_body<DIR, 0>(it.A, it.Pf, Lf, Rf, t);
-}
-
-template <int DIR>
-__global__ void __launch_bounds__(BS_MAX) kp_face_f32(BView V) {
-  const int g = block_grid(V);
-  const StageItem &it = V.items[g];
-  const long long t = block_tid(V, g);
-  const float *Lf = (const float *)it.Lf, *Rf = (const float *)it.Rf;
-  if (DIR == 2 && it.A.flat3) Lf = Rf = it.Pf;
-  face_f32_body<DIR>(it.A, it.geomf, Lf, Rf, it.F[DIR], t);
+  if (DIR == 0) {
+    if (it.A.recon == 1)
+      flux_f32_x1_body<1>(it.A, it.geomf, it.Pf, it.F[0], t);
+    else
+      flux_f32_x1_body<0>(it.A, it.geomf, it.Pf, it.F[0], t);
+  } else {
+    if (it.A.recon == 1)
+      flux_f32_walk_body<DIR, 1>(it.A, it.geomf, it.Pf, it.F[DIR], t);
+    else
+      flux_f32_walk_body<DIR, 0>(it.A, it.geomf, it.Pf, it.F[DIR], t);
+  }
 }
 
 __global__ void kp_to_ff(BView V, int in) {
@@ -316,12 +313,10 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
   for (int d = 0; d < 3; d++) {
     c[PC_FACE0 + d] = (f64 && !elec) ? n_face(D, d, fl) : 0;
     c[PC_FACE0E + d] = (f64 && elec) ? n_face(D, d, fl) : 0;
-    c[PC_FACE0F + d] = mx ? n_face(D, d, fl) : 0;
+    c[PC_FACE0F + d] = mx ? (d == 0 ? n_flux_f32_x1(D, fl) : n_flux_f32_walk(D, d, fl)) : 0;
     c[PC_FACE0X + d] = fx ? n_face(D, d, fl) : 0;
   }
   c[PC_TOF32] = mx ? (long long)NV * D.ntot : 0;
-  c[PC_RECON01F] = mx ? n_recon(D, fl) : 0;
-  c[PC_RECON2F] = (mx && !fl) ? n_recon(D, 0) : 0;
   c[PC_TOFF] = fx ? (long long)NV * D.ntot : 0;
   c[PC_RECON01X] = fx ? n_recon(D, fl) : 0;
   c[PC_RECON2X] = (fx && !fl) ? n_recon(D, 0) : 0;
@@ -440,12 +435,9 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   nl += launch(p, PC_FACE2E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<2, true><<<nb, bs, 0, st>>>(V, in); });
   // mixed-precision grids
   nl += launch(p, PC_TOF32, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_f32<<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });
-  nl += launch(p, PC_FACE0F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<0><<<nb, bs, 0, st>>>(V); });
-  nl += launch(p, PC_RECON01F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<1><<<nb, bs, 0, st>>>(V); });
-  nl += launch(p, PC_FACE1F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<1><<<nb, bs, 0, st>>>(V); });
-  nl += launch(p, PC_RECON2F, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<2><<<nb, bs, 0, st>>>(V); });
-  nl += launch(p, PC_FACE2F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<2><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE0F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_flux_f32<0><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE1F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_flux_f32<1><<<nb, bs, 0, st>>>(V); });
+  nl += launch(p, PC_FACE2F, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_flux_f32<2><<<nb, bs, 0, st>>>(V); });
   // float-float grids
   nl += launch(p, PC_TOFF, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_to_ff<<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON01X, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<0><<<nb, bs, 0, st>>>(V); });
@@ -579,7 +571,7 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     int which;  // what one pass launches
   };
   const Group groups[] = {{PC_RECON01, 0},  {PC_RECON2, 1},  {PC_FACE0, 2},    {PC_FACE1, 3},
-                          {PC_FACE2, 4},    {PC_UPD64, 5},   {PC_RECON01F, 6}, {PC_RECON2F, 7},
+                          {PC_FACE2, 4},    {PC_UPD64, 5},
                           {PC_FACE0F, 8},   {PC_FACE1F, 9},  {PC_FACE2F, 10},  {PC_RECON01X, 11},
                           {PC_RECON2X, 12}, {PC_FACE0X, 13}, {PC_FACE1X, 14},  {PC_FACE2X, 15},
                           {PC_UPDX, 16}};
@@ -608,21 +600,14 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
       case 16:
         L(PC_UPDX, [&](unsigned nb, unsigned bs, BView V) { kp_update_ff<<<nb, bs, 0, st>>>(V, 0, 0.5, 0); });
         break;
-      case 6:
-        L(PC_RECON01F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<0><<<nb, bs, 0, st>>>(V); });
-        L(PC_RECON01F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<1><<<nb, bs, 0, st>>>(V); });
-        break;
-      case 7:
-        L(PC_RECON2F, [&](unsigned nb, unsigned bs, BView V) { kp_recon_f32<2><<<nb, bs, 0, st>>>(V); });
-        break;
       case 8:
-        L(PC_FACE0F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<0><<<nb, bs, 0, st>>>(V); });
+        L(PC_FACE0F, [&](unsigned nb, unsigned bs, BView V) { kp_flux_f32<0><<<nb, bs, 0, st>>>(V); });
         break;
       case 9:
-        L(PC_FACE1F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<1><<<nb, bs, 0, st>>>(V); });
+        L(PC_FACE1F, [&](unsigned nb, unsigned bs, BView V) { kp_flux_f32<1><<<nb, bs, 0, st>>>(V); });
         break;
       case 10:
-        L(PC_FACE2F, [&](unsigned nb, unsigned bs, BView V) { kp_face_f32<2><<<nb, bs, 0, st>>>(V); });
+        L(PC_FACE2F, [&](unsigned nb, unsigned bs, BView V) { kp_flux_f32<2><<<nb, bs, 0, st>>>(V); });
         break;
       case 11:
         L(PC_RECON01X, [&](unsigned nb, unsigned bs, BView V) { kp_recon_ff<0><<<nb, bs, 0, st>>>(V); });

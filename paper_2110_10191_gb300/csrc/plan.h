@@ -46,9 +46,7 @@ enum {
   PC_FACE1E,
   PC_FACE2E,
   PC_TOF32,  // mixed: FP32 copy of the stage input
-  PC_RECON01F,
-  PC_RECON2F,
-  PC_FACE0F,
+  PC_FACE0F, // mixed: fused FP32 reconstruction + face fluxes per direction
   PC_FACE1F,
   PC_FACE2F,
   PC_TOFF,  // float-float: split copy of the stage input
