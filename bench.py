@@ -51,12 +51,13 @@ WORKLOADS = {
 # launch of each (kp_recon<0>, kp_face<0>, kp_update).  The figures hold
 # while the kernel sources hash to src_hash; otherwise the bench reports the
 # traffic as unknown (null).
-NCU_TRAFFIC = {"src_hash": "8f586f76c0bbb338",
-               "torus128": {"recon": 152264192 + 229483264, "flux": 297974016 + 113205504,
-                            "update": 594006016 + 271203840}}
+NCU_TRAFFIC = {"src_hash": "e2cc01990642d415",
+               "torus128": {"recon": 152241664 + 229469952, "flux": 297971456 + 113579264,
+                            "update": 593764864 + 271408640}}
 # sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of the same
-# captures (the hardware's view of the same launches)
-NCU_FP64_PIPE = {"torus128": {"recon": 0.861, "flux": 0.890, "update": 0.887}}
+# captures (the hardware's view of the same launches, as a fraction of the
+# nominal 2 FP64 instructions per SM per clock)
+NCU_FP64_PIPE = {"torus128": {"recon": 0.862, "flux": 0.889, "update": 0.887}}
 
 
 def kernel_source_hash():
@@ -839,6 +840,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision, batched and accuracy legs")
     ap.add_argument("--accuracy-steps", type=int, default=100)
+    ap.add_argument("--only", default="", choices=["", "batched", "batched_small"],
+                    help="run only this leg (no headline) and print its figures as one JSON line")
     ap.add_argument("--long-run", type=int, default=0,
                     help="instead of the benchmark, run this many cycles of the 128^3 torus in "
                          "every precision mode (half as many with each variant) and print their "
@@ -878,6 +881,15 @@ def main():
             print(json.dumps({"long_run": long_run_health(grmhd, args.long_run,
                                                          torch.cuda.current_stream())}))
         return
+    if args.only:
+        # one leg alone (for profiling captures of it)
+        st0 = torch.cuda.current_stream()
+        legs = {"batched": lambda: batched_throughput(grmhd, max(args.steps // 2, 5), args.warmup, st0),
+                "batched_small": lambda: batched_throughput(grmhd, args.steps, args.warmup, st0,
+                                                            nmin=32, nmax=48)}
+        if rank == 0:
+            print(json.dumps({args.only: legs[args.only]()}))
+        return
 
     pr = apply_variant(make_problem(args.config), args.variant)
     pr.precision = {"fp64": 0, "mixed": 1, "ff": 2, "mixed_ff": 3}[args.precision]
@@ -910,6 +922,13 @@ def main():
     st = sim.stats()
     ms = reduce_max(ms, world, "cuda")
     value = job_value(zones, args.steps, world, ms * 1e-3)
+
+    # ---- the same K steps as one grmhd_step call without profiling: the
+    # cycles replay a CUDA graph of one cycle (what a caller of the library
+    # gets); device-timed, beside the profiled timed region above ----
+    sim.step(2)  # captures the graph
+    graph_ms = _timed(stream, lambda: sim.step(args.steps, sync=False))
+    graph_ms = reduce_max(graph_ms, world, "cuda")
 
     # ---- end to end through the C ABI with host buffers ----
     io_bytes = 8 * 8 * zones
@@ -992,6 +1011,12 @@ def main():
                 "note": "set_prims(pinned host) + %d steps + get_prims(pinned host) per job"
                         % args.steps},
             "gpu_launches": launches,
+            "graph_replay": {"value": job_value(zones, args.steps, world, graph_ms * 1e-3),
+                             "unit": UNIT, "ms_per_step": graph_ms / args.steps,
+                             "note": "the same steps in one grmhd_step call with profiling off "
+                                     "(CUDA-graph replay of one cycle, the library's own path); "
+                                     "the timed region above launches each kernel between the "
+                                     "CUDA events that time it per class"},
             "kernel_ms": {k: v[0] for k, v in prof.items()},
             "roofline": roofline,
             "kernels": kernels,
