@@ -46,6 +46,18 @@ __device__ __forceinline__ void to_f32_body(const double *__restrict__ src, floa
   dst[t] = (float)fmax(fmin(x, (double)FLT_MAX), -(double)FLT_MAX);
 }
 
+// FP64 -> FP32 copy of a stage input (primitives: all inside the float
+// range), two elements per thread (n even; 16-byte aligned arrays), one
+// conversion each: on GB300 the conversion runs on the FP64 pipe, and the
+// clamp of to_f32_body would triple its work.
+__device__ __forceinline__ void to_f32_state_body(const double *__restrict__ src,
+                                                  float *__restrict__ dst, long long n,
+                                                  long long t) {
+  if (2 * t >= n) return;
+  const double2 x = reinterpret_cast<const double2 *>(src)[t];
+  reinterpret_cast<float2 *>(dst)[t] = make_float2((float)x.x, (float)x.y);
+}
+
 // Both face values (lo: low face, hi: high face) of the 8 primitives of
 // zone c along DIR (stride st).
 template <int RECON>

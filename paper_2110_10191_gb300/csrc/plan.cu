@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(BS_MAX) kp_face(BView V, int in) {
 __global__ void kp_to_f32(BView V, int in) {
   const int g = block_grid(V);
   const StageItem &it = V.items[g];
-  to_f32_body(arr(it, in), it.Pf, (long long)NV * it.A.D.ntot, block_tid(V, g));
+  to_f32_state_body(arr(it, in), it.Pf, (long long)NV * it.A.D.ntot, block_tid(V, g));
 }
 
 // fused FP32 reconstruction + face fluxes (mixed-precision grids)
@@ -316,7 +316,7 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
     c[PC_FACE0F + d] = mx ? (d == 0 ? n_flux_f32_x1(D, fl) : n_flux_f32_walk(D, d, fl)) : 0;
     c[PC_FACE0X + d] = fx ? n_face(D, d, fl) : 0;
   }
-  c[PC_TOF32] = mx ? (long long)NV * D.ntot : 0;
+  c[PC_TOF32] = mx ? (long long)NV * D.ntot / 2 : 0;  // two elements per thread (NV even)
   c[PC_TOFF] = fx ? (long long)NV * D.ntot : 0;
   c[PC_RECON01X] = fx ? n_recon(D, fl) : 0;
   c[PC_RECON2X] = (fx && !fl) ? n_recon(D, 0) : 0;
