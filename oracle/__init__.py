@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: the oracle is the correctness reference of the
 CUDA library.  Only tests/, ``__graft_entry__.smoke()`` and bench.py's
-cpu_baseline / ``--impl reference`` leg may import it.  It shares no code
+oracle leg (the CPU baseline, ``--impl reference`` and the accuracy figures
+measured against the oracle) may import it.  It shares no code
 with ``paper_2110_10191_gb300`` and imports nothing from it.
 
 ``build()`` compiles two shared objects with g++ (no -march flags, so the

@@ -3,8 +3,9 @@
  * predictor-corrector GRMHD step (iharm3D, arXiv:2110.10191).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference for the
- * CUDA library.  Only tests/, __graft_entry__.smoke() and bench.py's
- * cpu_baseline / reference leg may load it.  It shares no code, header,
+ * CUDA library.  Only tests/, __graft_entry__.smoke() and bench.py's oracle
+ * leg (the CPU baseline, the reference arm and the accuracy figures measured
+ * against the oracle) may load it.  It shares no code, header,
  * table or constant with the CUDA path (paper_2110_10191_gb300/csrc).
  *
  * What the paper fixes and what is read in:
