@@ -150,13 +150,14 @@ enum {
 
 /* READING: 1D_W iteration rule.  Newton on W' = W - D (>= 0 for any physical
  * state) from the guess primitives, W' clamped to >= 0.  Stop after the
- * iteration whose step is <= 1e-8 W, followed by 2 extra Newton steps; at
- * most 16 (+2) iterations.  A Newton step below W' = 0 halves W' instead.
+ * iteration whose step is <= 1e-8 W, followed by 1 extra Newton step (the
+ * error after a step of 1e-8 W is of order 1e-16 W by quadratic convergence,
+ * so one more step reaches round-off); at most 16 (+1) iterations.  A Newton step below W' = 0 halves W' instead.
  * An iterate with v^2(W) > 1 - 1e-10 (below the root, since v^2 falls with
  * W) is replaced by the bisection of the bracket [lo, hi] known from the
  * sign of f, or by doubling W while no upper end is known. */
 static const int INV_MAXIT = 16;
-static const int INV_EXTRA = 2;
+static const int INV_EXTRA = 1;
 static const double INV_TOL = 1.0e-8;
 static const double INV_VSQ_MAX = 1.0 - 1.0e-10;
 

@@ -186,11 +186,13 @@ __device__ __forceinline__ void prim_flux(const double P[NV], const FState &s, c
   F[B3] = G.gdet * (s.bcon[3] * ud - bd * s.ucon[3]);
 }
 
-// acc += F^dir + coef * U without the sqrt(-g) factor: the two rows T^dir_nu
-// and T^t_nu share (rho + u + p + b^2) u_nu and b_nu.
-__device__ __forceinline__ void flux_cons_acc(const double P[NV], const FState &s, double gam,
+// acc (+)= F^dir + coef * U without the sqrt(-g) factor: the two rows
+// T^dir_nu and T^t_nu share (rho + u + p + b^2) u_nu and b_nu.  FIRST: acc
+// is set rather than added to (the first state of a face).  gm1 = gamma - 1.
+template <bool FIRST>
+__device__ __forceinline__ void flux_cons_acc(const double P[NV], const FState &s, double gm1,
                                               int dir, double coef, double acc[NV]) {
-  const double pg = (gam - 1.0) * P[UU];
+  const double pg = gm1 * P[UU];
   const double w = P[RHO] + P[UU] + pg + s.bsq;
   const double pt = pg + 0.5 * s.bsq;
   const double ud = s.ucon[dir], ut = s.ucon[0];
@@ -205,26 +207,30 @@ __device__ __forceinline__ void flux_cons_acc(const double P[NV], const FState &
   T[dir] += pt;
   T[0] += coef * pt;
   const double mf = P[RHO] * uc;
-  acc[RHO] += mf;
-  acc[UU] += T[0] + mf;
-  acc[U1] += T[1];
-  acc[U2] += T[2];
-  acc[U3] += T[3];
-  acc[B1] += s.bcon[1] * uc - bc * s.ucon[1];
-  acc[B2] += s.bcon[2] * uc - bc * s.ucon[2];
-  acc[B3] += s.bcon[3] * uc - bc * s.ucon[3];
+  const double add[NV] = {mf,
+                          T[0] + mf,
+                          T[1],
+                          T[2],
+                          T[3],
+                          s.bcon[1] * uc - bc * s.ucon[1],
+                          s.bcon[2] * uc - bc * s.ucon[2],
+                          s.bcon[3] * uc - bc * s.ucon[3]};
+#pragma unroll
+  for (int v = 0; v < NV; v++) acc[v] = FIRST ? add[v] : acc[v] + add[v];
 }
 
 // Fast-magnetosonic coordinate speeds along dir: roots v of
 // (k.u)^2 = cms2 (k.k + (k.u)^2) for k_mu = delta^dir_mu - v delta^t_mu,
 // cms2 = cs2 + va2 - cs2 va2; a negative discriminant counts as zero.
+// ggm1 = gamma (gamma - 1).
 __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, const Geo &G,
-                                          double gam, int dir, double &vmax, double &vmin) {
+                                          double gam, double ggm1, int dir, double &vmax,
+                                          double &vmin) {
   const double ef = P[RHO] + gam * P[UU];
   const double ee = s.bsq + ef;
   const double iee = rcp_nr(ef * ee);  // one reciprocal for va2 and cs2
   const double va2 = s.bsq * ef * iee;
-  const double cs2 = gam * (gam - 1.0) * P[UU] * ee * iee;
+  const double cs2 = ggm1 * P[UU] * ee * iee;
   const double cms2 = cs2 + va2 - cs2 * va2;
   const double Asq = G.gcon[SY(dir, dir)];
   const double Bsq = G.gcon[SY(0, 0)];
@@ -321,13 +327,14 @@ __device__ __forceinline__ void weno5_pair(double a, double b, double c, double 
 // ---------------------------------------------------------------------------
 // 1D_W primitive recovery (Noble et al. 2006) in W' = W - D.
 // Iteration rule: guess W' from the guess primitives (clamped >= 0); Newton
-// until a step <= 1e-8 W, then 2 more steps; at most 16 (+2) iterations; a
+// until a step <= 1e-8 W, then 1 more step (round-off by quadratic
+// convergence); at most 16 (+1) iterations; a
 // step below W' = 0 halves W'; an iterate with v^2 > 1 - 1e-10 is replaced by
 // the bisection of the bracket known from sign(f), or doubles W while no
 // upper end is known.
 // ---------------------------------------------------------------------------
 constexpr int INV_MAXIT = 16;
-constexpr int INV_EXTRA = 2;
+constexpr int INV_EXTRA = 1;
 constexpr double INV_TOL = 1.0e-8;
 constexpr double INV_VSQ_MAX = 1.0 - 1.0e-10;
 

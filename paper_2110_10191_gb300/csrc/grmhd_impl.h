@@ -36,6 +36,7 @@ constexpr int BC_EXCHANGE = 4;
 struct StepArgs {
   Dims D;
   double gam, igam, cfl;  // adiabatic index, its reciprocal, Courant number
+  double gm1, ggm1;       // gamma - 1 and gamma (gamma - 1)
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   int floor_drift;  // bounds in the drift frame: a separate pass after the update

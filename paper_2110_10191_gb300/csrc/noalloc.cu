@@ -123,6 +123,8 @@ extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *
   A.D = D;
   A.gam = params->gamma;
   A.igam = 1.0 / params->gamma;
+  A.gm1 = params->gamma - 1.0;
+  A.ggm1 = params->gamma * (params->gamma - 1.0);
   A.cfl = params->cfl;
   for (int d = 0; d < 3; d++) {
     A.dx[d] = G.dx[d];

@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(BS) k_flux(StepArgs A, const double *__restric
     fluid_state(PL, G, sL);
     fluid_state(PR, G, sR);
     double vmaxL, vminL, vmaxR, vminR;
-    mhd_vchar(PL, sL, G, A.gam, DIR + 1, vmaxL, vminL);
-    mhd_vchar(PR, sR, G, A.gam, DIR + 1, vmaxR, vminR);
+    mhd_vchar(PL, sL, G, A.gam, A.ggm1, DIR + 1, vmaxL, vminL);
+    mhd_vchar(PR, sR, G, A.gam, A.ggm1, DIR + 1, vmaxR, vminR);
     const double cmax = fmax(fmax(0.0, vmaxL), vmaxR);
     const double cmin = fmax(fmax(0.0, -vminL), -vminR);
     const double ct = fmax(cmax, cmin);

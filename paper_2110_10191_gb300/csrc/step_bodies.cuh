@@ -256,18 +256,16 @@ __device__ __forceinline__ void face_body(const StepArgs &A, const double *__res
     fluid_state(PL, G, sL);
     fluid_state(PR, G, sR);
     double vmaxL, vminL, vmaxR, vminR;
-    mhd_vchar(PL, sL, G, A.gam, DIR + 1, vmaxL, vminL);
-    mhd_vchar(PR, sR, G, A.gam, DIR + 1, vmaxR, vminR);
-    const double cmax = fmax(fmax(0.0, vmaxL), vmaxR);
-    const double cmin = fmax(fmax(0.0, -vminL), -vminR);
-    const double ct = fmax(cmax, cmin);
+    mhd_vchar(PL, sL, G, A.gam, A.ggm1, DIR + 1, vmaxL, vminL);
+    mhd_vchar(PR, sR, G, A.gam, A.ggm1, DIR + 1, vmaxR, vminR);
+    // c_top = max(0, vmax_L, vmax_R, -vmin_L, -vmin_R); vmax >= vmin on each
+    // side, so max(vmax, -vmin) >= 0 and the 0 never decides
+    const double ct = fmax(fmax(vmaxL, -vminL), fmax(vmaxR, -vminR));
     // LLF: F = 1/2 sqrt(-g) [(F_L + ct U_L) + (F_R - ct U_R)]
     double acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) acc[v] = 0.0;
-    flux_cons_acc(PL, sL, A.gam, DIR + 1, ct, acc);
+    flux_cons_acc<true>(PL, sL, A.gm1, DIR + 1, ct, acc);
     const double mL = acc[RHO];  // rho_L (u^d_L + ct u^t_L): the left mass term
-    flux_cons_acc(PR, sR, A.gam, DIR + 1, -ct, acc);
+    flux_cons_acc<false>(PR, sR, A.gm1, DIR + 1, -ct, acc);
     const double hg = 0.5 * G.gdet;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v * D.ntot + c] = hg * acc[v];
@@ -530,8 +528,8 @@ __device__ __forceinline__ void update_body(const StepArgs &A, const double *Pi,
       const long long o = v * N + c;
       const double div = (F1[o + 1] - F1[o]) * idx1 + (F2[o + D.s[0]] - F2[o]) * idx2 +
                          (F3[o + D.n2d] - F3[o]) * idx3;
-      const double src = (v >= UU && v <= U3) ? S[v - UU] : 0.0;
-      Un[v] = Ui[v] + dtp * (src - div);
+      // the source enters the energy and momentum rows only
+      Un[v] = (v >= UU && v <= U3) ? fma(dtp, S[v - UU] - div, Ui[v]) : fma(-dtp, div, Ui[v]);
     }
     double pn[NV], bsq_n = 0.0, lor_n = 1.0;
     pf = invert_1dw(Un, G, A.gam, A.igam, pi, pn, bsq_n, lor_n);
