@@ -131,7 +131,7 @@ __device__ __forceinline__ void fluid_state(const double P[NV], const Geo &G, FS
   const double l2 = G.gcov[SY(1, 2)] * v1 + G.gcov[SY(2, 2)] * v2 + G.gcov[SY(2, 3)] * v3;
   const double l3 = G.gcov[SY(1, 3)] * v1 + G.gcov[SY(2, 3)] * v2 + G.gcov[SY(3, 3)] * v3;
   // gamma and 1/gamma from one reciprocal square root
-  const double g2 = 1.0 + (l1 * v1 + l2 * v2 + l3 * v3);
+  const double g2 = fma(l1, v1, fma(l2, v2, fma(l3, v3, 1.0)));
   const double rg = rsqrt_nr(g2);
   const double gam = g2 * rg;
   const double ga = gam * G.alpha;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void fluid_state(const double P[NV], const Geo &G, FS
   s.ucon[1] = v1 - ga * G.gcon[SY(0, 1)];
   s.ucon[2] = v2 - ga * G.gcon[SY(0, 2)];
   s.ucon[3] = v3 - ga * G.gcon[SY(0, 3)];
-  s.ucov[0] = -ga + (G.gcov[SY(0, 1)] * v1 + G.gcov[SY(0, 2)] * v2 + G.gcov[SY(0, 3)] * v3);
+  s.ucov[0] = fma(G.gcov[SY(0, 1)], v1, fma(G.gcov[SY(0, 2)], v2, fma(G.gcov[SY(0, 3)], v3, -ga)));
   s.ucov[1] = l1;
   s.ucov[2] = l2;
   s.ucov[3] = l3;
@@ -238,14 +238,15 @@ __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, c
   const double Au = s.ucon[dir];
   const double Bu = s.ucon[0];
   const double AuBu = Au * Bu;
+  // qa v^2 - 2 hb v + qc = 0: roots (hb +- sqrt(hb^2 - qa qc)) / qa
   const double qa = Bu * Bu - (Bsq + Bu * Bu) * cms2;
-  const double qb = -2.0 * (AuBu - (AB + AuBu) * cms2);
+  const double hb = AuBu - (AB + AuBu) * cms2;
   const double qc = Au * Au - (Asq + Au * Au) * cms2;
-  double disc = qb * qb - 4.0 * qa * qc;
+  double disc = fma(hb, hb, -(qa * qc));
   disc = (disc >= DBL_NORMAL_MIN) ? sqrt_nr(disc) : 0.0;  // a subnormal root is negligible
-  const double i2a = 0.5 * rcp_nr(qa);
-  const double v1 = (-qb + disc) * i2a;
-  const double v2 = (-qb - disc) * i2a;
+  const double ia = rcp_nr(qa);
+  const double v1 = (hb + disc) * ia;
+  const double v2 = (hb - disc) * ia;
   vmax = fmax(v1, v2);
   vmin = fmin(v1, v2);
 }
