@@ -272,12 +272,10 @@ __device__ __forceinline__ void flux_cons_acc_ff(const ff P[NV], const FStateFF 
 // gam: the adiabatic index, ggm1 = gam (gam - 1), both float-float
 __device__ __forceinline__ void mhd_vchar_ff(const ff P[NV], const FStateFF &s, const GeoFF &G,
                                              ff gam, ff ggm1, int dir, ff &vmax, ff &vmin) {
+  // cs2 + va2 - cs2 va2 = (gamma (gamma - 1) u + b^2) / (b^2 + e_f) exactly
   const ff ef = ff_add(P[RHO], ff_mul(P[UU], gam));
   const ff ee = ff_add(s.bsq, ef);
-  const ff iee = ff_rcp(ff_mul(ef, ee));
-  const ff va2 = ff_mul(ff_mul(s.bsq, ef), iee);
-  const ff cs2 = ff_mul(ff_mul(ff_mul(P[UU], ggm1), ee), iee);
-  const ff cms2 = ff_sub(ff_add(cs2, va2), ff_mul(cs2, va2));
+  const ff cms2 = ff_mul(ff_add(ff_mul(P[UU], ggm1), s.bsq), ff_rcp(ee));
   const ff Asq = G.gcon[SY(dir, dir)];
   const ff Bsq = G.gcon[SY(0, 0)];
   const ff AB = G.gcon[SY(0, dir)];

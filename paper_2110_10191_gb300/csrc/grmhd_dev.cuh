@@ -222,16 +222,16 @@ __device__ __forceinline__ void flux_cons_acc(const double P[NV], const FState &
 // Fast-magnetosonic coordinate speeds along dir: roots v of
 // (k.u)^2 = cms2 (k.k + (k.u)^2) for k_mu = delta^dir_mu - v delta^t_mu,
 // cms2 = cs2 + va2 - cs2 va2; a negative discriminant counts as zero.
-// ggm1 = gamma (gamma - 1).
+// With cs2 = gamma (gamma - 1) u / e_f, va2 = b^2 / (b^2 + e_f) and
+// e_f = rho + gamma u, the combination is exactly
+// cms2 = (gamma (gamma - 1) u + b^2) / (b^2 + e_f): one reciprocal, no
+// cancellation.  ggm1 = gamma (gamma - 1).
 __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, const Geo &G,
                                           double gam, double ggm1, int dir, double &vmax,
                                           double &vmin) {
-  const double ef = P[RHO] + gam * P[UU];
+  const double ef = fma(gam, P[UU], P[RHO]);
   const double ee = s.bsq + ef;
-  const double iee = rcp_nr(ef * ee);  // one reciprocal for va2 and cs2
-  const double va2 = s.bsq * ef * iee;
-  const double cs2 = ggm1 * P[UU] * ee * iee;
-  const double cms2 = cs2 + va2 - cs2 * va2;
+  const double cms2 = fma(ggm1, P[UU], s.bsq) * rcp_nr(ee);
   const double Asq = G.gcon[SY(dir, dir)];
   const double Bsq = G.gcon[SY(0, 0)];
   const double AB = G.gcon[SY(0, dir)];
