@@ -143,7 +143,7 @@ static void drop_graph(grmhd_batch *b) {
 
 extern "C" int grmhd_batch_set_launch(grmhd_batch *b, int kclass, int threads, int order) {
   if (!b) return GRMHD_ERR_INVALID;
-  static const int recon[] = {PC_RECON01, PC_RECON2, PC_TOF32, PC_RECON01X, PC_RECON2X};
+  static const int recon[] = {PC_RECON0, PC_RECON1, PC_RECON2, PC_TOF32, PC_RECON01X, PC_RECON2X};
   static const int flux[] = {PC_FACE0,  PC_FACE1,  PC_FACE2,  PC_FACE0E, PC_FACE1E, PC_FACE2E,
                              PC_FACE0F, PC_FACE1F, PC_FACE2F, PC_FACE0X, PC_FACE1X, PC_FACE2X};
   static const int zone[] = {PC_ZONE, PC_UPD64, PC_UPDX};
@@ -151,7 +151,7 @@ extern "C" int grmhd_batch_set_launch(grmhd_batch *b, int kclass, int threads, i
   int ncls = 0;
   if (kclass == GRMHD_K_RECON) {
     cls = recon;
-    ncls = 5;
+    ncls = 6;
   } else if (kclass == GRMHD_K_FLUX) {
     cls = flux;
     ncls = 12;

@@ -294,20 +294,23 @@ __device__ __forceinline__ double weno5_hi(double a, double b, double c, double 
 // the low face's by mirroring: Al = 2 D2 - 3 dp1 = D2 - C, Bl = dp1 + 2 dm1
 // = s1 + dm1, Cl.  The weights d_k/(eps + beta_k)^2 are taken over the
 // common denominator q0 q1 q2 of the squared (4 eps + 4 beta_k) and scaled
-// by 10, which leaves their ratios unchanged (4 eps + 4 beta_k costs one
-// multiply and two FMAs), and one reciprocal serves both faces, with the
-// 1/6 of the candidate differences folded into it.  The terms pair up under
-// the mirror a <-> e, b <-> d (A <-> Al, B <-> -Bl, C <-> -Cl), so a
-// mirrored stencil gives the same two values swapped, bit for bit.
-__device__ __forceinline__ void weno5_pair(double a, double b, double c, double d, double e,
-                                           double &lo, double &hi) {
-  const double eps4 = 4.0e-26, c13 = 13.0 / 3.0;
-  const double dm2 = b - a, dm1 = c - b, dp1 = d - c, dp2 = e - d;
-  const double D0 = dm1 - dm2, D1 = dp1 - dm1, D2 = dp2 - dp1;
+// by 10, which leaves their ratios unchanged, and one reciprocal serves
+// both faces, with the 1/6 of the candidate differences folded into it.
+// 4 eps + 4 beta_k = s_k^2 + T_k with T_k = (13/3) D_k^2 + 4 eps, a
+// function of the one second difference D_k: along a column the T_k of
+// one zone are T_{k+1}, T_{k+2} of its lower neighbours, so a walk forms one
+// new D and T per zone (weno5_walk).  The terms pair up under the mirror
+// a <-> e, b <-> d (A <-> Al, B <-> -Bl, C <-> -Cl, D0 <-> D2, s0 <-> -s2),
+// so a mirrored stencil gives the same two values swapped, bit for bit.
+__device__ __forceinline__ double weno5_T(double Dk) {
+  return fma((13.0 / 3.0) * Dk, Dk, 4.0e-26);
+}
+
+__device__ __forceinline__ void weno5_pair_dt(double c, double dm1, double dp1, double D0,
+                                              double D1, double D2, double T0, double T1,
+                                              double T2, double &lo, double &hi) {
   const double s0 = fma(2.0, dm1, D0), s1 = dm1 + dp1, s2 = fma(-2.0, dp1, D2);
-  const double e0 = fma(c13 * D0, D0, fma(s0, s0, eps4));
-  const double e1 = fma(c13 * D1, D1, fma(s1, s1, eps4));
-  const double e2 = fma(c13 * D2, D2, fma(s2, s2, eps4));
+  const double e0 = fma(s0, s0, T0), e1 = fma(s1, s1, T1), e2 = fma(s2, s2, T2);
   const double q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
   // linear weights in the ratio 1 : 6 : 3 (only ratios enter)
   const double q12 = q1 * q2, q02 = 6.0 * (q0 * q2), q01 = q0 * q1;
@@ -323,6 +326,48 @@ __device__ __forceinline__ void weno5_pair(double a, double b, double c, double 
   const double r = rcp_nr(H * L) * (1.0 / 6.0);
   hi = fma(nh, L * r, c);
   lo = fma(nl, H * r, c);
+}
+
+__device__ __forceinline__ void weno5_pair(double a, double b, double c, double d, double e,
+                                           double &lo, double &hi) {
+  const double dm2 = b - a, dm1 = c - b, dp1 = d - c, dp2 = e - d;
+  const double D0 = dm1 - dm2, D1 = dp1 - dm1, D2 = dp2 - dp1;
+  weno5_pair_dt(c, dm1, dp1, D0, D1, D2, weno5_T(D0), weno5_T(D1), weno5_T(D2), lo, hi);
+}
+
+// Both face values of n consecutive zones of one column (stride st; p, lf
+// and rf point at the first zone): each zone after the first loads one new
+// value and forms one first difference, one second difference and one T_k;
+// the values equal weno5_pair's on each zone's stencil bit for bit.
+__device__ __forceinline__ void weno5_walk(const double *__restrict__ p, double *__restrict__ lf,
+                                           double *__restrict__ rf, long long st, int n) {
+  const double xm1 = __ldg(p - st);
+  double x0 = __ldg(p), xp1 = __ldg(p + st), xp2 = __ldg(p + 2 * st);
+  double dm1 = x0 - xm1, dp1 = xp1 - x0, dp2 = xp2 - xp1;
+  double D0 = dm1 - (xm1 - __ldg(p - 2 * st)), D1 = dp1 - dm1, D2 = dp2 - dp1;
+  double T0 = weno5_T(D0), T1 = weno5_T(D1), T2 = weno5_T(D2);
+  for (int m = 0;; m++) {
+    // the next zone's new value, loaded before this zone's arithmetic
+    const double xn = (m + 1 < n) ? __ldg(p + (m + 3) * st) : 0.0;
+    double lo, hi;
+    weno5_pair_dt(x0, dm1, dp1, D0, D1, D2, T0, T1, T2, lo, hi);
+    lf[m * st] = lo;
+    rf[m * st] = hi;
+    if (m + 1 >= n) break;
+    const double dn = xn - xp2;
+    x0 = xp1;
+    xp1 = xp2;
+    xp2 = xn;
+    dm1 = dp1;
+    dp1 = dp2;
+    D0 = D1;
+    D1 = D2;
+    D2 = dn - dp2;
+    dp2 = dn;
+    T0 = T1;
+    T1 = T2;
+    T2 = weno5_T(D2);
+  }
 }
 
 // ---------------------------------------------------------------------------

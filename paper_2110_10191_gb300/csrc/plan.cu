@@ -308,8 +308,9 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
   c[PC_BX1] = n_bounds_x1(D);
   c[PC_BX2] = n_bounds_x2(D);
   c[PC_BX3] = n_bounds_x3(D);
-  c[PC_RECON01] = f64 ? n_recon(D, fl) : 0;
-  c[PC_RECON2] = (f64 && !fl) ? n_recon(D, 0) : 0;
+  c[PC_RECON0] = f64 ? n_recon_walk(D, 0, fl) : 0;
+  c[PC_RECON1] = f64 ? n_recon_walk(D, 1, fl) : 0;
+  c[PC_RECON2] = (f64 && !fl) ? n_recon_walk(D, 2, 0) : 0;
   for (int d = 0; d < 3; d++) {
     c[PC_FACE0 + d] = (f64 && !elec) ? n_face(D, d, fl) : 0;
     c[PC_FACE0E + d] = (f64 && elec) ? n_face(D, d, fl) : 0;
@@ -424,10 +425,10 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   int nl = plan_clock(p, 0, st, h);
   const int R = GRMHD_K_RECON, F = GRMHD_K_FLUX;
   // FP64 grids
-  nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON0, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0, true><<<nb, bs, 0, st>>>(V, in); });
-  nl += launch(p, PC_RECON01, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON1, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE1, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE1E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<1, true><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON2, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, in); });
@@ -570,8 +571,8 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     int cls;
     int which;  // what one pass launches
   };
-  const Group groups[] = {{PC_RECON01, 0},  {PC_RECON2, 1},  {PC_FACE0, 2},    {PC_FACE1, 3},
-                          {PC_FACE2, 4},    {PC_UPD64, 5},
+  const Group groups[] = {{PC_RECON0, 0},   {PC_RECON1, 6},  {PC_RECON2, 1},   {PC_FACE0, 2},
+                          {PC_FACE1, 3},    {PC_FACE2, 4},   {PC_UPD64, 5},
                           {PC_FACE0F, 8},   {PC_FACE1F, 9},  {PC_FACE2F, 10},  {PC_RECON01X, 11},
                           {PC_RECON2X, 12}, {PC_FACE0X, 13}, {PC_FACE1X, 14},  {PC_FACE2X, 15},
                           {PC_UPDX, 16}};
@@ -579,8 +580,10 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     auto L = [&](int cls, auto &&body) { launch(p, cls, 0, nullptr, body); };
     switch (which) {
       case 0:
-        L(PC_RECON01, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, 0); });
-        L(PC_RECON01, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, 0); });
+        L(PC_RECON0, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, 0); });
+        break;
+      case 6:
+        L(PC_RECON1, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, 0); });
         break;
       case 1:
         L(PC_RECON2, [&](unsigned nb, unsigned bs, BView V) { kp_recon<2><<<nb, bs, 0, st>>>(V, 0); });

@@ -37,8 +37,9 @@ enum {
   PC_BX1,
   PC_BX2,
   PC_BX3,
-  PC_RECON01,  // FP64 reconstruction along X1 and X2
-  PC_RECON2,   // along X3 (none for flat-X3 grids)
+  PC_RECON0,  // FP64 reconstruction along X1 (column walks)
+  PC_RECON1,  // along X2
+  PC_RECON2,  // along X3 (none for flat-X3 grids)
   PC_FACE0,
   PC_FACE1,
   PC_FACE2,

@@ -52,6 +52,14 @@ __host__ __device__ inline long long n_bounds_x3(const Dims &D) { return D.n2d *
 __host__ __device__ inline long long n_recon(const Dims &D, int flat3) {
   return (long long)(D.n[0] + 2) * (D.n[1] + 2) * (flat3 ? 1 : D.n[2] + 2);
 }
+// zones of one FP64 reconstruction walk (one thread each)
+constexpr int RWALK = 16;
+// threads of the FP64 reconstruction along dir: one per column and segment
+// of up to RWALK zones along dir
+__host__ __device__ inline long long n_recon_walk(const Dims &D, int dir, int flat3) {
+  const long long e[3] = {D.n[0] + 2, D.n[1] + 2, flat3 ? 1 : D.n[2] + 2};
+  return e[0] * e[1] * e[2] / e[dir] * ((e[dir] + RWALK - 1) / RWALK);
+}
 // faces along dir: dir index NG .. n+NG, transverse NG-1 .. n+NG (flux-CT
 // needs one transverse layer on each side); flat X3 keeps the k = NG layer
 __host__ __device__ inline void face_box(const Dims &D, int dir, int flat3, int lo[3], int ext[3]) {
@@ -192,35 +200,49 @@ __device__ __forceinline__ void warp_block_max(double v, unsigned long long *dst
   }
 }
 
-// Zone-centric reconstruction: one thread per zone reconstructs both face
-// values of its 8 primitives along DIR (zones NG-1 .. n+NG along DIR and the
-// extended transverse range), so each zone's WENO smoothness indicators are
-// formed once.  Lf = value at the zone's low face, Rf = at its high face.
+// Zone-centric reconstruction: both face values of each zone's 8 primitives
+// along DIR (zones NG-1 .. n+NG along DIR and the extended transverse
+// range), each zone's WENO smoothness indicators formed once.  One thread
+// walks a segment of up to RWALK zones of one column along DIR, so
+// consecutive zones share their differences (weno5_walk); consecutive
+// threads take neighbouring columns (along X2 for DIR = 0, along X1
+// otherwise).  Lf = value at the zone's low face, Rf = at its high face.
 template <int DIR, int RECON>
 __device__ __forceinline__ void recon_body(const StepArgs &A, const double *__restrict__ P,
                                            double *__restrict__ Lf, double *__restrict__ Rf,
                                            long long t) {
   const Dims &D = A.D;
-  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2;
-  if (t >= n_recon(D, A.flat3)) return;
-  const int i = NG - 1 + (int)(t % e0);
-  const int j = NG - 1 + (int)((t / e0) % e1);
-  const int k = (A.flat3 ? NG : NG - 1) + (int)(t / ((long long)e0 * e1));
+  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2, e2 = A.flat3 ? 1 : D.n[2] + 2;
+  const int ed = (DIR == 0) ? e0 : (DIR == 1) ? e1 : e2;
+  const int ea = (DIR == 0) ? e1 : e0;  // the column index that varies fastest
+  const int eb = (DIR == 2) ? e1 : e2;
+  const int nseg = (ed + RWALK - 1) / RWALK;
+  if (t >= (long long)ea * eb * nseg) return;
+  const int ca = (int)(t % ea);
+  const long long r = t / ea;
+  const int cb = (int)(r % eb);
+  const int m0 = (int)(r / eb) * RWALK;
+  const int kb = A.flat3 ? NG : NG - 1;
+  const int i = NG - 1 + ((DIR == 0) ? m0 : ca);
+  const int j = NG - 1 + ((DIR == 1) ? m0 : (DIR == 0) ? ca : cb);
+  const int k = (DIR == 2) ? NG - 1 + m0 : kb + cb;
+  const int n = min(RWALK, ed - m0);
   const long long c = zid(D, i, j, k);
   const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
-#pragma unroll
+#pragma unroll 1
   for (int v = 0; v < NV; v++) {
     const double *p = P + v * D.ntot + c;
-    double lo, hi;
+    double *lf = Lf + v * D.ntot + c, *rf = Rf + v * D.ntot + c;
     if (RECON == 1) {
-      weno5_pair(__ldg(p - 2 * st), __ldg(p - st), __ldg(p), __ldg(p + st), __ldg(p + 2 * st), lo, hi);
+      weno5_walk(p, lf, rf, st, n);
     } else {
-      const double x1 = __ldg(p), h = 0.5 * mc_slope(__ldg(p - st), x1, __ldg(p + st));
-      lo = x1 - h;
-      hi = x1 + h;
+      for (int m = 0; m < n; m++) {
+        const double *q = p + m * st;
+        const double x1 = __ldg(q), h = 0.5 * mc_slope(__ldg(q - st), x1, __ldg(q + st));
+        lf[m * st] = x1 - h;
+        rf[m * st] = x1 + h;
+      }
     }
-    Lf[v * D.ntot + c] = lo;
-    Rf[v * D.ntot + c] = hi;
   }
 }
 
