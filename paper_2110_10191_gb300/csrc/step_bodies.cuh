@@ -54,6 +54,7 @@ __host__ __device__ inline long long n_recon(const Dims &D, int flat3) {
 }
 // zones of one FP64 reconstruction walk (one thread each)
 constexpr int RWALK = 16;
+static_assert(RWALK <= 16, "weno5_walk unrolls over at most 16 zones");
 // threads of the FP64 reconstruction along dir: one per column and segment
 // of up to RWALK zones along dir
 __host__ __device__ inline long long n_recon_walk(const Dims &D, int dir, int flat3) {
