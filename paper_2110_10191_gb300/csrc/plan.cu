@@ -55,11 +55,20 @@ __global__ void __launch_bounds__(BS_MAX) kp_recon(BView V, int in) {
   const StageItem &it = V.items[g];
   const long long t = block_tid(V, g);
   const double *Ps = arr(it, in);
-  if (it.A.recon == 1)
-    recon_body<DIR, 1>(it.A, Ps, it.Lf, it.Rf, t);
-  else
+  if (it.A.recon == 1) {
+    if (DIR == 0) {  // launched with X1_WARP_BYTES of shared memory per warp
+      extern __shared__ __align__(16) unsigned char recon_sm[];
+      recon_x1_staged(it.A, Ps, it.Lf, it.Rf, t, recon_sm + (threadIdx.x >> 5) * X1_WARP_BYTES);
+    } else {
+      recon_body<DIR, 1>(it.A, Ps, it.Lf, it.Rf, t);
+    }
+  } else {
     recon_body<DIR, 0>(it.A, Ps, it.Lf, it.Rf, t);
+  }
 }
+
+// dynamic shared memory of a kp_recon<0> launch of bs threads
+inline unsigned recon_x1_smem(unsigned bs) { return (bs / 32) * X1_WARP_BYTES; }
 
 // ELEC: the grids of the launch evolve electron entropies (a class of their own)
 template <int DIR, bool ELEC = false>
@@ -369,6 +378,14 @@ int plan_build(Plan &p, const StageItem *items, int n) {
   }
   p.zones = zones;
   p.tab_cap = cap;
+  // kp_recon<0> takes more than the default 48 KiB of dynamic shared memory
+  // at the largest block (on the device current now, the plan's)
+  if (cudaFuncSetAttribute(kp_recon<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)recon_x1_smem(BS_MAX)) != cudaSuccess) {
+    cudaGetLastError();
+    plan_free(p);
+    return GRMHD_ERR_CUDA;
+  }
   if (cudaMalloc(&p.items, sizeof(StageItem) * n) != cudaSuccess ||
       cudaMalloc(&p.tab, sizeof(int) * (size_t)(cap > 0 ? cap : 1)) != cudaSuccess) {
     cudaGetLastError();
@@ -425,7 +442,7 @@ int plan_fluxes(const Plan &p, int in, cudaStream_t st, PlanHook *h) {
   int nl = plan_clock(p, 0, st, h);
   const int R = GRMHD_K_RECON, F = GRMHD_K_FLUX;
   // FP64 grids
-  nl += launch(p, PC_RECON0, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, in); });
+  nl += launch(p, PC_RECON0, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, recon_x1_smem(bs), st>>>(V, in); });
   nl += launch(p, PC_FACE0, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_FACE0E, F, h, [&](unsigned nb, unsigned bs, BView V) { kp_face<0, true><<<nb, bs, 0, st>>>(V, in); });
   nl += launch(p, PC_RECON1, R, h, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, in); });
@@ -580,7 +597,7 @@ int plan_autotune(Plan &p, int trials, cudaStream_t st, double *ms_before, doubl
     auto L = [&](int cls, auto &&body) { launch(p, cls, 0, nullptr, body); };
     switch (which) {
       case 0:
-        L(PC_RECON0, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, 0, st>>>(V, 0); });
+        L(PC_RECON0, [&](unsigned nb, unsigned bs, BView V) { kp_recon<0><<<nb, bs, recon_x1_smem(bs), st>>>(V, 0); });
         break;
       case 6:
         L(PC_RECON1, [&](unsigned nb, unsigned bs, BView V) { kp_recon<1><<<nb, bs, 0, st>>>(V, 0); });

@@ -247,6 +247,99 @@ __device__ __forceinline__ void recon_body(const StepArgs &A, const double *__re
   }
 }
 
+// The WENO5 reconstruction along X1 with each warp's rows staged in shared
+// memory.  The lanes of a warp walk 32 different rows (neighbouring j), so
+// their direct loads and stores touch 32 rows' sectors per instruction; here
+// the warp loads its rows' stencil values together (consecutive addresses),
+// walks them in shared memory, collects the face values of 8 zones per row
+// and writes them back row by row.  Same arithmetic and results as
+// recon_body<0, 1>.  Every thread of the block must call it (warp
+// synchronisation); wsm: the warp's X1_WARP_BYTES of shared memory.
+constexpr int X1_IN = RWALK + 5;  // a row's values at zones -2 .. RWALK+1, odd stride
+constexpr int X1_OUT = 9;         // 8 face values per row and chunk, odd stride
+constexpr int X1_HI = 32 * X1_OUT + 8;  // offset of the high-face chunk (another bank half)
+constexpr int X1_WARP_BYTES = (32 * X1_IN + 2 * X1_HI) * 8 + 32 * 8 + 32 * 4;
+
+__device__ __forceinline__ void recon_x1_staged(const StepArgs &A, const double *__restrict__ P,
+                                                double *__restrict__ Lf, double *__restrict__ Rf,
+                                                long long t, unsigned char *wsm) {
+  const Dims &D = A.D;
+  const int e0 = D.n[0] + 2, e1 = D.n[1] + 2, e2 = A.flat3 ? 1 : D.n[2] + 2;
+  const int nseg = (e0 + RWALK - 1) / RWALK;
+  const int lane = threadIdx.x & 31;
+  double *tin = reinterpret_cast<double *>(wsm);
+  double *tout = tin + 32 * X1_IN;
+  long long *rbase = reinterpret_cast<long long *>(tout + 2 * X1_HI);
+  int *rn = reinterpret_cast<int *>(rbase + 32);
+  int n = 0;  // this lane's zones (0: past the end of the grid's threads)
+  long long c = 0;
+  if (t < (long long)e1 * e2 * nseg) {
+    const int ca = (int)(t % e1);
+    const long long r = t / e1;
+    const int cb = (int)(r % e2);
+    const int m0 = (int)(r / e2) * RWALK;
+    c = zid(D, NG - 1 + m0, NG - 1 + ca, (A.flat3 ? NG : NG - 1) + cb);
+    n = min(RWALK, e0 - m0);
+  }
+  rbase[lane] = c;
+  rn[lane] = n;
+  __syncwarp();
+  const double *x = tin + lane * X1_IN;  // x[q]: this row's value at zone q - 2
+#pragma unroll 1
+  for (int v = 0; v < NV; v++) {
+    const long long ov = v * D.ntot;
+#pragma unroll 4
+    for (int e = lane; e < 32 * (RWALK + 4); e += 32) {
+      const int q = e / (RWALK + 4), xq = e - q * (RWALK + 4);
+      const int nq = rn[q];  // rows past the end (nq = 0) load nothing
+      if (nq > 0 && xq < nq + 4) tin[q * X1_IN + xq] = __ldg(P + ov + rbase[q] - 2 + xq);
+    }
+    __syncwarp();
+    const double xm1 = x[1];
+    double x0 = x[2], xp1 = x[3], xp2 = x[4];
+    double dm1 = x0 - xm1, dp1 = xp1 - x0, dp2 = xp2 - xp1;
+    double D0 = dm1 - (xm1 - x[0]), D1 = dp1 - dm1, D2 = dp2 - dp1;
+    double T0 = weno5_T(D0), T1 = weno5_T(D1), T2 = weno5_T(D2);
+#pragma unroll
+    for (int m = 0; m < RWALK; m++) {
+      if (m < n) {
+        double lo, hi;
+        weno5_pair_dt(x0, dm1, dp1, D0, D1, D2, T0, T1, T2, lo, hi);
+        tout[lane * X1_OUT + (m & 7)] = lo;
+        tout[X1_HI + lane * X1_OUT + (m & 7)] = hi;
+        if (m + 1 < n) {
+          const double dn = x[m + 5] - xp2;
+          x0 = xp1;
+          xp1 = xp2;
+          xp2 = x[m + 5];
+          dm1 = dp1;
+          dp1 = dp2;
+          D0 = D1;
+          D1 = D2;
+          D2 = dn - dp2;
+          dp2 = dn;
+          T0 = T1;
+          T1 = T2;
+          T2 = weno5_T(D2);
+        }
+      }
+      if ((m & 7) == 7) {  // write zones m-7 .. m of every row: 4 rows x 8 zones per store
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 16; it++) {
+          const int e = it * 32 + lane;
+          const int q = (e >> 3) & 31, col = e & 7, z = (m & ~7) + col;
+          if (z < rn[q]) {
+            double *dst = (it < 8) ? Lf : Rf;
+            dst[ov + rbase[q] + z] = tout[((it < 8) ? 0 : X1_HI) + q * X1_OUT + col];
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // One thread per face combines Rf of zone c-1 (left state) and Lf of zone c
 // (right state) into the LLF flux; every thread of the block must call it.
 // ELEC: the grid evolves electron entropies, whose flux weights it stores.
