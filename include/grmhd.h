@@ -319,6 +319,17 @@ int grmhd_divb(grmhd_sim *sim, double *divb_max, double *gb_max);
  * tuned kernels with the previous and the chosen settings. */
 int grmhd_autotune(grmhd_sim *sim, int trials, double *ms_before, double *ms_after);
 
+/* Zones per thread of the FP64 reconstruction ("Implementation Notes",
+ * WENO5 / linear reconstruction).  With 2, 4, 8 or 16, one thread walks
+ * that many consecutive zones of a column along the direction, and
+ * consecutive zones share their stencil differences. With 1, one thread
+ * takes one zone.  0 restores the automatic choice: the longest walk that
+ * still gives every reconstruction launch 152 x 256 threads, else 1.  The
+ * values do not depend on the setting; only the launch shape and the FP64
+ * instruction count do.  Synchronises the device.  *chosen (may be NULL)
+ * receives the length in use.  GRMHD_ERR_INVALID for other values. */
+int grmhd_set_recon_walk(grmhd_sim *sim, int zones_per_thread, int *chosen);
+
 /* Measured double-precision FMA throughput of the current device: runs a
  * dependency-free DFMA kernel for about `iters` FMAs per thread on every SM
  * and returns FLOP/s (2 per FMA) in *flops.  Used as the roofline peak of

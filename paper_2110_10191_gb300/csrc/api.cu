@@ -757,6 +757,14 @@ extern "C" int grmhd_autotune(grmhd_sim *s, int trials, double *ms_before, doubl
   return plan_autotune(s->plan, trials, s->st, ms_before, ms_after);
 }
 
+extern "C" int grmhd_set_recon_walk(grmhd_sim *s, int zones_per_thread, int *chosen) {
+  if (!s) return GRMHD_ERR_INVALID;
+  sim_drop_graph(s);  // the launch shapes change
+  const int rc = plan_set_rwalk(s->plan, zones_per_thread);
+  if (rc == GRMHD_OK && chosen) *chosen = s->plan.host_items[0].A.rwalk;
+  return rc;
+}
+
 extern "C" int grmhd_profile(grmhd_sim *s, int enable) {
   if (!s) return GRMHD_ERR_INVALID;
   s->prof_on = enable ? 1 : 0;

@@ -39,6 +39,9 @@ struct StepArgs {
   double gm1, ggm1;       // gamma - 1 and gamma (gamma - 1)
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
+  // zones per thread of the FP64 reconstruction along a column (2..16), or 1:
+  // one thread per zone; set by the plan from its grids' sizes
+  int rwalk;
   int floor_drift;  // bounds in the drift frame: a separate pass after the update
   // electron entropies (GRMHD_ELEC_* model, 0: off): adiabatic indices of
   // electrons and protons, the constant share, the bounds on T_p/T_e

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(BS_MAX) kp_recon(BView V, int in) {
   const long long t = block_tid(V, g);
   const double *Ps = arr(it, in);
   if (it.A.recon == 1) {
-    if (DIR == 0) {  // launched with X1_WARP_BYTES of shared memory per warp
+    if (DIR == 0 && it.A.rwalk > 1) {  // launched with X1_WARP_BYTES of shared memory per warp
       extern __shared__ __align__(16) unsigned char recon_sm[];
       recon_x1_staged(it.A, Ps, it.Lf, it.Rf, t, recon_sm + (threadIdx.x >> 5) * X1_WARP_BYTES);
     } else {
@@ -307,7 +307,8 @@ int upload_tables(Plan &p) {
 
 }  // namespace
 
-void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long long c[PC_N]) {
+void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, int rwalk,
+                 long long c[PC_N]) {
   const int fl = flat3;
   // the flux stage: FP64, FP32 (mixed, and mixed with the float-float
   // update) or float-float; the update: FP64 or float-float
@@ -317,9 +318,9 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
   c[PC_BX1] = n_bounds_x1(D);
   c[PC_BX2] = n_bounds_x2(D);
   c[PC_BX3] = n_bounds_x3(D);
-  c[PC_RECON0] = f64 ? n_recon_walk(D, 0, fl) : 0;
-  c[PC_RECON1] = f64 ? n_recon_walk(D, 1, fl) : 0;
-  c[PC_RECON2] = (f64 && !fl) ? n_recon_walk(D, 2, 0) : 0;
+  c[PC_RECON0] = f64 ? n_recon_walk(D, 0, fl, rwalk) : 0;
+  c[PC_RECON1] = f64 ? n_recon_walk(D, 1, fl, rwalk) : 0;
+  c[PC_RECON2] = (f64 && !fl) ? n_recon_walk(D, 2, 0, rwalk) : 0;
   for (int d = 0; d < 3; d++) {
     c[PC_FACE0 + d] = (f64 && !elec) ? n_face(D, d, fl) : 0;
     c[PC_FACE0E + d] = (f64 && elec) ? n_face(D, d, fl) : 0;
@@ -345,9 +346,28 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long l
 
 long long plan_bytes(const Dims &D, int flat3, int prec, int drift, int elec) {
   long long c[PC_N], ints = 0;
-  plan_counts(D, flat3, prec, drift, elec, c);
+  plan_counts(D, flat3, prec, drift, elec, 1, c);  // one thread per zone: the most blocks
   for (int q = 0; q < PC_N; q++) ints += 2 * nblk(c[q], 64);
   return (long long)sizeof(StageItem) + 4 * ints;
+}
+
+int plan_rwalk(const StageItem *items, int n) {
+  for (int rw = RWALK; rw >= 2; rw /= 2) {
+    long long least = -1;  // the FP64 reconstruction launch with the fewest threads
+    bool any = false;
+    for (int d = 0; d < 3; d++) {
+      long long tot = 0;
+      for (int g = 0; g < n; g++) {
+        const StepArgs &A = items[g].A;
+        if (items[g].prec != GRMHD_PREC_FP64 || (d == 2 && A.flat3)) continue;
+        tot += n_recon_walk(A.D, d, A.flat3, rw);
+        any = true;
+      }
+      if (tot > 0 && (least < 0 || tot < least)) least = tot;
+    }
+    if (!any || least >= RWALK_MIN_THREADS) return rw;
+  }
+  return 1;
 }
 
 int plan_build(Plan &p, const StageItem *items, int n) {
@@ -361,14 +381,18 @@ int plan_build(Plan &p, const StageItem *items, int n) {
     return GRMHD_ERR_NOMEM;
   }
   memcpy(p.host_items, items, sizeof(StageItem) * n);
+  const int rw = plan_rwalk(items, n);
+  for (int g = 0; g < n; g++) p.host_items[g].A.rwalk = rw;
   long long zones = 0, cap = 0;
   for (int g = 0; g < n; g++) {
-    long long c[PC_N];
-    plan_counts(items[g].A.D, items[g].A.flat3, items[g].prec, items[g].A.floor_drift,
-                items[g].A.elec, c);
+    long long c[PC_N], c1[PC_N];
+    const StepArgs &A = items[g].A;
+    plan_counts(A.D, A.flat3, items[g].prec, A.floor_drift, A.elec, rw, c);
+    plan_counts(A.D, A.flat3, items[g].prec, A.floor_drift, A.elec, 1, c1);
     for (int q = 0; q < PC_N; q++) {
       p.count[(size_t)q * n + g] = c[q];
-      cap += 2 * nblk(c[q], 64);  // the smallest block the tuner tries
+      // room for the smallest block the tuner tries and any walk length
+      cap += 2 * nblk(c1[q] > c[q] ? c1[q] : c[q], 64);
     }
     zones += n_zone(items[g].A.D);
   }
@@ -392,7 +416,7 @@ int plan_build(Plan &p, const StageItem *items, int n) {
     plan_free(p);
     return GRMHD_ERR_NOMEM;
   }
-  if (cudaMemcpy(p.items, items, sizeof(StageItem) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpy(p.items, p.host_items, sizeof(StageItem) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
     plan_free(p);
     return GRMHD_ERR_CUDA;
   }
@@ -411,6 +435,24 @@ void plan_free(Plan &p) {
   p.count = nullptr;
   p.host_items = nullptr;
   p.ngrid = 0;
+}
+
+int plan_set_rwalk(Plan &p, int rw) {
+  if (rw < 0 || rw > RWALK || (rw > 1 && (rw & (rw - 1)))) return GRMHD_ERR_INVALID;
+  if (rw == 0) rw = plan_rwalk(p.host_items, p.ngrid);
+  // kernels still in flight may read the items and tables
+  if (cudaDeviceSynchronize() != cudaSuccess) return GRMHD_ERR_CUDA;
+  const int n = p.ngrid;
+  for (int g = 0; g < n; g++) {
+    StageItem &it = p.host_items[g];
+    it.A.rwalk = rw;
+    long long c[PC_N];
+    plan_counts(it.A.D, it.A.flat3, it.prec, it.A.floor_drift, it.A.elec, rw, c);
+    for (int q = PC_RECON0; q <= PC_RECON2; q++) p.count[(size_t)q * n + g] = c[q];
+  }
+  if (cudaMemcpy(p.items, p.host_items, sizeof(StageItem) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  return upload_tables(p);
 }
 
 int plan_set_class(Plan &p, int cls, int bs, int sched) {

@@ -106,8 +106,20 @@ struct PlanHook {
 // GRMHD_ERR_NOMEM or GRMHD_ERR_CUDA.
 int plan_build(Plan &p, const StageItem *items, int n);
 // threads per launch class of one grid (dimensions, flat X3, GRMHD_PREC_*,
-// bounds in the drift frame, electrons evolved)
-void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, long long c[PC_N]);
+// bounds in the drift frame, electrons evolved, the plan's reconstruction
+// walk length)
+void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, int rwalk,
+                 long long c[PC_N]);
+// The FP64 reconstruction's walk length for a plan of these grids: the
+// longest of 16, 8, 4, 2 zones per thread that still gives each of its
+// launches RWALK_MIN_THREADS threads (enough warps for every SM's FP64
+// unit), else 1 (one thread per zone).
+constexpr long long RWALK_MIN_THREADS = 152 * 256;
+int plan_rwalk(const StageItem *items, int n);
+// Set the plan's reconstruction walk length (1, 2, 4, 8 or 16 zones per
+// thread; 0: plan_rwalk's choice) and re-lay the reconstruction's block
+// tables.  The values do not depend on it.
+int plan_set_rwalk(Plan &p, int rw);
 // device bytes a one-grid plan of such a grid holds (item + block tables)
 long long plan_bytes(const Dims &D, int flat3, int prec, int drift, int elec);
 void plan_free(Plan &p);

@@ -52,14 +52,15 @@ __host__ __device__ inline long long n_bounds_x3(const Dims &D) { return D.n2d *
 __host__ __device__ inline long long n_recon(const Dims &D, int flat3) {
   return (long long)(D.n[0] + 2) * (D.n[1] + 2) * (flat3 ? 1 : D.n[2] + 2);
 }
-// zones of one FP64 reconstruction walk (one thread each)
+// longest FP64 reconstruction walk (zones per thread)
 constexpr int RWALK = 16;
 static_assert(RWALK <= 16, "weno5_walk unrolls over at most 16 zones");
 // threads of the FP64 reconstruction along dir: one per column and segment
-// of up to RWALK zones along dir
-__host__ __device__ inline long long n_recon_walk(const Dims &D, int dir, int flat3) {
+// of rw zones along dir (rw >= 2), or one per zone (rw = 1)
+__host__ __device__ inline long long n_recon_walk(const Dims &D, int dir, int flat3, int rw) {
   const long long e[3] = {D.n[0] + 2, D.n[1] + 2, flat3 ? 1 : D.n[2] + 2};
-  return e[0] * e[1] * e[2] / e[dir] * ((e[dir] + RWALK - 1) / RWALK);
+  if (rw <= 1) return e[0] * e[1] * e[2];
+  return e[0] * e[1] * e[2] / e[dir] * ((e[dir] + rw - 1) / rw);
 }
 // faces along dir: dir index NG .. n+NG, transverse NG-1 .. n+NG (flux-CT
 // needs one transverse layer on each side); flat X3 keeps the k = NG layer
@@ -203,33 +204,58 @@ __device__ __forceinline__ void warp_block_max(double v, unsigned long long *dst
 
 // Zone-centric reconstruction: both face values of each zone's 8 primitives
 // along DIR (zones NG-1 .. n+NG along DIR and the extended transverse
-// range), each zone's WENO smoothness indicators formed once.  One thread
-// walks a segment of up to RWALK zones of one column along DIR, so
-// consecutive zones share their differences (weno5_walk); consecutive
-// threads take neighbouring columns (along X2 for DIR = 0, along X1
-// otherwise).  Lf = value at the zone's low face, Rf = at its high face.
+// range), each zone's WENO smoothness indicators formed once.  With
+// A.rwalk >= 2 one thread walks a segment of A.rwalk zones of one column
+// along DIR, so consecutive zones share their differences (weno5_walk);
+// consecutive threads take neighbouring columns (along X2 for DIR = 0, along
+// X1 otherwise).  With A.rwalk = 1 (grids too small to fill the GPU with
+// walks) one thread takes one zone, consecutive threads along X1.  Same
+// values either way.  Lf = value at the zone's low face, Rf = at its high
+// face.
 template <int DIR, int RECON>
 __device__ __forceinline__ void recon_body(const StepArgs &A, const double *__restrict__ P,
                                            double *__restrict__ Lf, double *__restrict__ Rf,
                                            long long t) {
   const Dims &D = A.D;
   const int e0 = D.n[0] + 2, e1 = D.n[1] + 2, e2 = A.flat3 ? 1 : D.n[2] + 2;
+  const int kb = A.flat3 ? NG : NG - 1;
+  const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
+  const int rw = A.rwalk;
+  if (rw <= 1) {
+    if (t >= (long long)e0 * e1 * e2) return;
+    const long long c = zid(D, NG - 1 + (int)(t % e0), NG - 1 + (int)((t / e0) % e1),
+                            kb + (int)(t / ((long long)e0 * e1)));
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const double *p = P + v * D.ntot + c;
+      double lo, hi;
+      if (RECON == 1) {
+        weno5_pair(__ldg(p - 2 * st), __ldg(p - st), __ldg(p), __ldg(p + st), __ldg(p + 2 * st),
+                   lo, hi);
+      } else {
+        const double x1 = __ldg(p), h = 0.5 * mc_slope(__ldg(p - st), x1, __ldg(p + st));
+        lo = x1 - h;
+        hi = x1 + h;
+      }
+      Lf[v * D.ntot + c] = lo;
+      Rf[v * D.ntot + c] = hi;
+    }
+    return;
+  }
   const int ed = (DIR == 0) ? e0 : (DIR == 1) ? e1 : e2;
   const int ea = (DIR == 0) ? e1 : e0;  // the column index that varies fastest
   const int eb = (DIR == 2) ? e1 : e2;
-  const int nseg = (ed + RWALK - 1) / RWALK;
+  const int nseg = (ed + rw - 1) / rw;
   if (t >= (long long)ea * eb * nseg) return;
   const int ca = (int)(t % ea);
   const long long r = t / ea;
   const int cb = (int)(r % eb);
-  const int m0 = (int)(r / eb) * RWALK;
-  const int kb = A.flat3 ? NG : NG - 1;
+  const int m0 = (int)(r / eb) * rw;
   const int i = NG - 1 + ((DIR == 0) ? m0 : ca);
   const int j = NG - 1 + ((DIR == 1) ? m0 : (DIR == 0) ? ca : cb);
   const int k = (DIR == 2) ? NG - 1 + m0 : kb + cb;
-  const int n = min(RWALK, ed - m0);
+  const int n = min(rw, ed - m0);
   const long long c = zid(D, i, j, k);
-  const long long st = (DIR == 0) ? 1 : (DIR == 1) ? D.s[0] : D.n2d;
 #pragma unroll 1
   for (int v = 0; v < NV; v++) {
     const double *p = P + v * D.ntot + c;
@@ -253,8 +279,8 @@ __device__ __forceinline__ void recon_body(const StepArgs &A, const double *__re
 // the warp loads its rows' stencil values together (consecutive addresses),
 // walks them in shared memory, collects the face values of 8 zones per row
 // and writes them back row by row.  Same arithmetic and results as
-// recon_body<0, 1>.  Every thread of the block must call it (warp
-// synchronisation); wsm: the warp's X1_WARP_BYTES of shared memory.
+// recon_body<0, 1>, for A.rwalk >= 2.  Every thread of the block must call it
+// (warp synchronisation); wsm: the warp's X1_WARP_BYTES of shared memory.
 constexpr int X1_IN = RWALK + 5;  // a row's values at zones -2 .. RWALK+1, odd stride
 constexpr int X1_OUT = 9;         // 8 face values per row and chunk, odd stride
 constexpr int X1_HI = 32 * X1_OUT + 8;  // offset of the high-face chunk (another bank half)
@@ -265,7 +291,8 @@ __device__ __forceinline__ void recon_x1_staged(const StepArgs &A, const double 
                                                 long long t, unsigned char *wsm) {
   const Dims &D = A.D;
   const int e0 = D.n[0] + 2, e1 = D.n[1] + 2, e2 = A.flat3 ? 1 : D.n[2] + 2;
-  const int nseg = (e0 + RWALK - 1) / RWALK;
+  const int rw = A.rwalk;  // 2 .. RWALK
+  const int nseg = (e0 + rw - 1) / rw;
   const int lane = threadIdx.x & 31;
   double *tin = reinterpret_cast<double *>(wsm);
   double *tout = tin + 32 * X1_IN;
@@ -277,9 +304,9 @@ __device__ __forceinline__ void recon_x1_staged(const StepArgs &A, const double 
     const int ca = (int)(t % e1);
     const long long r = t / e1;
     const int cb = (int)(r % e2);
-    const int m0 = (int)(r / e2) * RWALK;
+    const int m0 = (int)(r / e2) * rw;
     c = zid(D, NG - 1 + m0, NG - 1 + ca, (A.flat3 ? NG : NG - 1) + cb);
-    n = min(RWALK, e0 - m0);
+    n = min(rw, e0 - m0);
   }
   rbase[lane] = c;
   rn[lane] = n;

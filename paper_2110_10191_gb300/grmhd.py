@@ -114,6 +114,7 @@ EXPORTS = ["grmhd_create", "grmhd_destroy", "grmhd_set_prims", "grmhd_set_prims_
            "grmhd_get_geometry", "grmhd_set_geometry", "grmhd_divb", "grmhd_profile", "grmhd_get_profile",
            "grmhd_fp64_peak", "grmhd_fluxes_noalloc", "grmhd_batch_create", "grmhd_batch_destroy",
            "grmhd_batch_step", "grmhd_batch_get_info", "grmhd_batch_sync", "grmhd_autotune",
+           "grmhd_set_recon_walk",
            "grmhd_batch_autotune", "grmhd_batch_set_launch", "grmhd_footprint", "grmhd_server_create",
            "grmhd_server_submit", "grmhd_server_poll", "grmhd_server_drain", "grmhd_server_get_stats",
            "grmhd_server_now", "grmhd_server_destroy", "grmhd_decomp_create", "grmhd_decomp_destroy",
@@ -170,6 +171,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.grmhd_batch_get_info.argtypes = [vp, P(grmhd_batch_info)]
         L.grmhd_batch_sync.argtypes = [vp]
         L.grmhd_autotune.argtypes = [vp, i, P(d), P(d)]
+        L.grmhd_set_recon_walk.argtypes = [vp, i, P(i)]
         L.grmhd_divb.argtypes = [vp, P(d), P(d)]
         L.grmhd_batch_autotune.argtypes = [vp, i, P(d), P(d)]
         L.grmhd_batch_set_launch.argtypes = [vp, i, i, i]
@@ -450,6 +452,14 @@ class Sim:
         _check(self.L.grmhd_autotune(self.h, int(trials), ctypes.byref(a), ctypes.byref(b)),
                "grmhd_autotune")
         return a.value, b.value
+
+    def set_recon_walk(self, zones_per_thread: int = 0) -> int:
+        """Zones per thread of the FP64 reconstruction (1, 2, 4, 8, 16; 0:
+        automatic); returns the length in use.  Values do not depend on it."""
+        c = ctypes.c_int()
+        _check(self.L.grmhd_set_recon_walk(self.h, int(zones_per_thread), ctypes.byref(c)),
+               "grmhd_set_recon_walk")
+        return c.value
 
     def geom(self, loc: int) -> np.ndarray:
         nc = 64 if loc == 3 else 34
