@@ -47,17 +47,19 @@ WORKLOADS = {
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each FP64-bound kernel class on the 128^3 torus, from an ncu capture of one
-# launch of each (kp_recon<0>, kp_face<0>, kp_update).  The figures hold
-# while the kernel sources hash to src_hash; otherwise the bench reports the
-# traffic as unknown (null).
-NCU_TRAFFIC = {"src_hash": "e2cc01990642d415",
-               "torus128": {"recon": 152241664 + 229469952, "flux": 297971456 + 113579264,
-                            "update": 593764864 + 271408640}}
-# sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of the same
-# captures (the hardware's view of the same launches, as a fraction of the
-# nominal 2 FP64 instructions per SM per clock)
-NCU_FP64_PIPE = {"torus128": {"recon": 0.862, "flux": 0.889, "update": 0.887}}
+# each FP64-bound kernel class on the 128^3 torus: the mean over the class's
+# launches (the three directions of kp_recon and kp_face, both stages of
+# kp_update) in the one-pass ncu launch list of the 2-cycle bench command.
+# The figures hold while the kernel sources hash to src_hash; otherwise the
+# bench reports the traffic as unknown (null).
+NCU_TRAFFIC = {"src_hash": "2c7b6619d9bddab2",
+               "torus128": {"recon": 187945118 + 238525750, "flux": 295317912 + 110507282,
+                            "update": 727413302 + 203932617}}
+# sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of full ncu
+# captures of single launches (kp_recon<0> and <1>, the X3 walk taken as X2's;
+# kp_face<0,0>; kp_update): the hardware's view of the same kernels, as a
+# fraction of the nominal 2 FP64 instructions per SM per clock
+NCU_FP64_PIPE = {"torus128": {"recon": 0.858, "flux": 0.902, "update": 0.889}}
 
 
 def kernel_source_hash():
@@ -814,12 +816,14 @@ def build_roofline(prof, cpu, pr, zones, fp64, config, variant="none"):
                         "fp64_pipe_ncu": kd["fp64_pipe_ncu"],
                         "note": "algorithmic flops are the counting oracle's (adds, multiplies, "
                                 "divisions and square roots counted as one each); the kernel spends "
-                                "several FP64 instructions on each division and square root, and a "
-                                "lone add or multiply takes an issue slot worth two flops, so a "
-                                "kernel whose FP64 pipe is saturated reads below 1",
-                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                          "capture of one launch of %s on this workload"
-                                          % kd["kernel"].split()[0]}
+                                "several FP64 instructions on each division and square root and a "
+                                "lone add or multiply takes an issue slot worth two flops, while an "
+                                "FMA does two counted flops in one slot and the kernels form fewer "
+                                "terms than the oracle's plain order (shared differences of the "
+                                "reconstruction walk), so a saturated kernel can read above 1",
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                          "launch of %s, mean over its launches in the ncu launch "
+                                          "list of this workload" % kd["kernel"].split()[0]}
     return roofline, kernels, flops_zc
 
 

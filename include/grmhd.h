@@ -324,7 +324,7 @@ int grmhd_autotune(grmhd_sim *sim, int trials, double *ms_before, double *ms_aft
  * that many consecutive zones of a column along the direction, and
  * consecutive zones share their stencil differences. With 1, one thread
  * takes one zone.  0 restores the automatic choice: the longest walk that
- * still gives every reconstruction launch 152 x 256 threads, else 1.  The
+ * still gives every reconstruction launch 152 x 640 threads, else 1.  The
  * values do not depend on the setting; only the launch shape and the FP64
  * instruction count do.  Synchronises the device.  *chosen (may be NULL)
  * receives the length in use.  GRMHD_ERR_INVALID for other values. */

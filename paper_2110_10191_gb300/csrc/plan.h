@@ -112,9 +112,12 @@ void plan_counts(const Dims &D, int flat3, int prec, int drift, int elec, int rw
                  long long c[PC_N]);
 // The FP64 reconstruction's walk length for a plan of these grids: the
 // longest of 16, 8, 4, 2 zones per thread that still gives each of its
-// launches RWALK_MIN_THREADS threads (enough warps for every SM's FP64
-// unit), else 1 (one thread per zone).
-constexpr long long RWALK_MIN_THREADS = 152 * 256;
+// launches RWALK_MIN_THREADS threads, else 1 (one thread per zone).  About
+// 20 warps per SM keep the FP64 unit at its issue rate; with fewer, each
+// thread's longer chain of dependent work shows (64 small 2D grids with
+// 2-zone walks, 11 warps per SM: 115 us per launch against 84 us one
+// thread per zone).
+constexpr long long RWALK_MIN_THREADS = 152 * 640;
 int plan_rwalk(const StageItem *items, int n);
 // Set the plan's reconstruction walk length (1, 2, 4, 8 or 16 zones per
 // thread; 0: plan_rwalk's choice) and re-lay the reconstruction's block

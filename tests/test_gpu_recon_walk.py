@@ -59,7 +59,7 @@ def test_walk_lengths_bitwise(grmhd, make):
 def test_walk_length_choice_and_errors(grmhd):
     pr = pb.fm_torus(24, 20, 8)
     s = grmhd.Sim(pr)
-    # 26 x 22 x 10 zones cannot give a walk launch 152 x 256 threads
+    # 26 x 22 x 10 zones cannot give a walk launch 152 x 640 threads
     assert s.set_recon_walk(0) == 1
     for bad in (3, 5, 17, 32, -1):
         with pytest.raises(RuntimeError):
