@@ -52,9 +52,9 @@ WORKLOADS = {
 # kp_update) in the one-pass ncu launch list of the 2-cycle bench command.
 # The figures hold while the kernel sources hash to src_hash; otherwise the
 # bench reports the traffic as unknown (null).
-NCU_TRAFFIC = {"src_hash": "2c7b6619d9bddab2",
-               "torus128": {"recon": 187945118 + 238525750, "flux": 295317912 + 110507282,
-                            "update": 727413302 + 203932617}}
+NCU_TRAFFIC = {"src_hash": "eba88d31c039d8f3",
+               "torus128": {"recon": 187897197 + 238533717, "flux": 295329926 + 110699404,
+                            "update": 727515300 + 204019236}}
 # sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of full ncu
 # captures of single launches (kp_recon<0> and <1>, the X3 walk taken as X2's;
 # kp_face<0,0>; kp_update): the hardware's view of the same kernels, as a

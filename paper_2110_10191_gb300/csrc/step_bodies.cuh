@@ -310,6 +310,8 @@ __device__ __forceinline__ void recon_x1_staged(const StepArgs &A, const double 
   }
   rbase[lane] = c;
   rn[lane] = n;
+  if (n == 0)  // a row past the end is never loaded: its walk reads zeros, stores nothing
+    for (int q = 0; q < X1_IN; q++) tin[lane * X1_IN + q] = 0.0;
   __syncwarp();
   const double *x = tin + lane * X1_IN;  // x[q]: this row's value at zone q - 2
 #pragma unroll 1
