@@ -345,6 +345,34 @@ def test_step_parity_torus(grmhd, shape, recon):
     assert st["t"] == pytest.approx(o.time()[0], rel=1e-14)
 
 
+def test_step_parity_unmagnetised_torus(grmhd):
+    """B = 0, the degenerate case of the field terms: the magnetosonic speed
+    is the sound speed (b^2 = 0), 1D_W has no field (B^2 = Q.B = 0), flux-CT
+    carries zero EMFs.  Two steps, primitives and flags against the oracle;
+    the field stays exactly zero."""
+    pr = pb.fm_torus(24, 20, 8, field=False)
+    o, s = _pair(pr, grmhd)
+    o.step(2)
+    s.step(2)
+    Pg, Po = s.get_prims(), o.get_prims()
+    compare(Pg, Po, what="B = 0", ref=o)
+    assert not Pg[5:8].any() and not Po[5:8].any()
+    assert np.array_equal(s.flags()[0], o.flags()[0])
+
+
+@pytest.mark.parametrize("shape,rw", [((37, 21, 9), 16), ((24, 20, 8), 4), ((32, 32, 1), 2)])
+def test_step_parity_walk_lengths(grmhd, shape, rw):
+    """The reconstruction's column walk (forced on grids the automatic choice
+    gives one thread per zone) against the oracle: two steps."""
+    pr = pb.fm_torus(*shape)
+    o, s = _pair(pr, grmhd)
+    assert s.set_recon_walk(rw) == rw
+    o.step(2)
+    s.step(2)
+    compare(s.get_prims(), o.get_prims(), what="walk %d %s" % (rw, shape), ref=o)
+    assert np.array_equal(s.flags()[0], o.flags()[0])
+
+
 def test_bondi_fixed_boundary_parity(grmhd):
     """Michel inflow with X1 ghosts held at the analytic solution (fixed
     boundaries) and the bounds on: three steps against the oracle."""
