@@ -339,6 +339,7 @@ int sim_create(const grmhd_grid *grid, const grmhd_metric *metric, const grmhd_p
     A.xhi[d] = blk ? blk->xhi[d] : 0;
   }
   set_ff_constants(A);
+  set_gas_constants(A);
   A.geomff = s->geomff;
   A.connff = s->connff;
   A.geom = s->geom;

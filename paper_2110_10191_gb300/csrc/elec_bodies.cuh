@@ -230,8 +230,8 @@ __device__ __forceinline__ void elec_post_body(const StepArgs &A, const double *
       const double rho_n = pn[RHO];
       if (A.floors_on) {
         const double rho_fl = __ldg(A.floors + ij), u_fl = __ldg(A.floors + D.n2d + ij);
-        ff = A.floor_drift ? apply_floors_drift(pn, G, rho_fl, u_fl, A.gam, A.igam)
-                           : apply_floors(pn, G, rho_fl, u_fl, A.gam);
+        ff = A.floor_drift ? apply_floors_drift(pn, G, rho_fl, u_fl, A.gk)
+                           : apply_floors(pn, G, rho_fl, u_fl, A.gk);
       }
       ff |= elec_close(A, pn, kn, (pn[RHO] == rho_n) ? ln : log(pn[RHO]));
 #pragma unroll

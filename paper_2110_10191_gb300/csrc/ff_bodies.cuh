@@ -665,10 +665,10 @@ __device__ __forceinline__ void update_ff_body(const StepArgs &A, const double *
       if (lor > FL_GAMMA) {  // the Lorentz-factor cap needs the FP64 fluid state
         Geo Gd;
         load_geo(A.geom, D.n2d, ij, Gd);
-        fl = apply_floors(pd, Gd, rho_fl, u_fl, A.gam);
+        fl = apply_floors(pd, Gd, rho_fl, u_fl, A.gk);
       } else {
         Geo Gd;  // not read on this path
-        fl = apply_floors_known(pd, Gd, rho_fl, u_fl, A.gam, ff_to(bsq_n) * sc.s, lor);
+        fl = apply_floors_known(pd, Gd, rho_fl, u_fl, A.gk, ff_to(bsq_n) * sc.s, lor);
       }
     }
 #pragma unroll

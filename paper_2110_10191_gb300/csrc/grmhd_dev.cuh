@@ -44,6 +44,16 @@ constexpr double FL_BETA = 2.5e-5;
 constexpr double FL_TEMP = 100.0;
 constexpr double FL_GAMMA = 50.0;
 constexpr double FL_DRIFT_BSQ = 1.0e-20;  // drift-frame bounds: weaker fields count as none
+// correctly rounded reciprocals of the divisors above
+constexpr double FL_SIGMA_RCP = 1.0 / FL_SIGMA;
+constexpr double FL_TEMP_RCP = 1.0 / FL_TEMP;
+
+// Adiabatic-index constants of the inversion and the bounds, formed once on
+// the host: gamma, 1/gamma, (gamma - 1)/gamma, and the beta bound's divisor
+// 2 (gamma - 1) with its correctly rounded reciprocal.
+struct GasK {
+  double gam, igam, gf, ubd, ubd_rcp;
+};
 enum {
   FF_GAMMA = 1, FF_RHO_GEOM = 2, FF_U_GEOM = 4, FF_SIGMA = 8, FF_BETA = 16, FF_TEMP = 32,
   FF_DRIFT = 64,      // drift-frame bounds: parcel added, sum inverted
@@ -87,6 +97,17 @@ __device__ __forceinline__ double sqrt_nr(double x) { return x * rsqrt_nr(x); }
 
 // smallest positive normal double
 constexpr double DBL_NORMAL_MIN = 2.2250738585072014e-308;
+
+// x / c correctly rounded, from rc = RN(1/c): q0 = x rc is within one ulp of
+// x/c, its residual x - q0 c is exact in one FMA, and q0 + r rc rounds to
+// RN(x/c) (Markstein's correction, IBM J. Res. Dev. 34 (1990) 111).  For
+// finite x with x/c and x rc in the normal range; three FP64 instructions
+// where the IEEE division sequence takes several more.
+__device__ __forceinline__ double div_rn(double x, double c, double rc) {
+  const double q0 = x * rc;
+  const double r = fma(-q0, c, x);
+  return fma(r, rc, q0);
+}
 
 struct Dims {
   int n[3];   // interior zones
@@ -390,9 +411,10 @@ constexpr double INV_VSQ_MAX = 1.0 - 1.0e-10;
 // On success also returns b^2 = B^2 (1 - v^2) + (Q.B / W)^2 (normal-frame
 // field B, B.v = Q.B/W) and the Lorentz factor of the recovered state, so the
 // bounds need not rebuild the fluid state.
-__device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, double gam,
-                                          double igam, const double Pg[NV], double P[NV],
-                                          double &bsq_out, double &lorentz_out) {
+__device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, const GasK &K,
+                                          const double Pg[NV], double P[NV], double &bsq_out,
+                                          double &lorentz_out) {
+  const double gam = K.gam, igam = K.igam;
 #pragma unroll
   for (int v = 0; v < NV; v++) P[v] = Pg[v];
   const double igd = G.igdet;
@@ -431,7 +453,7 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
   double Wp = (Pg[RHO] + gam * Pg[UU]) * (1.0 + qsq) - D;
   if (Wp < 0.0) Wp = 0.0;
 
-  const double gf = (gam - 1.0) / gam;
+  const double gf = K.gf;  // (gamma - 1)/gamma
   int converged = 0, extra = 0, invalid = 0, have_hi = 0;
   double lo = 0.0, hi = 0.0;
   for (int it = 0; it < INV_MAXIT + INV_EXTRA; it++) {
@@ -512,26 +534,28 @@ __device__ __forceinline__ int invert_1dw(const double U[NV], const Geo &G, doub
 // ---------------------------------------------------------------------------
 // The bounds with b^2 and the Lorentz factor already known (from the
 // inversion); zones that need the Lorentz-factor cap take the general path.
+// The quotients b^2/sigma, beta b^2 / (2 (gamma - 1)) and u/T are the IEEE
+// divisions' values bit for bit (div_rn).
 __device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double rho_fl,
-                                            double u_fl, double gam);
+                                            double u_fl, const GasK &K);
 __device__ __forceinline__ int apply_floors_known(double P[NV], const Geo &G, double rho_fl,
-                                                  double u_fl, double gam, double bsq,
+                                                  double u_fl, const GasK &K, double bsq,
                                                   double lorentz) {
-  if (lorentz > FL_GAMMA) return apply_floors(P, G, rho_fl, u_fl, gam);
+  if (lorentz > FL_GAMMA) return apply_floors(P, G, rho_fl, u_fl, K);
   int fl = 0;
   if (P[RHO] < rho_fl) { P[RHO] = rho_fl; fl |= FF_RHO_GEOM; }
   if (P[UU] < u_fl) { P[UU] = u_fl; fl |= FF_U_GEOM; }
-  const double rs = bsq / FL_SIGMA;
+  const double rs = div_rn(bsq, FL_SIGMA, FL_SIGMA_RCP);
   if (P[RHO] < rs) { P[RHO] = rs; fl |= FF_SIGMA; }
-  const double ub = FL_BETA * bsq / (2.0 * (gam - 1.0));
+  const double ub = div_rn(FL_BETA * bsq, K.ubd, K.ubd_rcp);
   if (P[UU] < ub) { P[UU] = ub; fl |= FF_BETA; }
-  const double rt = P[UU] / FL_TEMP;
+  const double rt = div_rn(P[UU], FL_TEMP, FL_TEMP_RCP);
   if (P[RHO] < rt) { P[RHO] = rt; fl |= FF_TEMP; }
   return fl;
 }
 
 __device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double rho_fl,
-                                            double u_fl, double gam) {
+                                            double u_fl, const GasK &K) {
   int fl = 0;
   const double v1 = P[U1], v2 = P[U2], v3 = P[U3];
   const double qsq = v1 * (G.gcov[SY(1, 1)] * v1 + G.gcov[SY(1, 2)] * v2 + G.gcov[SY(1, 3)] * v3) +
@@ -548,11 +572,11 @@ __device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double r
   fluid_state(P, G, s);
   if (P[RHO] < rho_fl) { P[RHO] = rho_fl; fl |= FF_RHO_GEOM; }
   if (P[UU] < u_fl) { P[UU] = u_fl; fl |= FF_U_GEOM; }
-  const double rs = s.bsq / FL_SIGMA;
+  const double rs = div_rn(s.bsq, FL_SIGMA, FL_SIGMA_RCP);
   if (P[RHO] < rs) { P[RHO] = rs; fl |= FF_SIGMA; }
-  const double ub = FL_BETA * s.bsq / (2.0 * (gam - 1.0));
+  const double ub = div_rn(FL_BETA * s.bsq, K.ubd, K.ubd_rcp);
   if (P[UU] < ub) { P[UU] = ub; fl |= FF_BETA; }
-  const double rt = P[UU] / FL_TEMP;
+  const double rt = div_rn(P[UU], FL_TEMP, FL_TEMP_RCP);
   if (P[RHO] < rt) { P[RHO] = rt; fl |= FF_TEMP; }
   return fl;
 }
@@ -569,11 +593,12 @@ __device__ __forceinline__ int apply_floors(double P[NV], const Geo &G, double r
 // bounds run once more.  If that inversion fails the fluid-frame result is
 // kept.
 static __device__ __noinline__ int apply_floors_drift(double P[NV], const Geo &G, double rho_fl,
-                                                      double u_fl, double gam, double igam) {
+                                                      double u_fl, const GasK &K) {
+  const double gam = K.gam;
   double Pf[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) Pf[v] = P[v];
-  int fl = apply_floors(Pf, G, rho_fl, u_fl, gam);
+  int fl = apply_floors(Pf, G, rho_fl, u_fl, K);
   if (!(fl & ~FF_GAMMA)) {
 #pragma unroll
     for (int v = 0; v < NV; v++) P[v] = Pf[v];
@@ -616,12 +641,12 @@ static __device__ __noinline__ int apply_floors_drift(double P[NV], const Geo &G
 #pragma unroll
   for (int v = 0; v < NV; v++) Us[v] += Up[v];
   double Pn[NV], bsq, lor;
-  if (invert_1dw(Us, G, gam, igam, Pf, Pn, bsq, lor) != PF_OK) {
+  if (invert_1dw(Us, G, K, Pf, Pn, bsq, lor) != PF_OK) {
 #pragma unroll
     for (int v = 0; v < NV; v++) P[v] = Pf[v];
     return fl | FF_DRIFT_FAIL;
   }
-  fl |= FF_DRIFT | apply_floors(Pn, G, rho_fl, u_fl, gam);
+  fl |= FF_DRIFT | apply_floors(Pn, G, rho_fl, u_fl, K);
 #pragma unroll
   for (int v = 0; v < NV; v++) P[v] = Pn[v];
   return fl;

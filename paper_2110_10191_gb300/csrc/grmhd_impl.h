@@ -37,6 +37,7 @@ struct StepArgs {
   Dims D;
   double gam, igam, cfl;  // adiabatic index, its reciprocal, Courant number
   double gm1, ggm1;       // gamma - 1 and gamma (gamma - 1)
+  GasK gk;                // the inversion's and the bounds' constants (set_gas_constants)
   double dx[3], idx[3];  // zone widths and their reciprocals
   int recon, floors_on;
   // zones per thread of the FP64 reconstruction along a column (2..16), or 1:
@@ -65,6 +66,16 @@ struct StepArgs {
   const double *floors;
   Clock *clk;
 };
+
+// the inversion's and the bounds' adiabatic-index constants (IEEE host
+// arithmetic: the values a per-zone division would give)
+inline void set_gas_constants(StepArgs &A) {
+  A.gk.gam = A.gam;
+  A.gk.igam = A.igam;
+  A.gk.gf = (A.gam - 1.0) / A.gam;
+  A.gk.ubd = 2.0 * (A.gam - 1.0);
+  A.gk.ubd_rcp = 1.0 / A.gk.ubd;
+}
 
 // the float-float words of the adiabatic-index constants
 inline void set_ff_constants(StepArgs &A) {

@@ -139,6 +139,7 @@ extern "C" int grmhd_fluxes_noalloc(const grmhd_grid *grid, const grmhd_metric *
   A.floors = G.floors;
   A.clk = clk;
   set_ff_constants(A);
+  set_gas_constants(A);
 
   // faces outside the computed ranges read as zero, as in grmhd_get_fluxes
   const size_t fbytes = sizeof(double) * NV * (size_t)D.ntot;

@@ -677,9 +677,9 @@ __device__ __forceinline__ void update_body(const StepArgs &A, const double *Pi,
       Un[v] = (v >= UU && v <= U3) ? fma(dtp, S[v - UU] - div, Ui[v]) : fma(-dtp, div, Ui[v]);
     }
     double pn[NV], bsq_n = 0.0, lor_n = 1.0;
-    pf = invert_1dw(Un, G, A.gam, A.igam, pi, pn, bsq_n, lor_n);
+    pf = invert_1dw(Un, G, A.gk, pi, pn, bsq_n, lor_n);
     if (pf == PF_OK && A.floors_on && !A.floor_drift && !A.elec)
-      ff = apply_floors_known(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
+      ff = apply_floors_known(pn, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gk,
                               bsq_n, lor_n);
 #pragma unroll
     for (int v = 0; v < NV; v++) Pout[v * N + c] = pn[v];
@@ -715,8 +715,7 @@ __device__ __forceinline__ void floor_drift_body(const StepArgs &A, double *P,
       double p[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) p[v] = P[v * N + c];
-      ff = apply_floors_drift(p, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam,
-                              A.igam);
+      ff = apply_floors_drift(p, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gk);
       if (ff) {
 #pragma unroll
         for (int v = 0; v < NV; v++) P[v * N + c] = p[v];
@@ -773,7 +772,7 @@ __device__ __forceinline__ void fixup_body(const StepArgs &A, double *P, const i
           const long long ij = (long long)j * D.s[0] + i;
           Geo G;
           load_geo(A.geom, D.n2d, ij, G);
-          const int f = apply_floors(p, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gam);
+          const int f = apply_floors(p, G, __ldg(A.floors + ij), __ldg(A.floors + D.n2d + ij), A.gk);
           if (f) {
             fflag[c] |= f;
             hit = true;
