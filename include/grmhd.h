@@ -360,7 +360,11 @@ int grmhd_fp64_probe(int op, int chains, int blocks_per_sm, long long iters,
  * the approximations flush subnormal inputs and results to zero: for fn 0 a
  * zero or subnormal x gives NaN and |x| > 2^1022 a zero of x's sign; the
  * step sends zero and subnormal arguments of fn 2 to a branch of its own.
- * GRMHD_ERR_INVALID: fn outside 0..2, n < 0, NULL pointers with n > 0. */
+ * fn 3, 4: the quotients of the bounds ("Implementation Notes", list of
+ * bounds), x / 400 (b^2 / sigma_max) and x / 100 (u / T-bound), by one
+ * correction step from the divisor's correctly rounded reciprocal: the IEEE
+ * quotient bit for bit for finite x whose quotient is normal.
+ * GRMHD_ERR_INVALID: fn outside 0..4, n < 0, NULL pointers with n > 0. */
 int grmhd_arith(int fn, const double *x, double *out, long long n, void *stream);
 
 /* Face-flux stage without any device allocation (no counterpart in the

@@ -7,8 +7,8 @@
 // over directions with more than one zone; corners between interior zones
 // only (a direction with one zone takes its single layer and the ghost copy
 // below it).  Also the step's reciprocal, reciprocal square root and square
-// root on an array (grmhd_arith), so that their accuracy can be checked on
-// the device.
+// root, and the bounds' quotients, on an array (grmhd_arith), so that their
+// accuracy can be checked on the device.
 #include "../../include/grmhd.h"
 #include "grmhd_dev.cuh"
 #include "grmhd_impl.h"
@@ -72,13 +72,17 @@ __global__ void k_arith(const double *__restrict__ x, double *__restrict__ out, 
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
   const double v = x[t];
-  out[t] = FN == 0 ? rcp_nr(v) : FN == 1 ? rsqrt_nr(v) : sqrt_nr(v);
+  out[t] = FN == 0   ? rcp_nr(v)
+           : FN == 1 ? rsqrt_nr(v)
+           : FN == 2 ? sqrt_nr(v)
+           : FN == 3 ? div_rn(v, FL_SIGMA, FL_SIGMA_RCP)
+                     : div_rn(v, FL_TEMP, FL_TEMP_RCP);
 }
 
 }  // namespace grmhd
 
 extern "C" int grmhd_arith(int fn, const double *x, double *out, long long n, void *stream) {
-  if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !out))) return GRMHD_ERR_INVALID;
+  if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !out))) return GRMHD_ERR_INVALID;
   if (n == 0) return GRMHD_OK;
   const long long nb = (n + grmhd::BS - 1) / grmhd::BS;
   if (nb >= (1ll << 31)) return GRMHD_ERR_INVALID;
@@ -86,5 +90,7 @@ extern "C" int grmhd_arith(int fn, const double *x, double *out, long long n, vo
   if (fn == 0) grmhd::k_arith<0><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
   if (fn == 1) grmhd::k_arith<1><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
   if (fn == 2) grmhd::k_arith<2><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
+  if (fn == 3) grmhd::k_arith<3><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
+  if (fn == 4) grmhd::k_arith<4><<<(unsigned)nb, grmhd::BS, 0, st>>>(x, out, n);
   return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }

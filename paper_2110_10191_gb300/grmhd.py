@@ -286,12 +286,13 @@ def fluxes_noalloc(problem, P, F, stream=None):
     return ct
 
 
-ARITH = {"rcp": 0, "rsqrt": 1, "sqrt": 2}
+ARITH = {"rcp": 0, "rsqrt": 1, "sqrt": 2, "div_sigma": 3, "div_temp": 4}
 
 
 def arith(fn, x, out, stream=None):
-    """The step's reciprocal ("rcp"), reciprocal square root ("rsqrt") or
-    square root ("sqrt") of every element of the device tensor x into out
+    """The step's reciprocal ("rcp"), reciprocal square root ("rsqrt"),
+    square root ("sqrt") or the bounds' quotients x / 400 ("div_sigma") and
+    x / 100 ("div_temp") of every element of the device tensor x into out
     (float64, same size; see grmhd_arith in include/grmhd.h)."""
     xp, xdev = _ptr(x)
     op, odev = _ptr(out)

@@ -11,7 +11,9 @@ magnitudes the WENO5 pair feeds the reciprocal (products of two sums of
 squared smoothness indicators), 1 + q^2 and 1 - v^2 as the fluid state and
 the inversion form them, and exact powers of two.  Outside
 [2^-1022, 2^1022] the reciprocal flushes (zero or subnormal x -> NaN,
-|x| > 2^1022 -> 0), as the header states."""
+|x| > 2^1022 -> 0), as the header states.  The bounds' quotients (one
+correction step from the divisor's reciprocal) must equal the device's IEEE
+division bit for bit."""
 import numpy as np
 import pytest
 
@@ -57,9 +59,10 @@ def _run(dev, fn, xs):
     x = torch.from_numpy(xs).cuda()
     out = torch.empty_like(x)
     grmhd.arith(fn, x, out)
-    ref = {"rcp": torch.reciprocal, "rsqrt": torch.rsqrt, "sqrt": torch.sqrt}[fn](x)
+    refs = {"rcp": torch.reciprocal, "rsqrt": torch.rsqrt, "sqrt": torch.sqrt}
+    ref = refs[fn](x) if fn in refs else None
     torch.cuda.synchronize()
-    return out.cpu().numpy(), ref.cpu().numpy()
+    return out.cpu().numpy(), None if ref is None else ref.cpu().numpy()
 
 
 def _normal(xs):
@@ -114,4 +117,25 @@ def test_rcp_outside_the_normal_range(dev):
     with pytest.raises(grmhd.GrmhdError):
         x = torch.zeros(4, dtype=torch.float64, device="cuda")
         grmhd.load()
-        grmhd._check(grmhd.load().grmhd_arith(3, x.data_ptr(), x.data_ptr(), 4, None), "grmhd_arith")
+        grmhd._check(grmhd.load().grmhd_arith(5, x.data_ptr(), x.data_ptr(), 4, None), "grmhd_arith")
+
+
+@pytest.mark.parametrize("fn,c", [("div_sigma", 400.0), ("div_temp", 100.0)])
+def test_bound_quotients_bitwise_ieee(dev, fn, c):
+    """The bounds' quotients b^2/400 and u/100 by one correction step from
+    the divisor's correctly rounded reciprocal: the IEEE quotient bit for bit
+    (numpy's division on the host; torch's division of a CUDA tensor by a
+    scalar multiplies by the scalar's reciprocal, which is not the IEEE
+    quotient), over 1e6 values spread log-uniformly over 1e-290 .. 1e290 and
+    powers of two, their multiples of the divisor and the neighbours of
+    both."""
+    torch, grmhd = dev
+    rng = np.random.default_rng(7)
+    xs = 10.0 ** rng.uniform(-290.0, 290.0, 1_000_000)
+    p2 = 2.0 ** np.arange(-960, 960, 7, dtype=np.float64)
+    edge = np.concatenate([p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf), p2 * c,
+                           np.nextafter(p2 * c, 0.0), np.nextafter(p2 * c, np.inf)])
+    xs = np.concatenate([xs, edge])
+    a, _ = _run(dev, fn, xs)
+    ref = xs / c
+    assert np.array_equal(a.view(np.int64), ref.view(np.int64)), int((a != ref).sum())
