@@ -268,7 +268,7 @@ __device__ __forceinline__ void flux_cons_acc_ff(const ff P[NV], const FStateFF 
   acc[B3] = ff_add(acc[B3], ff_sub(ff_mul(s.bcon[3], uc), ff_mul(bc, s.ucon[3])));
 }
 
-// fast magnetosonic speeds along dir (mhd_vchar)
+// fast magnetosonic speeds along dir (the quadratic of mhd_cmax)
 // gam: the adiabatic index, ggm1 = gam (gam - 1), both float-float
 __device__ __forceinline__ void mhd_vchar_ff(const ff P[NV], const FStateFF &s, const GeoFF &G,
                                              ff gam, ff ggm1, int dir, ff &vmax, ff &vmin) {

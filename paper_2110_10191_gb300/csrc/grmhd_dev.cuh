@@ -246,10 +246,12 @@ __device__ __forceinline__ void flux_cons_acc(const double P[NV], const FState &
 // With cs2 = gamma (gamma - 1) u / e_f, va2 = b^2 / (b^2 + e_f) and
 // e_f = rho + gamma u, the combination is exactly
 // cms2 = (gamma (gamma - 1) u + b^2) / (b^2 + e_f): one reciprocal, no
-// cancellation.  ggm1 = gamma (gamma - 1).
-__device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, const Geo &G,
-                                          double gam, double ggm1, int dir, double &vmax,
-                                          double &vmin) {
+// cancellation.  ggm1 = gamma (gamma - 1).  Returns the larger magnitude of
+// the two roots (hb +- disc)/qa, disc >= 0: (|hb| + disc)/|qa|, the same
+// rounded value as the larger rounded root's magnitude (the LLF flux and
+// the time step need only it).
+__device__ __forceinline__ double mhd_cmax(const double P[NV], const FState &s, const Geo &G,
+                                           double gam, double ggm1, int dir) {
   const double ef = fma(gam, P[UU], P[RHO]);
   const double ee = s.bsq + ef;
   const double cms2 = fma(ggm1, P[UU], s.bsq) * rcp_nr(ee);
@@ -265,11 +267,7 @@ __device__ __forceinline__ void mhd_vchar(const double P[NV], const FState &s, c
   const double qc = Au * Au - (Asq + Au * Au) * cms2;
   double disc = fma(hb, hb, -(qa * qc));
   disc = (disc >= DBL_NORMAL_MIN) ? sqrt_nr(disc) : 0.0;  // a subnormal root is negligible
-  const double ia = rcp_nr(qa);
-  const double v1 = (hb + disc) * ia;
-  const double v2 = (hb - disc) * ia;
-  vmax = fmax(v1, v2);
-  vmin = fmin(v1, v2);
+  return (fabs(hb) + disc) * fabs(rcp_nr(qa));
 }
 
 // ---------------------------------------------------------------------------

@@ -61,12 +61,8 @@ __global__ void __launch_bounds__(BS) k_flux(StepArgs A, const double *__restric
     FState sL, sR;
     fluid_state(PL, G, sL);
     fluid_state(PR, G, sR);
-    double vmaxL, vminL, vmaxR, vminR;
-    mhd_vchar(PL, sL, G, A.gam, A.ggm1, DIR + 1, vmaxL, vminL);
-    mhd_vchar(PR, sR, G, A.gam, A.ggm1, DIR + 1, vmaxR, vminR);
-    const double cmax = fmax(fmax(0.0, vmaxL), vmaxR);
-    const double cmin = fmax(fmax(0.0, -vminL), -vminR);
-    const double ct = fmax(cmax, cmin);
+    const double ct = fmax(mhd_cmax(PL, sL, G, A.gam, A.ggm1, DIR + 1),
+                           mhd_cmax(PR, sR, G, A.gam, A.ggm1, DIR + 1));
     double FL[NV], FR[NV], UL[NV], UR[NV];
     prim_flux(PL, sL, G, A.gam, DIR + 1, FL);
     prim_flux(PR, sR, G, A.gam, DIR + 1, FR);

@@ -400,12 +400,10 @@ __device__ __forceinline__ void face_body(const StepArgs &A, const double *__res
     FState sL, sR;
     fluid_state(PL, G, sL);
     fluid_state(PR, G, sR);
-    double vmaxL, vminL, vmaxR, vminR;
-    mhd_vchar(PL, sL, G, A.gam, A.ggm1, DIR + 1, vmaxL, vminL);
-    mhd_vchar(PR, sR, G, A.gam, A.ggm1, DIR + 1, vmaxR, vminR);
-    // c_top = max(0, vmax_L, vmax_R, -vmin_L, -vmin_R); vmax >= vmin on each
-    // side, so max(vmax, -vmin) >= 0 and the 0 never decides
-    const double ct = fmax(fmax(vmaxL, -vminL), fmax(vmaxR, -vminR));
+    // c_top = max(0, vmax_L, vmax_R, -vmin_L, -vmin_R): the larger root
+    // magnitude of either side
+    const double ct = fmax(mhd_cmax(PL, sL, G, A.gam, A.ggm1, DIR + 1),
+                           mhd_cmax(PR, sR, G, A.gam, A.ggm1, DIR + 1));
     // LLF: F = 1/2 sqrt(-g) [(F_L + ct U_L) + (F_R - ct U_R)]
     double acc[NV];
     flux_cons_acc<true>(PL, sL, A.gm1, DIR + 1, ct, acc);
