@@ -425,6 +425,8 @@ typedef struct {
   long long launches;     /* kernels launched by grmhd_batch_step so far */
   int graph;              /* 1 once a CUDA graph of the step has been captured */
   int tuned;              /* 1 after grmhd_batch_autotune */
+  int recon_walk;         /* zones per thread of the FP64 reconstruction (1: one per
+                             zone; see grmhd_set_recon_walk), chosen over all grids */
 } grmhd_batch_info;
 
 /* Group nsims simulations (created by grmhd_create on the current device;

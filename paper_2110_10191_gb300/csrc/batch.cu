@@ -190,6 +190,7 @@ extern "C" int grmhd_batch_get_info(grmhd_batch *b, grmhd_batch_info *out) {
   out->launches = b->launches;
   out->graph = b->exec ? 1 : 0;
   out->tuned = b->plan.tuned;
+  out->recon_walk = b->plan.ngrid > 0 ? b->plan.host_items[0].A.rwalk : 0;
   return GRMHD_OK;
 }
 

@@ -78,7 +78,7 @@ class grmhd_stats(ctypes.Structure):
 class grmhd_batch_info(ctypes.Structure):
     _fields_ = [("ngrid", ctypes.c_int), ("zones", ctypes.c_longlong),
                 ("launches_per_step", ctypes.c_int), ("launches", ctypes.c_longlong),
-                ("graph", ctypes.c_int), ("tuned", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("tuned", ctypes.c_int), ("recon_walk", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -48,6 +48,39 @@ def _alone(grmhd, pr, nsteps):
     return out, st
 
 
+def test_batch_with_walks_bitwise_equals_alone(grmhd):
+    """A batch large enough for the reconstruction's column walks (six tori
+    of three sizes, different perturbations, fields and reconstructions, with
+    a 2D and a mixed-precision grid beside them: 2-zone walks) while each
+    grid alone is too small for them and takes one thread per zone: every
+    grid bitwise its state alone, the X1 walk's shared-memory staging
+    included."""
+    probs = [pb.fm_torus(40, 32, 24, seed=s) for s in range(3)]
+    probs += [pb.fm_torus(64, 32, 16, seed=s) for s in range(2)]
+    probs.append(pb.fm_torus(40, 40, 20, recon=pb.RECON_MC, beta=30.0))
+    probs.append(pb.orszag_tang(64, recon=pb.RECON_WENO5))
+    mixed = pb.orszag_tang(64, recon=pb.RECON_WENO5)
+    mixed.precision = 1
+    probs.append(mixed)
+    nsteps = 2
+    ref = [_alone(grmhd, pr, nsteps) for pr in probs]
+    one = grmhd.Sim(probs[0])
+    assert one.set_recon_walk(0) == 1  # alone: one thread per zone
+    one.close()
+    sims = []
+    for pr in probs:
+        s = grmhd.Sim(pr)
+        s.set_prims(pr.P)
+        sims.append(s)
+    b = grmhd.Batch(sims)
+    assert b.info()["recon_walk"] >= 2
+    b.step(nsteps, graph=True, sync=True)
+    for s, (P, st), pr in zip(sims, ref, probs):
+        assert np.array_equal(s.get_prims(with_ghosts=True), P), pr.name
+        assert s.stats()["t"] == st["t"], pr.name
+    b.close()
+
+
 @pytest.mark.parametrize("graph", [True, False])
 def test_batch_bitwise_equals_alone(grmhd, graph):
     probs = _mixture()
