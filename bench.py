@@ -55,9 +55,9 @@ WORKLOADS = {
 # kp_update) in the one-pass ncu launch list of the 2-cycle bench command.
 # The figures hold while the kernel sources hash to src_hash; otherwise the
 # bench reports the traffic as unknown (null).
-NCU_TRAFFIC = {"src_hash": "868d5fe6db9c976e",
-               "torus128": {"recon": 187819111 + 238393526, "flux": 295344487 + 110695350,
-                            "update": 727535396 + 204101906}}
+NCU_TRAFFIC = {"src_hash": "5e804b7ef44b62a1",
+               "torus128": {"recon": 187957174 + 238592572, "flux": 295317248 + 110696210,
+                            "update": 727520073 + 204079488}}
 # sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active of full ncu
 # captures of single launches (kp_recon<0> and <1>, the X3 walk taken as X2's;
 # kp_face<0,0>; kp_update): the hardware's view of the same kernels, as a
